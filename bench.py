@@ -1,0 +1,358 @@
+"""Benchmark: batched 3D E,T,pH-REMD C(pH,E)MD steps on one GB300.
+
+Workload (one "step" = one step of the full schedule for every walker: Born
+radii, GB + Coulomb + LJ pair pass, chain rule + bonded terms, Langevin; MC
+sweeps every 10 steps, one exchange attempt every 100): 8 E x 6 T x 8 pH = 384
+replicas over three seeded synthetic systems of 500, 2000 and 8000 atoms
+(128 replicas each), FP32 pair arithmetic with int64 fixed-point accumulation.
+
+Metric: aggregate replica-steps/s (and unordered GB pair-evaluations/s through
+all three pair passes), batched launch; the same steps issued as per-replica
+launches are timed beside it.  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own independent 384-replica
+ensemble (own seed) on its own GPU: no data-path collective; the value is the
+sum over ranks of replica-steps divided by the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "aggregate replica-steps/s & GB pair evals/s, batched vs per-replica launches"
+WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-atom systems"
+# Algorithmic cost of one unordered pair in each pass, counted from the closed
+# forms (FP32-pipe instructions incl. FMA as 1, MUFU transcendental ops).
+PASS_COST = {"born": (45, 7), "gb": (41, 3), "chain": (47, 7)}
+N_SM = 152
+
+
+def pairs_per_clk_per_sm(fp32, mufu):
+    """Issue-slot and MUFU bound: 128 instructions / clk / SM over all
+    instructions, 16 MUFU ops / clk / SM."""
+    return min(128.0 / (fp32 + mufu), 16.0 / mufu)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload():
+    from paper_1809_07726_gb300 import synth
+    return synth.config_c4()
+
+
+def pair_count(systems, grid):
+    n = [systems[s].n for s in grid.system_of_slot]
+    return sum(k * (k - 1) // 2 for k in n)
+
+
+def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
+    n = 4 + 1  # born, gb, chain, langevin + the step-counter tick of a one-step cph_run
+    if t > 0:
+        n += int(t % mc_ph == 0) + int(t % mc_redox == 0) + int(t % ex_every == 0)
+    return n
+
+
+# ----------------------------------------------------------------- oracle arm
+
+def oracle_sample(systems, grid, walkers, n_steps, seed):
+    """Time the FP64 oracle (as it stands) on ``walkers`` for n_steps of the
+    schedule, single-threaded; returns (seconds, pairs processed)."""
+    import oracle
+    W = oracle.Walkers(systems, grid, seed=seed)
+    W.t = 1
+    t0 = time.perf_counter()
+    oracle.run_schedule(W, n_steps, walkers=walkers)
+    dt = time.perf_counter() - t0
+    pairs = sum(systems[grid.system_of_slot[w]].n * (systems[grid.system_of_slot[w]].n - 1) // 2
+                for w in walkers) * n_steps
+    return dt, pairs
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample (one walker of the 500-atom system), scaled to the workload's
+    replica-steps/s by pair count (the oracle's cost is O(N^2) pair loops)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    systems, grid = workload()
+    total_pairs = pair_count(systems, grid)
+    sample = [0]
+    for _ in range(args.warmup):
+        oracle_sample(systems, grid, sample, 1, seed=4)
+    secs = 0.0
+    pairs = 0
+    for _ in range(args.steps):
+        dt, p = oracle_sample(systems, grid, sample, 1, seed=4)
+        secs += dt
+        pairs += p
+    pair_rate = pairs / secs
+    value = 384.0 / (total_pairs / pair_rate)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "replica-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_pairs / pair_rate, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "cpu oracle, 1 thread"},
+            "pair_evals_per_s": pair_rate,
+            "cpu_baseline": {"value": value, "unit": "replica-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: one full-schedule step of one 500-atom walker, "
+                                       "scaled to the 384-walker mix by unordered pair count"},
+            "e2e": {"value": value, "unit": "replica-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_07726_gb300 import build, cphremd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    systems, grid = workload()
+    total_pairs = pair_count(systems, grid)
+    W = grid.n_slots
+    seed = 4 + 1000 * rank
+    eng = cphremd.init_system(systems, grid, seed=seed)
+    # L2 flush buffer (256 MB > 129 MB L2), written between timed steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    eng.run(1)  # step 0
+    eng.run(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    t_first = eng.get_step()
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            eng.run(1)
+            ends[k].record(stream)
+            launches += schedule_launches(t_first + k)
+        barrier()
+        wall = time.perf_counter() - wall0
+    eng.status()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(ms) / 1e3
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * W * args.steps / t_max
+    clocks = clk.summary()
+
+    # graph replay of whole schedule periods (no flush between steps)
+    period = 100
+    while eng.get_step() % period != 1:
+        eng.run(1)
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    eng.run(period)
+    g1.record(stream)
+    barrier()
+    graph_ms = g0.elapsed_time(g1) / period
+
+    # dominant pair pass: CUDA events around each pass on the launching stream
+    pass_ms = eng.time_passes(reps=3)
+    names = ["born", "gb", "chain"]
+    dom = int(np.argmax(pass_ms))
+    f_mhz = clocks["sm_mhz"] or 2070.0
+    fp, mu = PASS_COST[names[dom]]
+    peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(fp, mu) / 1e9
+    achieved = total_pairs / (pass_ms[dom] / 1e3) / 1e9
+    step_peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(
+        sum(v[0] for v in PASS_COST.values()), sum(v[1] for v in PASS_COST.values())) / 1e9
+
+    # per-replica launches of the same steps
+    pr = cphremd.init_system(systems, grid, seed=seed)
+    pr.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
+    pr.run(1)
+    pr.run(2)
+    barrier()
+    n_pr = max(3, args.steps // 10)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(n_pr):
+        pr.run(1)
+    p1.record(stream)
+    barrier()
+    pr_ms = p0.elapsed_time(p1) / n_pr
+    pr_pass_ms = pr.time_passes(reps=1)
+    del pr
+
+    # end to end through the public API from host buffers: init (H2D of the
+    # systems) + per-step run and D2H of energies and the condition map
+    barrier()
+    e2e0 = time.perf_counter()
+    e2 = cphremd.init_system(systems, grid, seed=seed)
+    h2d = sum(s.n * (3 * 8 + 7 * 8) for s in systems) + sum(
+        systems[s].n * 3 * 8 for s in grid.system_of_slot)
+    n_e2e = args.steps
+    d2h = 0
+    for _ in range(n_e2e):
+        e2.run(1)
+        e2.energies()
+        e2.condition_map()
+        d2h += W * 6 * 8 + W * 4
+    barrier()
+    e2e_s = time.perf_counter() - e2e0
+    e2e_value = W * n_e2e / e2e_s
+    del e2
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1:
+        import oracle
+        oracle.build()
+        sample = [0, 128, 320]  # one walker per system size (500, 2000, 8000 atoms)
+        secs, pairs = oracle_sample(systems, grid, sample, 1, seed=seed)
+        cpu_value = 384.0 / (total_pairs / (pairs / secs))
+        cpu = {"value": cpu_value, "unit": "replica-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "one full-schedule step of 3 walkers (500, 2000, 8000 atoms), "
+                         f"{secs:.1f} s single-threaded, scaled to the 384-walker mix by "
+                         "unordered pair count"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "replica-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "replicas": W, "atoms": [s.n for s in systems],
+                   "precision": "FP32 pair math, int64 fixed-point accumulation",
+                   "schedule": "MC (pH then redox) every 10 steps, exchange every 100 (E,pH,T)",
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas batched per launch; {world} independent ensemble(s)"},
+        "pair_evals_per_s": world * total_pairs * args.steps / t_max,
+        "per_replica": {"value": W / (pr_ms / 1e3), "unit": "replica-steps/s", "ms_per_step": pr_ms,
+                        "pass_ms": [float(x) for x in pr_pass_ms],
+                        "speedup_batched": pr_ms / (1e3 * t_max / args.steps)},
+        "graph_replay": {"value": W / (graph_ms / 1e3), "unit": "replica-steps/s",
+                         "ms_per_step": graph_ms, "steps": period},
+        "pass_ms": {n: float(x) for n, x in zip(names, pass_ms)},
+        "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
+                     "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) x "
+                                   f"min(128/({fp}+{mu}), 16/{mu}) pairs/clk/SM",
+                     "step_frac": (total_pairs / (sum(pass_ms) / 1e3) / 1e9) / step_peak},
+        "e2e": {"value": e2e_value, "unit": "replica-steps/s",
+                "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

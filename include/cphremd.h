@@ -1,0 +1,297 @@
+/*
+ * cphremd.h -- C ABI of the GB300 engine for multidimensional E,pH,T replica
+ * exchange with constant pH and redox potential MD (C(pH,E)MD) in OBC
+ * generalized-Born implicit solvent (Cruzeiro & Roitberg, arXiv 1809.07726).
+ *
+ * Paper passages the calls follow (section names of the paper):
+ *   - C(pH,E)MD: MD runs for a set number of steps, then protonation and/or
+ *     redox state changes are attempted by Monte Carlo; protonation goes first
+ *     when both fall on one step; intervals are independent
+ *     ("Constant pH and Redox Potential Molecular Dynamics").
+ *   - Exchange probabilities along pH, E and T: eqs (3), (4), (5).
+ *   - Multidimensional REMD: one dimension per attempt, in a user order,
+ *     between nearest neighbours that share the other two conditions, every
+ *     EAF steps ("AMBER's multidimensional REMD module").
+ *   - Implicit solvent: the Onufriev-Bashford-Case GB model ("igb=2") is used
+ *     for MD and for the state-change attempts ("Implicit Solvent
+ *     Calculations"); Langevin dynamics with 10 ps^-1 friction and 2 fs steps
+ *     (same section).
+ *
+ * Conventions
+ *   Units: kcal/mol, Angstrom, e, amu, ps, K, V.
+ *   Every call returns CPH_OK (0) or a negative CPH_E_* code; the message of
+ *   the last failure is available from cph_last_error().  No C++ exception
+ *   crosses this interface.  Calls on one engine are not thread-safe.
+ *   Host pointers ("host") are read during the call and not retained; device
+ *   pointers ("device") belong to the caller.  The engine owns every device
+ *   buffer it allocates; cph_destroy() frees them.
+ *   Work on an engine is queued on the CUDA stream passed as `stream`
+ *   (a cudaStream_t; NULL = the legacy default stream).  Getters synchronise
+ *   that stream first.  Asynchronous device errors surface at the next getter
+ *   or cph_status().
+ *
+ * Condition grid: slot = iE + nE * (ipH + npH * iT).  Walker w starts at slot
+ * w; exchanges move walkers between slots (conditions), never coordinates.
+ * Atom a of walker w is stored at global index offsets[w] + a
+ * (cph_walker_offsets).
+ */
+#ifndef CPHREMD_H
+#define CPHREMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes */
+#define CPH_OK 0
+#define CPH_E_INVALID (-1)   /* bad argument or descriptor; nothing was changed */
+#define CPH_E_CUDA (-2)      /* a CUDA runtime call failed */
+#define CPH_E_OOM (-3)       /* device allocation failed */
+#define CPH_E_NONFINITE (-4) /* a non-finite force, energy or position was produced */
+#define CPH_E_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define CPH_E_STATE (-6)     /* call not valid in the engine's current state */
+
+/* ---- enumerations */
+#define CPH_SITE_PH 0
+#define CPH_SITE_REDOX 1
+
+#define CPH_DIM_E 0
+#define CPH_DIM_PH 1
+#define CPH_DIM_T 2
+#define CPH_DIM_NEXT (-1) /* next dimension of the user order */
+
+#define CPH_MC_PH 1
+#define CPH_MC_REDOX 2
+#define CPH_MC_BOTH 3 /* protonation sweep, then redox sweep */
+
+#define CPH_PREC_FP64 0 /* FP64 pair arithmetic and accumulation */
+#define CPH_PREC_FP32 1 /* FP32 pair arithmetic, int64 fixed-point accumulation */
+
+/* energy terms returned per walker */
+#define CPH_E_GB 0
+#define CPH_E_COUL 1
+#define CPH_E_LJ 2
+#define CPH_E_BOND 3
+#define CPH_E_ANGLE 4
+#define CPH_E_TOTAL 5
+#define CPH_NTERMS 6
+
+/* ---- descriptors (all host memory, copied by cph_init_system) */
+
+/* A titratable site ("Constant pH and Redox Potential MD" section): a set of
+ * atoms whose charges take one of n_states discrete sets. */
+typedef struct cph_site_desc {
+    int kind;             /* CPH_SITE_PH or CPH_SITE_REDOX */
+    int n_atoms;          /* atoms whose charge changes, 1..64 */
+    const int* atoms;     /* [n_atoms] atom indices in the system */
+    int n_states;         /* 2..8 */
+    const double* q;      /* [n_states * n_atoms] charges, state-major */
+    const int* n_prot;    /* [n_states] protons of each state (pH sites) */
+    const int* n_elec;    /* [n_states] electrons of each state (redox sites) */
+    double ref;           /* pKa_ref (pH site) or E0_ref in volts (redox site) */
+    int init_state;       /* starting state */
+} cph_site_desc;
+
+/* One molecular system.  Sites must not share atoms.  Exclusions from
+ * Coulomb and LJ are every pair one or two bonds apart (1-2 and 1-3 in the
+ * bond graph) plus the optional extra list; GB runs over all pairs. */
+typedef struct cph_system_desc {
+    int n_atoms;                    /* 1..65536 */
+    const double* x;                /* [3N] starting positions, xyz interleaved */
+    const double* v;                /* [3N] starting velocities (A/ps) or NULL for zero */
+    const double* mass;             /* [N] amu, > 0 */
+    const double* q;                /* [N] charges; site atoms are overwritten by the
+                                       charges of the site's init_state */
+    const double* rho;              /* [N] intrinsic Born radii (A), > gb.offset */
+    const double* screen;           /* [N] HCT screening factors */
+    const double* sigma;            /* [N] LJ sigma (A); Lorentz-Berthelot mixing */
+    const double* eps;              /* [N] LJ epsilon (kcal/mol) */
+    int n_bonds;
+    const int* bonds;               /* [2 * n_bonds] atom pairs */
+    const double* bond_k;           /* [n_bonds] E = k (r - r0)^2 */
+    const double* bond_r0;          /* [n_bonds] */
+    int n_angles;
+    const int* angles;              /* [3 * n_angles] i-j-k, j the vertex */
+    const double* angle_k;          /* [n_angles] E = k (theta - theta0)^2 */
+    const double* angle_t0;         /* [n_angles] radians */
+    int n_excl;
+    const int* excl;                /* [2 * n_excl] extra excluded pairs, or NULL */
+    int n_sites;
+    const cph_site_desc* sites;     /* [n_sites]; swept in index order within a kind */
+} cph_system_desc;
+
+/* The E x pH x T grid ("AMBER's multidimensional REMD module"). */
+typedef struct cph_grid_desc {
+    int nE, npH, nT;                /* each >= 1 */
+    const double* E;                /* [nE] volts, ascending */
+    const double* pH;               /* [npH] ascending */
+    const double* T;                /* [nT] kelvin, ascending */
+    const int* system_of_slot;      /* [nE*npH*nT] system index of the walker starting there */
+    int n_order;                    /* 1..3 */
+    int order[3];                   /* exchange dimension order, CPH_DIM_* */
+} cph_grid_desc;
+
+/* OBC generalized-Born parameters ("igb=2": offset 0.09 A, alpha 0.8,
+ * beta 0.0, gamma 2.909125; eps_in 1, eps_out 78.5). */
+typedef struct cph_gb_params {
+    double eps_in, eps_out;
+    double offset;                  /* rho_tilde = rho - offset */
+    double alpha, beta, gamma;      /* tanh(alpha psi - beta psi^2 + gamma psi^3) */
+} cph_gb_params;
+
+typedef struct cph_run_params {
+    cph_gb_params gb;
+    double dt;                      /* ps, e.g. 0.002 */
+    double gamma_ln;                /* Langevin friction, ps^-1, e.g. 10 */
+    int precision;                  /* CPH_PREC_FP64 or CPH_PREC_FP32 */
+    int mc_ph_every;                /* protonation sweep interval in steps (0 = never) */
+    int mc_redox_every;             /* redox sweep interval in steps (0 = never) */
+    int exchange_every;             /* steps between exchange attempts (0 = never) */
+} cph_run_params;
+
+typedef struct cph_engine cph_engine; /* opaque */
+
+/* One Monte-Carlo decision of the last cph_mc_titrate / cph_run MC event. */
+typedef struct cph_mc_record {
+    int walker, site, from, to, accepted, pad_;
+    double dU;      /* U_el(to) - U_el(from), kcal/mol */
+    double x;       /* -(G(to) - G(from)) / kT */
+    double lnu;     /* ln u of the acceptance draw; accepted = lnu < x */
+} cph_mc_record;
+
+/* One pair of the last exchange attempt. */
+typedef struct cph_exchange_record {
+    int dim, slot_lo, slot_hi, walker_lo, walker_hi, accepted;
+    double x;       /* exponent of eq (3), (4) or (5) */
+    double lnu;
+} cph_exchange_record;
+
+/* ---- engine lifetime */
+
+/* Validate the descriptors, compute each site state's isolated reference
+ * energy U_ref (U_el of the site's atoms alone in the starting geometry),
+ * allocate device state for every walker of the grid and upload it.
+ * Random numbers come from Philox4x32-10 keyed by `seed`.  On failure *out is
+ * NULL and cph_last_error(NULL) describes why. */
+int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* grid,
+                    const cph_run_params* p, uint64_t seed, cph_engine** out);
+void cph_destroy(cph_engine* e);
+/* Message of the last failure on `e`, or of the calling thread's last failed
+ * cph_init_system / ABI-level call when e is NULL.  Never NULL. */
+const char* cph_last_error(const cph_engine* e);
+
+int cph_num_walkers(const cph_engine* e);
+int cph_total_atoms(const cph_engine* e);
+int cph_walker_offsets(const cph_engine* e, int* offsets /* host [W+1] */);
+int cph_site_offsets(const cph_engine* e, int* offsets /* host [W+1] into site-state arrays */);
+
+/* ---- the hot path */
+
+/* Launch shape of the hot path: CPH_LAUNCH_BATCHED (default) runs every
+ * walker of the grid in one launch per pass; CPH_LAUNCH_PER_REPLICA issues the
+ * same kernels once per walker (the one-replica-per-process shape of the
+ * paper's runs), for comparison.  Results are bitwise identical. */
+#define CPH_LAUNCH_BATCHED 0
+#define CPH_LAUNCH_PER_REPLICA 1
+int cph_set_launch_mode(cph_engine* e, int mode);
+
+/* Forces and energies of every walker at the current state (Born radii,
+ * GB + Coulomb + LJ pair pass, chain rule through the radii, bonded terms,
+ * energy totals); nothing moves. */
+int cph_evaluate(cph_engine* e, void* stream);
+/* n_steps of plain MD (no MC, no exchange) for every walker; the step counter
+ * advances by n_steps. */
+int cph_step_replicas(cph_engine* e, int64_t n_steps, void* stream);
+/* One Monte-Carlo sweep at the current positions: kind = CPH_MC_PH, REDOX or
+ * BOTH (protonation first).  Each sweep visits every site of that kind once,
+ * in index order, proposing a uniformly chosen other state and accepting with
+ * the Metropolis rule on G(s) = U_el(s) - U_ref(s) + kT ln10 N_H(s)(pH - pKa_ref)
+ * + F N_e(s)(E - E0_ref) at fixed Born radii. */
+int cph_mc_titrate(cph_engine* e, int kind, void* stream);
+/* One exchange attempt along `dim` (CPH_DIM_E/PH/T, or CPH_DIM_NEXT for the
+ * next dimension of the order).  Neighbours (m, m+1) of the attempt's parity
+ * (alternating per dimension) within each line of the other two conditions,
+ * walkers of the same system only; accept iff ln u < x with x from eq (3),
+ * (4) or (5); T swaps scale velocities by sqrt(T_new/T_old).  A T attempt
+ * evaluates the energies at the current state first. */
+int cph_attempt_exchanges(cph_engine* e, int dim, void* stream);
+/* n_steps of the full schedule.  Step t: Born radii at x_t; protonation sweep
+ * if t > 0 and t % mc_ph_every == 0; redox sweep if t > 0 and
+ * t % mc_redox_every == 0; pair pass and bonded terms; exchange along the next
+ * dimension if t > 0 and t % exchange_every == 0; Langevin step to x_{t+1}.
+ * Whole periods of the schedule replay a captured CUDA graph. */
+int cph_run(cph_engine* e, int64_t n_steps, void* stream);
+
+/* Diagnostic timing of the three pair passes at the current state, with CUDA
+ * events recorded on `stream` around each launch (batched or per-replica, per
+ * the launch mode): ms[0] Born radii, ms[1] GB + Coulomb + LJ, ms[2] chain
+ * rule + bonded terms, each the mean over `reps` launches.  The passes only
+ * rewrite derived per-atom quantities (radii, forces); positions, velocities,
+ * charges and site states are unchanged.  Synchronises `stream`. */
+int cph_time_passes(cph_engine* e, int reps, double* ms /* host [3] */, void* stream);
+
+/* ---- getters and setters (host buffers; getters synchronise `stream`) */
+int cph_get_energies(cph_engine* e, double* out /* [W * CPH_NTERMS] */, void* stream);
+int cph_get_forces(cph_engine* e, double* out /* [total_atoms * 3] */, void* stream);
+int cph_get_born_radii(cph_engine* e, double* out /* [total_atoms] */, void* stream);
+int cph_get_positions(cph_engine* e, double* out /* [total_atoms * 3] */, void* stream);
+int cph_set_positions(cph_engine* e, const double* in, void* stream);
+int cph_get_velocities(cph_engine* e, double* out, void* stream);
+int cph_set_velocities(cph_engine* e, const double* in, void* stream);
+int cph_get_charges(cph_engine* e, double* out /* [total_atoms] */, void* stream);
+int cph_get_site_states(cph_engine* e, int* out /* [site_offsets[W]] */, void* stream);
+int cph_set_site_states(cph_engine* e, const int* in, void* stream); /* also resets charges */
+int cph_get_counts(cph_engine* e, int* n_prot, int* n_elec /* [W] each */, void* stream);
+int cph_get_condition_map(cph_engine* e, int* slot_of_walker /* [W] */, void* stream);
+int cph_set_condition_map(cph_engine* e, const int* slot_of_walker, void* stream);
+/* [0..5]: exchange attempts / accepted pairs along E, pH, T (pairs tried and
+ * pairs swapped); [6..9]: MC proposals / acceptances for pH, redox sites. */
+int cph_get_accept_stats(cph_engine* e, int64_t* out /* [10] */, void* stream);
+int cph_get_reference_energies(cph_engine* e, double* out /* [sum over systems of
+                               sum over sites of n_states] */);
+/* Records of the last MC event: one per (walker, visited site), walker-major. */
+int cph_get_mc_records(cph_engine* e, cph_mc_record* out, int max, int* n_out, void* stream);
+int cph_get_exchange_records(cph_engine* e, cph_exchange_record* out, int max, int* n_out,
+                             void* stream);
+int64_t cph_get_step(const cph_engine* e);
+int cph_set_step(cph_engine* e, int64_t step);
+/* Synchronise `stream` and report device-side status: CPH_OK, CPH_E_NONFINITE
+ * (a walker produced a non-finite energy or position) or a CUDA error. */
+int cph_status(cph_engine* e, void* stream);
+/* Energies returned by cph_get_energies are those of the last evaluation that
+ * computed them: cph_evaluate, cph_attempt_exchanges, or a cph_run step that
+ * attempted an exchange. */
+
+/* ---- differentiable GB energy (device buffers, caller-owned) */
+
+/* E_GB of n_rep independent configurations of one n-atom system (no Coulomb,
+ * no LJ; OBC radii as above, all pairs including self terms).
+ *   x      device float [n_rep * n * 3]
+ *   q      device float [n_rep * n]
+ *   rho    device float [n_rep * n] intrinsic radii (> offset)
+ *   screen device float [n] screening factors (shared by all replicas)
+ *   E      device double [n_rep], written
+ * FP32 pair arithmetic, int64 fixed-point accumulation.  Needs
+ * cph_gb_workspace_bytes(n_rep, n) bytes of device workspace (caller-owned,
+ * 256-byte aligned); the library allocates nothing. */
+size_t cph_gb_workspace_bytes(int n_rep, int n);
+int cph_gb_energy(int n_rep, int n, const float* x, const float* q, const float* rho,
+                  const float* screen, const cph_gb_params* gb, double* E,
+                  void* workspace, size_t workspace_bytes, void* stream);
+/* Gradient of sum_r dE[r] * E_GB[r] with respect to x, q and rho (the
+ * adjoint of cph_gb_energy).  Born radii are recomputed, not stored.
+ *   dE     device double [n_rep] upstream gradient
+ *   dx     device float [n_rep * n * 3], dq and drho device float [n_rep * n]:
+ *          written (not accumulated). */
+int cph_gb_energy_backward(int n_rep, int n, const float* x, const float* q,
+                           const float* rho, const float* screen, const cph_gb_params* gb,
+                           const double* dE, float* dx, float* dq, float* drho,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPHREMD_H */

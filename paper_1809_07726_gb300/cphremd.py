@@ -1,0 +1,447 @@
+"""Thin Python binding of libcphremd.so (the C ABI in include/cphremd.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Function names follow the C calls without their ``cph_``
+prefix.  The library must have been built (``paper_1809_07726_gb300.build``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+# ---- constants mirrored from cphremd.h
+OK, E_INVALID, E_CUDA, E_OOM, E_NONFINITE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6
+SITE_PH, SITE_REDOX = 0, 1
+DIM_E, DIM_PH, DIM_T, DIM_NEXT = 0, 1, 2, -1
+MC_PH, MC_REDOX, MC_BOTH = 1, 2, 3
+PREC_FP64, PREC_FP32 = 0, 1
+LAUNCH_BATCHED, LAUNCH_PER_REPLICA = 0, 1
+NTERMS = 6
+TERMS = ("gb", "coul", "lj", "bond", "angle", "total")
+DIM_NAMES = {"E": DIM_E, "pH": DIM_PH, "T": DIM_T}
+
+
+class CphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cph error {code}: {msg}")
+        self.code = code
+
+
+class SiteDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_atoms", C.c_int), ("atoms", C.c_void_p),
+                ("n_states", C.c_int), ("q", C.c_void_p), ("n_prot", C.c_void_p),
+                ("n_elec", C.c_void_p), ("ref", C.c_double), ("init_state", C.c_int)]
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("x", C.c_void_p), ("v", C.c_void_p),
+                ("mass", C.c_void_p), ("q", C.c_void_p), ("rho", C.c_void_p),
+                ("screen", C.c_void_p), ("sigma", C.c_void_p), ("eps", C.c_void_p),
+                ("n_bonds", C.c_int), ("bonds", C.c_void_p), ("bond_k", C.c_void_p),
+                ("bond_r0", C.c_void_p), ("n_angles", C.c_int), ("angles", C.c_void_p),
+                ("angle_k", C.c_void_p), ("angle_t0", C.c_void_p), ("n_excl", C.c_int),
+                ("excl", C.c_void_p), ("n_sites", C.c_int), ("sites", C.c_void_p)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nE", C.c_int), ("npH", C.c_int), ("nT", C.c_int), ("E", C.c_void_p),
+                ("pH", C.c_void_p), ("T", C.c_void_p), ("system_of_slot", C.c_void_p),
+                ("n_order", C.c_int), ("order", C.c_int * 3)]
+
+
+class GBParams(C.Structure):
+    _fields_ = [("eps_in", C.c_double), ("eps_out", C.c_double), ("offset", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double)]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("gb", GBParams), ("dt", C.c_double), ("gamma_ln", C.c_double),
+                ("precision", C.c_int), ("mc_ph_every", C.c_int), ("mc_redox_every", C.c_int),
+                ("exchange_every", C.c_int)]
+
+
+class MCRecord(C.Structure):
+    _fields_ = [("walker", C.c_int), ("site", C.c_int), ("frm", C.c_int), ("to", C.c_int),
+                ("accepted", C.c_int), ("pad_", C.c_int), ("dU", C.c_double),
+                ("x", C.c_double), ("lnu", C.c_double)]
+
+
+class ExRecord(C.Structure):
+    _fields_ = [("dim", C.c_int), ("slot_lo", C.c_int), ("slot_hi", C.c_int),
+                ("walker_lo", C.c_int), ("walker_hi", C.c_int), ("accepted", C.c_int),
+                ("x", C.c_double), ("lnu", C.c_double)]
+
+
+def default_gb() -> GBParams:
+    """OBC "igb=2": offset 0.09, (alpha, beta, gamma) = (0.8, 0, 2.909125), eps 1 / 78.5."""
+    return GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125)
+
+
+_lib = None
+
+
+def lib():
+    """Load libcphremd.so; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: run paper_1809_07726_gb300.build.build() first")
+        L = C.CDLL(LIB)
+        vp, i, i64, d = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "cph_init_system": ([vp, i, C.POINTER(GridDesc), C.POINTER(RunParams), C.c_uint64,
+                                 C.POINTER(vp)], i),
+            "cph_destroy": ([vp], None),
+            "cph_last_error": ([vp], C.c_char_p),
+            "cph_num_walkers": ([vp], i),
+            "cph_total_atoms": ([vp], i),
+            "cph_walker_offsets": ([vp, vp], i),
+            "cph_site_offsets": ([vp, vp], i),
+            "cph_set_launch_mode": ([vp, i], i),
+            "cph_evaluate": ([vp, vp], i),
+            "cph_step_replicas": ([vp, i64, vp], i),
+            "cph_mc_titrate": ([vp, i, vp], i),
+            "cph_attempt_exchanges": ([vp, i, vp], i),
+            "cph_run": ([vp, i64, vp], i),
+            "cph_get_energies": ([vp, vp, vp], i),
+            "cph_get_forces": ([vp, vp, vp], i),
+            "cph_get_born_radii": ([vp, vp, vp], i),
+            "cph_get_positions": ([vp, vp, vp], i),
+            "cph_set_positions": ([vp, vp, vp], i),
+            "cph_get_velocities": ([vp, vp, vp], i),
+            "cph_set_velocities": ([vp, vp, vp], i),
+            "cph_get_charges": ([vp, vp, vp], i),
+            "cph_get_site_states": ([vp, vp, vp], i),
+            "cph_set_site_states": ([vp, vp, vp], i),
+            "cph_get_counts": ([vp, vp, vp, vp], i),
+            "cph_get_condition_map": ([vp, vp, vp], i),
+            "cph_set_condition_map": ([vp, vp, vp], i),
+            "cph_get_accept_stats": ([vp, vp, vp], i),
+            "cph_get_reference_energies": ([vp, vp], i),
+            "cph_get_mc_records": ([vp, vp, i, vp, vp], i),
+            "cph_get_exchange_records": ([vp, vp, i, vp, vp], i),
+            "cph_get_step": ([vp], i64),
+            "cph_set_step": ([vp, i64], i),
+            "cph_status": ([vp, vp], i),
+            "cph_time_passes": ([vp, i, vp, vp], i),
+            "cph_gb_workspace_bytes": ([i, i], C.c_size_t),
+            "cph_gb_energy": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, C.c_size_t,
+                               vp], i),
+            "cph_gb_energy_backward": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, vp,
+                                        vp, vp, C.c_size_t, vp], i),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc, eng=None):
+    if rc != OK:
+        msg = lib().cph_last_error(eng)
+        raise CphError(rc, msg.decode() if msg else "")
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, np.int32)
+
+
+class _Keep:
+    """Holds the numpy buffers a descriptor points into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def __call__(self, a):
+        self.refs.append(a)
+        return _p(a)
+
+
+def system_desc(sysd, keep: _Keep, velocities=None) -> SystemDesc:
+    """cph_system_desc for a ``synth.System``-like object."""
+    n = sysd.n
+    sites = (SiteDesc * max(1, len(sysd.sites)))()
+    for k, st in enumerate(sysd.sites):
+        sites[k] = SiteDesc(SITE_PH if st.kind == "ph" else SITE_REDOX, len(st.atoms),
+                            keep(_i32(st.atoms)), st.q.shape[0], keep(_f64(st.q)),
+                            keep(_i32(st.n_prot)), keep(_i32(st.n_elec)), float(st.ref),
+                            int(st.init_state))
+    keep.refs.append(sites)
+    d = SystemDesc()
+    d.n_atoms = n
+    d.x = keep(_f64(sysd.x).reshape(-1))
+    d.v = keep(_f64(velocities).reshape(-1)) if velocities is not None else None
+    d.mass, d.q, d.rho, d.screen, d.sigma, d.eps = (keep(_f64(a)) for a in (
+        sysd.mass, sysd.q, sysd.rho, sysd.screen, sysd.sigma, sysd.eps))
+    d.n_bonds = len(sysd.bonds)
+    d.bonds = keep(_i32(sysd.bonds).reshape(-1))
+    d.bond_k = keep(_f64(sysd.bond_k))
+    d.bond_r0 = keep(_f64(sysd.bond_r0))
+    d.n_angles = len(sysd.angles)
+    d.angles = keep(_i32(sysd.angles).reshape(-1))
+    d.angle_k = keep(_f64(sysd.angle_k))
+    d.angle_t0 = keep(_f64(sysd.angle_t0))
+    d.n_excl = 0
+    d.excl = None
+    d.n_sites = len(sysd.sites)
+    d.sites = C.cast(sites, C.c_void_p) if sysd.sites else None
+    return d
+
+
+class Engine:
+    """Owns a cph_engine*.  Methods mirror the C calls."""
+
+    def __init__(self, ptr, systems, grid):
+        self.ptr = ptr
+        self.systems = systems
+        self.grid = grid
+        L = lib()
+        self.W = L.cph_num_walkers(ptr)
+        self.total_atoms = L.cph_total_atoms(ptr)
+        self.offsets = np.zeros(self.W + 1, np.int32)
+        _check(L.cph_walker_offsets(ptr, _p(self.offsets)))
+        self.site_offsets = np.zeros(self.W + 1, np.int32)
+        _check(L.cph_site_offsets(ptr, _p(self.site_offsets)))
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().cph_destroy(self.ptr)
+            self.ptr = None
+
+    close = __del__
+
+    def _c(self, rc):
+        _check(rc, self.ptr)
+
+    # ---- hot path
+    def set_launch_mode(self, mode):
+        self._c(lib().cph_set_launch_mode(self.ptr, mode))
+
+    def evaluate(self, stream=None):
+        self._c(lib().cph_evaluate(self.ptr, _stream(stream)))
+
+    def step_replicas(self, n_steps, stream=None):
+        self._c(lib().cph_step_replicas(self.ptr, int(n_steps), _stream(stream)))
+
+    def mc_titrate(self, kind=MC_BOTH, stream=None):
+        self._c(lib().cph_mc_titrate(self.ptr, kind, _stream(stream)))
+
+    def attempt_exchanges(self, dim=DIM_NEXT, stream=None):
+        self._c(lib().cph_attempt_exchanges(self.ptr, dim, _stream(stream)))
+
+    def run(self, n_steps, stream=None):
+        self._c(lib().cph_run(self.ptr, int(n_steps), _stream(stream)))
+
+    # ---- getters / setters
+    def _get(self, fn, shape, dtype=np.float64, stream=None):
+        out = np.zeros(shape, dtype)
+        self._c(fn(self.ptr, _p(out), _stream(stream)))
+        return out
+
+    def energies(self, stream=None):
+        return self._get(lib().cph_get_energies, (self.W, NTERMS), stream=stream)
+
+    def forces(self, stream=None):
+        return self._get(lib().cph_get_forces, (self.total_atoms, 3), stream=stream)
+
+    def born_radii(self, stream=None):
+        return self._get(lib().cph_get_born_radii, (self.total_atoms,), stream=stream)
+
+    def positions(self, stream=None):
+        return self._get(lib().cph_get_positions, (self.total_atoms, 3), stream=stream)
+
+    def velocities(self, stream=None):
+        return self._get(lib().cph_get_velocities, (self.total_atoms, 3), stream=stream)
+
+    def charges(self, stream=None):
+        return self._get(lib().cph_get_charges, (self.total_atoms,), stream=stream)
+
+    def site_states(self, stream=None):
+        return self._get(lib().cph_get_site_states, (int(self.site_offsets[-1]),), np.int32,
+                         stream=stream)
+
+    def condition_map(self, stream=None):
+        return self._get(lib().cph_get_condition_map, (self.W,), np.int32, stream=stream)
+
+    def accept_stats(self, stream=None):
+        return self._get(lib().cph_get_accept_stats, (10,), np.int64, stream=stream)
+
+    def set_positions(self, x, stream=None):
+        self._c(lib().cph_set_positions(self.ptr, _p(_f64(x).reshape(-1)), _stream(stream)))
+
+    def set_velocities(self, v, stream=None):
+        self._c(lib().cph_set_velocities(self.ptr, _p(_f64(v).reshape(-1)), _stream(stream)))
+
+    def set_site_states(self, s, stream=None):
+        self._c(lib().cph_set_site_states(self.ptr, _p(_i32(s)), _stream(stream)))
+
+    def set_condition_map(self, m, stream=None):
+        self._c(lib().cph_set_condition_map(self.ptr, _p(_i32(m)), _stream(stream)))
+
+    def counts(self, stream=None):
+        npr = np.zeros(self.W, np.int32)
+        nel = np.zeros(self.W, np.int32)
+        self._c(lib().cph_get_counts(self.ptr, _p(npr), _p(nel), _stream(stream)))
+        return npr, nel
+
+    def reference_energies(self):
+        n = sum(sum(len(st.q) for st in s.sites) for s in self.systems)
+        out = np.zeros(max(1, n))
+        self._c(lib().cph_get_reference_energies(self.ptr, _p(out)))
+        return out[:n]
+
+    def mc_records(self, stream=None):
+        n = int(self.site_offsets[-1])
+        buf = (MCRecord * max(1, n))()
+        got = C.c_int(0)
+        self._c(lib().cph_get_mc_records(self.ptr, C.cast(buf, C.c_void_p), n, C.byref(got),
+                                         _stream(stream)))
+        return [buf[i] for i in range(got.value)]
+
+    def exchange_records(self, stream=None):
+        buf = (ExRecord * max(1, self.W))()
+        got = C.c_int(0)
+        self._c(lib().cph_get_exchange_records(self.ptr, C.cast(buf, C.c_void_p), self.W,
+                                               C.byref(got), _stream(stream)))
+        return [buf[i] for i in range(got.value)]
+
+    def get_step(self):
+        return int(lib().cph_get_step(self.ptr))
+
+    def set_step(self, t):
+        self._c(lib().cph_set_step(self.ptr, int(t)))
+
+    def time_passes(self, reps=3, stream=None):
+        """Mean CUDA-event durations (ms) of the Born, GB/Coulomb/LJ and chain passes."""
+        ms = np.zeros(3)
+        self._c(lib().cph_time_passes(self.ptr, int(reps), _p(ms), _stream(stream)))
+        return ms
+
+    def status(self, stream=None):
+        self._c(lib().cph_status(self.ptr, _stream(stream)))
+
+    def walker_slice(self, w):
+        return slice(int(self.offsets[w]), int(self.offsets[w + 1]))
+
+
+def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.0,
+                mc_ph_every=10, mc_redox_every=10, exchange_every=100, gb=None,
+                velocities=None) -> Engine:
+    """cph_init_system for a list of ``synth.System`` and a ``synth.Grid``."""
+    keep = _Keep()
+    descs = (SystemDesc * len(systems))()
+    for k, s in enumerate(systems):
+        descs[k] = system_desc(s, keep, None if velocities is None else velocities[k])
+    g = GridDesc()
+    g.nE, g.npH, g.nT = len(grid.E), len(grid.pH), len(grid.T)
+    g.E, g.pH, g.T = keep(_f64(grid.E)), keep(_f64(grid.pH)), keep(_f64(grid.T))
+    g.system_of_slot = keep(_i32(grid.system_of_slot))
+    g.n_order = len(grid.order)
+    for k, name in enumerate(grid.order):
+        g.order[k] = DIM_NAMES[name]
+    p = RunParams(gb or default_gb(), dt, gamma_ln, precision, mc_ph_every, mc_redox_every,
+                  exchange_every)
+    out = C.c_void_p()
+    rc = lib().cph_init_system(C.cast(descs, C.c_void_p), len(systems), C.byref(g), C.byref(p),
+                               C.c_uint64(seed), C.byref(out))
+    _check(rc, None)
+    return Engine(out, systems, grid)
+
+
+# ---------------------------------------------------- differentiable GB energy
+
+def gb_workspace_bytes(n_rep, n):
+    return int(lib().cph_gb_workspace_bytes(n_rep, n))
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def gb_energy(x, q, rho, screen, gb=None, workspace=None, stream=None):
+    """E_GB [n_rep] (float64 CUDA tensor) for x [n_rep, n, 3], q and rho [n_rep, n]
+    (float32 CUDA tensors) and screen [n]."""
+    import torch
+    n_rep, n = q.shape
+    x, q, rho, screen = (t.contiguous() for t in (x, q, rho, screen))
+    E = torch.empty(n_rep, dtype=torch.float64, device=q.device)
+    ws = workspace if workspace is not None else _workspace(n_rep, n, q.device)
+    g = gb or default_gb()
+    _check(lib().cph_gb_energy(n_rep, n, _dptr(x), _dptr(q), _dptr(rho), _dptr(screen),
+                               C.byref(g), _dptr(E), _dptr(ws), ws.numel(), _stream(stream)))
+    return E
+
+
+def gb_energy_backward(x, q, rho, screen, dE, gb=None, workspace=None, stream=None):
+    import torch
+    n_rep, n = q.shape
+    x, q, rho, screen = (t.contiguous() for t in (x, q, rho, screen))
+    dE = dE.to(torch.float64).contiguous()
+    dx = torch.empty_like(x)
+    dq = torch.empty_like(q)
+    drho = torch.empty_like(rho)
+    ws = workspace if workspace is not None else _workspace(n_rep, n, q.device)
+    g = gb or default_gb()
+    _check(lib().cph_gb_energy_backward(n_rep, n, _dptr(x), _dptr(q), _dptr(rho), _dptr(screen),
+                                        C.byref(g), _dptr(dE), _dptr(dx), _dptr(dq),
+                                        _dptr(drho), _dptr(ws), ws.numel(), _stream(stream)))
+    return dx, dq, drho
+
+
+def _workspace(n_rep, n, device):
+    import torch
+    nb = gb_workspace_bytes(n_rep, n)
+    return torch.empty(nb, dtype=torch.uint8, device=device)  # caching allocator: 512-B aligned
+
+
+def _gb_function():
+    import torch
+
+    class GBEnergy(torch.autograd.Function):
+        """E_GB with the hand-written adjoint kernel as its backward."""
+
+        @staticmethod
+        def forward(ctx, x, q, rho, screen):
+            ctx.save_for_backward(x, q, rho, screen)
+            return gb_energy(x, q, rho, screen)
+
+        @staticmethod
+        def backward(ctx, gE):
+            x, q, rho, screen = ctx.saved_tensors
+            dx, dq, drho = gb_energy_backward(x, q, rho, screen, gE)
+            return dx, dq, drho, None
+
+    return GBEnergy
+
+
+def __getattr__(name):
+    if name == "GBEnergy":
+        return _gb_function()
+    raise AttributeError(name)

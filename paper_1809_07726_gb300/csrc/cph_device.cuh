@@ -1,0 +1,287 @@
+// Device-side building blocks of the engine: constants, Philox4x32-10,
+// fixed-point helpers and the per-pair arithmetic of the OBC generalized-Born
+// model ("igb=2", named in the paper's Implicit Solvent Calculations
+// section) with Hawkins-Cramer-Truhlar pairwise descreening.
+//
+// Pair quantities for atom i and a partner j at distance r:
+//   H(r, rt, s)  descreening integral of sphere s (partner's scaled radius)
+//                outside the ball rt (this atom's offset radius):
+//                0 if rt >= r + s; else with L = max(rt, |r - s|), U = r + s
+//                H = 1/L - 1/U + (r/4)(1/U^2 - 1/L^2) + ln(L/U)/(2r)
+//                    + (s^2/(4r))(1/L^2 - 1/U^2)  [+ 2(1/rt - 1/L) if rt < s - r]
+//   When the spheres are disjoint (L = r - s) H depends on r and x = s/r only:
+//   H = (1/r) (x/(1 - x^2) - atanh x) = (1/r) sum_{k>=1} 2k/(2k+1) x^(2k+1).
+//   The FP32 path evaluates that series (Horner in x^2, nine terms) whenever
+//   x <= 0.35: it needs no transcendental, and it avoids the cancellation of
+//   the closed form (whose terms are O(x) while H is O(x^3)).  Nine terms
+//   leave a relative truncation error below 1e-8 at x = 0.35.
+//   Derivatives: in every branch the L- and U-dependence of H cancels (the
+//   integrand vanishes on the moving boundary), so
+//     dH/dr  = -(1/4)(1/L^2 - 1/U^2)(1 + s^2/r^2) - ln(L/U)/(2 r^2)
+//            = -(1/r^2) sum 2k(2k+2)/(2k+1) x^(2k+1)      (disjoint)
+//     dH/ds  = (s/(2r))(1/L^2 - 1/U^2) = (1/r^2) sum 2k x^(2k)
+//     dH/drt = ((L - r)^2 - s^2)/(2 r L^3) when L = rt, -2/rt^2 when the ball
+//              lies inside sphere s, else 0.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cph {
+
+// Physical constants (kcal/mol, A, e, amu, ps, K, V).
+constexpr double kCoulomb = 332.0522173;   // kcal A / (mol e^2)
+constexpr double kBoltzmann = 0.0019872041; // kcal / (mol K)
+constexpr double kFaraday = 23.0605;       // kcal / (mol V)
+constexpr double kAccel = 418.4;           // (kcal/mol/A)/amu -> A/ps^2
+constexpr double kLn10 = 2.302585092994046;
+
+// Fixed-point scales of the int64 accumulators.
+constexpr double kScaleE = 4294967296.0;   // energies and forces: 2^32
+constexpr double kScaleH = 1099511627776.0; // descreening sums: 2^40
+
+// Random-number purposes (last counter word).
+constexpr uint32_t kRngLangevin = 1, kRngMcPh = 2, kRngMcRedox = 3, kRngExchange = 4;
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32 with ten rounds (Salmon, Moraes, Dror and Shaw, SC'11).  A round
+// multiplies counter words 0 and 2 by 0xD2511F53 and 0xCD9E8D57, XORs the
+// high product words with counter words 1 and 3 and the key, and permutes;
+// between rounds the key advances by the Weyl increments 0x9E3779B9 and
+// 0xBB67AE85.
+struct U4 {
+    uint32_t a, b, c, d;
+};
+
+__host__ __device__ inline U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * ctr.a;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * ctr.c;
+        U4 n;
+        n.a = (uint32_t)(p1 >> 32) ^ ctr.b ^ k0;
+        n.b = (uint32_t)p1;
+        n.c = (uint32_t)(p0 >> 32) ^ ctr.d ^ k1;
+        n.d = (uint32_t)p0;
+        ctr = n;
+    }
+    return ctr;
+}
+
+// Counter (index, stream, step low word, purpose | step high bits << 8),
+// key (seed low word, seed high word).
+__host__ __device__ inline U4 draw(uint64_t seed, uint32_t index, uint32_t stream,
+                                   uint64_t step, uint32_t purpose) {
+    U4 c{index, stream, (uint32_t)step, (purpose & 0xffu) | ((uint32_t)(step >> 32) << 8)};
+    return philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// u in (0, 1): u32 * 2^-32 + 2^-33, exact in FP64.
+__host__ __device__ inline double unit_open(uint32_t u) {
+    return (double)u * 2.3283064365386963e-10 + 1.1641532182693481e-10;
+}
+
+// --------------------------------------------------------- fixed point
+__device__ inline long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
+__device__ inline long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
+
+// ------------------------------------------------------------- HCT, FP32
+constexpr float kHctXmax = 0.35f;
+
+// sum_{k=1..9} 2k/(2k+1) y^(k-1)
+__device__ __forceinline__ float hct_series_h(float y) {
+    float p = 18.f / 19.f;
+    p = fmaf(p, y, 16.f / 17.f);
+    p = fmaf(p, y, 14.f / 15.f);
+    p = fmaf(p, y, 12.f / 13.f);
+    p = fmaf(p, y, 10.f / 11.f);
+    p = fmaf(p, y, 8.f / 9.f);
+    p = fmaf(p, y, 6.f / 7.f);
+    p = fmaf(p, y, 4.f / 5.f);
+    p = fmaf(p, y, 2.f / 3.f);
+    return p;
+}
+
+// sum_{k=1..9} 2k(2k+2)/(2k+1) y^(k-1)
+__device__ __forceinline__ float hct_series_dr(float y) {
+    float p = 360.f / 19.f;
+    p = fmaf(p, y, 288.f / 17.f);
+    p = fmaf(p, y, 224.f / 15.f);
+    p = fmaf(p, y, 168.f / 13.f);
+    p = fmaf(p, y, 120.f / 11.f);
+    p = fmaf(p, y, 80.f / 9.f);
+    p = fmaf(p, y, 48.f / 7.f);
+    p = fmaf(p, y, 24.f / 5.f);
+    p = fmaf(p, y, 8.f / 3.f);
+    return p;
+}
+
+// sum_{k=1..9} 2k y^(k-1)
+__device__ __forceinline__ float hct_series_ds(float y) {
+    float p = 18.f;
+    p = fmaf(p, y, 16.f);
+    p = fmaf(p, y, 14.f);
+    p = fmaf(p, y, 12.f);
+    p = fmaf(p, y, 10.f);
+    p = fmaf(p, y, 8.f);
+    p = fmaf(p, y, 6.f);
+    p = fmaf(p, y, 4.f);
+    p = fmaf(p, y, 2.f);
+    return p;
+}
+
+__device__ __forceinline__ bool hct_far(float r, float rt, float s) {
+    return (r - s >= rt) && (s <= kHctXmax * r);
+}
+
+struct HctClosed {
+    float iL, iU, lg;
+};
+
+__device__ __forceinline__ HctClosed hct_closed(float r, float rt, float s) {
+    float U = r + s;
+    float L = fmaxf(rt, fabsf(r - s));
+    float iLU = __fdividef(1.f, L * U);
+    HctClosed h;
+    h.iL = U * iLU;
+    h.iU = L * iLU;
+    h.lg = __logf(L * h.iU);
+    return h;
+}
+
+__device__ __forceinline__ float hct(float r, float rinv, float rt, float irt, float s) {
+    if (hct_far(r, rt, s)) {
+        float x = s * rinv, y = x * x;
+        return x * y * hct_series_h(y) * rinv;
+    }
+    if (rt >= r + s) return 0.f;
+    HctClosed c = hct_closed(r, rt, s);
+    float h = (c.iL - c.iU) * fmaf((c.iL + c.iU) * 0.25f * rinv, (s - r) * (s + r), 1.f)
+            + 0.5f * rinv * c.lg;
+    if (rt < s - r) h += 2.f * (irt - c.iL);
+    return h;
+}
+
+__device__ __forceinline__ float hct_dr(float r, float rinv, float rt, float s) {
+    float rinv2 = rinv * rinv;
+    if (hct_far(r, rt, s)) {
+        float x = s * rinv, y = x * x;
+        return -x * y * hct_series_dr(y) * rinv2;
+    }
+    if (rt >= r + s) return 0.f;
+    HctClosed c = hct_closed(r, rt, s);
+    return -0.25f * (c.iL - c.iU) * (c.iL + c.iU) * fmaf(s * s, rinv2, 1.f)
+           - 0.5f * c.lg * rinv2;
+}
+
+__device__ __forceinline__ float hct_ds(float r, float rinv, float rt, float s) {
+    if (hct_far(r, rt, s)) {
+        float x = s * rinv, y = x * x;
+        return y * hct_series_ds(y) * rinv * rinv;
+    }
+    if (rt >= r + s) return 0.f;
+    HctClosed c = hct_closed(r, rt, s);
+    return 0.5f * s * rinv * (c.iL - c.iU) * (c.iL + c.iU);
+}
+
+__device__ __forceinline__ float hct_drt(float r, float rt, float irt, float s) {
+    if (hct_far(r, rt, s) || rt >= r + s) return 0.f;
+    if (rt < s - r) return -2.f * irt * irt;
+    if (rt > fabsf(r - s)) {
+        float a = rt - r;
+        return (a * a - s * s) * 0.5f * __fdividef(1.f, r) * irt * irt * irt;
+    }
+    return 0.f;
+}
+
+// ------------------------------------------------------------- HCT, FP64
+// Closed forms throughout (FP64 has no cancellation problem at these sizes).
+__device__ __forceinline__ double hct(double r, double rinv, double rt, double irt, double s) {
+    if (rt >= r + s) return 0.0;
+    double U = r + s;
+    double L = fmax(rt, fabs(r - s));
+    double iL = 1.0 / L, iU = 1.0 / U;
+    double h = (iL - iU) * (1.0 + (iL + iU) * 0.25 * rinv * (s - r) * (s + r))
+             + 0.5 * rinv * log(L * iU);
+    if (rt < s - r) h += 2.0 * (irt - iL);
+    return h;
+}
+
+__device__ __forceinline__ double hct_dr(double r, double rinv, double rt, double s) {
+    if (rt >= r + s) return 0.0;
+    double U = r + s;
+    double L = fmax(rt, fabs(r - s));
+    double iL = 1.0 / L, iU = 1.0 / U;
+    double rinv2 = rinv * rinv;
+    return -0.25 * (iL - iU) * (iL + iU) * (1.0 + s * s * rinv2) - 0.5 * log(L * iU) * rinv2;
+}
+
+__device__ __forceinline__ double hct_ds(double r, double rinv, double rt, double s) {
+    if (rt >= r + s) return 0.0;
+    double U = r + s;
+    double L = fmax(rt, fabs(r - s));
+    double iL = 1.0 / L, iU = 1.0 / U;
+    return 0.5 * s * rinv * (iL - iU) * (iL + iU);
+}
+
+__device__ __forceinline__ double hct_drt(double r, double rt, double irt, double s) {
+    if (rt >= r + s) return 0.0;
+    if (rt < s - r) return -2.0 * irt * irt;
+    if (rt > fabs(r - s)) {
+        double a = rt - r;
+        return (a * a - s * s) * 0.5 / r * irt * irt * irt;
+    }
+    return 0.0;
+}
+
+// ------------------------------------------------- compensated summation
+// Kahan summation of a tile's partial energies: the energy sums cancel
+// strongly (sum |terms| >> |E|), so plain FP32 partials over a 128-atom tile
+// would lose ~1e-6 of |E|.  FP64 needs no compensation.
+template <class Real>
+struct KSum {
+    Real s = 0, c = 0;
+    __device__ __forceinline__ void add(Real v) {
+        const Real y = v - c;
+        const Real t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ Real value() const { return s; }
+};
+
+template <>
+struct KSum<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// ------------------------------------------------------ precision traits
+template <class Real>
+struct Prec;
+
+template <>
+struct Prec<float> {
+    using Acc = long long; // int64 fixed point
+    __device__ static float rsqrt(float x) { return rsqrtf(x); }
+    __device__ static float expm(float x) { return __expf(-x); } // e^-x
+    __device__ static float recip(float x) { return __fdividef(1.f, x); }
+    __device__ static void add(Acc& a, float part, float scale) { a += to_fixed(part, scale); }
+    __device__ static double value(Acc a, double scale) { return (double)a / scale; }
+};
+
+template <>
+struct Prec<double> {
+    using Acc = double;
+    __device__ static double rsqrt(double x) { return 1.0 / sqrt(x); }
+    __device__ static double expm(double x) { return exp(-x); }
+    __device__ static double recip(double x) { return 1.0 / x; }
+    __device__ static void add(Acc& a, double part, double) { a += part; }
+    __device__ static double value(Acc a, double) { return a; }
+};
+
+} // namespace cph

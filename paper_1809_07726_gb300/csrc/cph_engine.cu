@@ -1,0 +1,1314 @@
+// Engine: set-up, Monte-Carlo titration, replica exchange and the C ABI of
+// cphremd.h.  The pair passes and the integrator are in cph_kernels.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cph_kernels.cuh"
+
+namespace cph {
+
+// =====================================================================
+// Monte-Carlo titration sweep (one CTA per walker)
+// =====================================================================
+// For the visited site with charges q -> q + dq (dq only on the site's atoms),
+//   dU = sum_m dq_m (A q)_m + 1/2 sum_{m,n} dq_m dq_n A_mn,
+// A_ij = k/(eps_in r_ij) [not excluded] - tau k / f_ij (i != j), A_ii = -tau k / R_i,
+// i.e. U_el(q + dq) - U_el(q) for U_el = E_coul + E_GB at fixed Born radii.
+// The linear term runs over all N atoms (threads split j); the Coulomb part of
+// excluded pairs is removed afterwards, and the small quadratic term is summed
+// in FP64.
+constexpr int kMcThreads = 256;
+constexpr int kMaxSiteAtoms = 64;
+
+template <class Real>
+__global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, int clear_others,
+                                                   int w_begin) {
+    using Pr = Prec<Real>;
+    using Acc = typename Pr::Acc;
+    const int w = w_begin + blockIdx.x;
+    const int s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
+    const int g0 = V.sys_site_off[s], ns = V.sys_site_off[s + 1] - g0, so = V.w_site_off[w];
+    const uint64_t t = (uint64_t)(*V.step + s_off);
+    const int tid = threadIdx.x;
+    const int slot = V.slot_of[w];
+    const int iE = slot % V.nE, ipH = (slot / V.nE) % V.npH, iT = slot / (V.nE * V.npH);
+    const double E = V.gE[iE], pH = V.gpH[ipH], T = V.gT[iT];
+    const double kT = kBoltzmann * T;
+    const uint32_t purpose = (kind == CPH_SITE_PH) ? kRngMcPh : kRngMcRedox;
+    __shared__ Real mx[kMaxSiteAtoms], my[kMaxSiteAtoms], mz[kMaxSiteAtoms], mR[kMaxSiteAtoms],
+        mdq[kMaxSiteAtoms];
+    __shared__ int mat[kMaxSiteAtoms];
+    __shared__ int sh_a, sh_b, sh_acc;
+    __shared__ double sh_lnu;
+    __shared__ long long redl[kMcThreads / 32];
+    __shared__ double redd[kMcThreads / 32];
+    const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
+    const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
+    for (int k = 0; k < ns; ++k) {
+        const int g = g0 + k;
+        if (V.site_kind[g] != kind) {
+            if (clear_others && tid == 0) V.mc_rec[so + k].walker = -1;
+            continue;
+        }
+        const int nat = V.site_nat[g], nst = V.site_nst[g], ao = V.site_aoff[g];
+        const int qo = V.site_qoff[g], no = V.site_noff[g];
+        if (tid == 0) {
+            const U4 u = draw(V.seed, (uint32_t)k, (uint32_t)w, t, purpose);
+            const int a = V.site_state[so + k];
+            const int jj = (int)floor(unit_open(u.a) * (double)(nst - 1));
+            sh_a = a;
+            sh_b = jj < a ? jj : jj + 1;
+            sh_lnu = log(unit_open(u.b));
+        }
+        __syncthreads();
+        const int a = sh_a, b = sh_b;
+        for (int m = tid; m < nat; m += kMcThreads) {
+            const int at = V.site_atoms[ao + m];
+            mat[m] = at;
+            mx[m] = Real(V.x[3 * (A + at)] - cx);
+            my[m] = Real(V.x[3 * (A + at) + 1] - cy);
+            mz[m] = Real(V.x[3 * (A + at) + 2] - cz);
+            mR[m] = Real(V.R[A + at]);
+            mdq[m] = Real((V.site_q[qo + b * nat + m] - V.q[A + at]) * V.sqrt_k);
+        }
+        __syncthreads();
+        Acc lin = 0;
+        for (int j = tid; j < N; j += kMcThreads) {
+            const Real xj = Real(V.x[3 * (A + j)] - cx), yj = Real(V.x[3 * (A + j) + 1] - cy),
+                       zj = Real(V.x[3 * (A + j) + 2] - cz);
+            const Real qj = Real(V.q[A + j]) * sqk;
+            const Real Rj = Real(V.R[A + j]);
+            Real part = 0;
+            for (int m = 0; m < nat; ++m) {
+                if (mat[m] == j) {
+                    part += mdq[m] * qj * (-tau / mR[m]);
+                } else {
+                    const Real dx = mx[m] - xj, dy = my[m] - yj, dz = mz[m] - zj;
+                    const Real r2 = dx * dx + dy * dy + dz * dz;
+                    const Real rinv = Pr::rsqrt(r2);
+                    const Real D = Real(0.25) * r2 / (mR[m] * Rj);
+                    const Real fi = Pr::rsqrt(r2 + mR[m] * Rj * Pr::expm(D));
+                    part += mdq[m] * qj * (iei * rinv - tau * fi);
+                }
+            }
+            Pr::add(lin, part, Real(kScaleE));
+        }
+        double corr = 0.0;
+        for (int m = tid; m < nat; m += kMcThreads) {
+            const int at = mat[m];
+            const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
+            const double xm0 = V.x[3 * (A + at)], xm1 = V.x[3 * (A + at) + 1], xm2 = V.x[3 * (A + at) + 2];
+            for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e) {
+                const int j = V.excl_j[e];
+                const double d0 = xm0 - V.x[3 * (A + j)], d1 = xm1 - V.x[3 * (A + j) + 1],
+                             d2 = xm2 - V.x[3 * (A + j) + 2];
+                const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                corr -= dqm * V.q[A + j] * kCoulomb * V.inv_eps_in / r;
+            }
+            const double Rm = V.R[A + at];
+            for (int n = 0; n < nat; ++n) {
+                const int an = V.site_atoms[ao + n];
+                const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
+                if (n == m) {
+                    corr += 0.5 * dqm * dqn * (-V.tau * kCoulomb / Rm);
+                    continue;
+                }
+                const double d0 = xm0 - V.x[3 * (A + an)], d1 = xm1 - V.x[3 * (A + an) + 1],
+                             d2 = xm2 - V.x[3 * (A + an) + 2];
+                const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                const double RR = Rm * V.R[A + an];
+                const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+                double amn = -V.tau * kCoulomb / f;
+                bool ex = false;
+                for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e)
+                    if (V.excl_j[e] == an) ex = true;
+                if (!ex) amn += kCoulomb * V.inv_eps_in / sqrt(r2);
+                corr += 0.5 * dqm * dqn * amn;
+            }
+        }
+        // block reduction (fixed order)
+        long long lv = 0;
+        double lin_d = 0.0;
+        if (sizeof(Real) == 4) {
+            lv = (long long)lin;
+        } else {
+            lin_d = (double)lin;
+        }
+        double tot_d = lin_d + corr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lv += __shfl_down_sync(0xffffffffu, lv, o);
+            tot_d += __shfl_down_sync(0xffffffffu, tot_d, o);
+        }
+        if ((tid & 31) == 0) {
+            redl[tid >> 5] = lv;
+            redd[tid >> 5] = tot_d;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long L = 0;
+            double D = 0.0;
+            for (int q = 0; q < kMcThreads / 32; ++q) {
+                L += redl[q];
+                D += redd[q];
+            }
+            const double dU = (double)L / kScaleE + D;
+            double dG = dU - (V.site_uref[no + b] - V.site_uref[no + a]);
+            if (kind == CPH_SITE_PH)
+                dG += kT * kLn10 * (double)(V.site_np[no + b] - V.site_np[no + a]) * (pH - V.site_ref[g]);
+            else
+                dG += kFaraday * (double)(V.site_ne[no + b] - V.site_ne[no + a]) * (E - V.site_ref[g]);
+            const double x = -dG / kT;
+            const int acc = sh_lnu < x ? 1 : 0;
+            cph_mc_record rec;
+            rec.walker = w;
+            rec.site = k;
+            rec.from = a;
+            rec.to = b;
+            rec.accepted = acc;
+            rec.pad_ = 0;
+            rec.dU = dU;
+            rec.x = x;
+            rec.lnu = sh_lnu;
+            V.mc_rec[so + k] = rec;
+            if (acc) V.site_state[so + k] = b;
+            sh_acc = acc;
+            const int base = (kind == CPH_SITE_PH) ? 6 : 8;
+            atomicAdd((unsigned long long*)&V.stats[base], 1ull);
+            if (acc) atomicAdd((unsigned long long*)&V.stats[base + 1], 1ull);
+        }
+        __syncthreads();
+        if (sh_acc) {
+            for (int m = tid; m < nat; m += kMcThreads) V.q[A + mat[m]] = V.site_q[qo + b * nat + m];
+        }
+        __syncthreads();
+    }
+}
+
+// =====================================================================
+// Replica exchange (one CTA): one attempt along one dimension.
+// =====================================================================
+__device__ inline int walker_nprot(const View& V, int w) {
+    const int s = V.w_sys[w];
+    int n = 0;
+    for (int g = V.sys_site_off[s], k = 0; g < V.sys_site_off[s + 1]; ++g, ++k)
+        n += V.site_np[V.site_noff[g] + V.site_state[V.w_site_off[w] + k]];
+    return n;
+}
+
+__device__ inline int walker_nelec(const View& V, int w) {
+    const int s = V.w_sys[w];
+    int n = 0;
+    for (int g = V.sys_site_off[s], k = 0; g < V.sys_site_off[s + 1]; ++g, ++k)
+        n += V.site_ne[V.site_noff[g] + V.site_state[V.w_site_off[w] + k]];
+    return n;
+}
+
+__device__ inline double walker_energy(const View& V, int w) {
+    long long e = 0;
+    for (int t = 0; t < kEAcc; ++t) e += V.eacc[w * kEAcc + t];
+    return (double)e / kScaleE;
+}
+
+constexpr int kExThreads = 256;
+
+__global__ void __launch_bounds__(kExThreads) k_exchange(View V, int dim_req, int s_off) {
+    __shared__ int sdim, spar;
+    const int tid = threadIdx.x;
+    const uint64_t t = (uint64_t)(*V.step + s_off);
+    if (tid == 0) {
+        int dim = dim_req;
+        if (dim < 0) {
+            dim = V.order[V.ex_state[0] % V.n_order];
+            V.ex_state[0] += 1;
+        }
+        sdim = dim;
+        spar = V.ex_state[1 + dim] & 1;
+        V.ex_state[1 + dim] += 1;
+    }
+    for (int w = tid; w < V.W; w += kExThreads) V.vscale[w] = 1.0;
+    __syncthreads();
+    const int dim = sdim, par = spar;
+    const int nd = dim == CPH_DIM_E ? V.nE : (dim == CPH_DIM_PH ? V.npH : V.nT);
+    const int nslots = V.nE * V.npH * V.nT;
+    const int nlines = nslots / nd;
+    const int npl = (nd - par) / 2; // pairs (m, m+1), m = par, par+2, ... , m+1 < nd
+    const int total = nlines * npl;
+    for (int idx = tid; idx < total; idx += kExThreads) {
+        const int line = idx / npl, p = idx % npl;
+        const int m = par + 2 * p;
+        int s1, s2;
+        if (dim == CPH_DIM_E) {
+            const int ipH = line % V.npH, iT = line / V.npH;
+            s1 = m + V.nE * (ipH + V.npH * iT);
+            s2 = s1 + 1;
+        } else if (dim == CPH_DIM_PH) {
+            const int iE = line % V.nE, iT = line / V.nE;
+            s1 = iE + V.nE * (m + V.npH * iT);
+            s2 = s1 + V.nE;
+        } else {
+            const int iE = line % V.nE, ipH = line / V.nE;
+            s1 = iE + V.nE * (ipH + V.npH * m);
+            s2 = s1 + V.nE * V.npH;
+        }
+        const int w1 = V.walker_at[s1], w2 = V.walker_at[s2];
+        cph_exchange_record rec;
+        rec.dim = dim;
+        rec.slot_lo = s1;
+        rec.slot_hi = s2;
+        rec.walker_lo = w1;
+        rec.walker_hi = w2;
+        rec.x = 0.0;
+        rec.lnu = 0.0;
+        if (V.w_sys[w1] != V.w_sys[w2]) {
+            rec.accepted = -1;
+            V.ex_rec[idx] = rec;
+            continue;
+        }
+        const double T1 = V.gT[s1 / (V.nE * V.npH)], T2 = V.gT[s2 / (V.nE * V.npH)];
+        double x;
+        if (dim == CPH_DIM_PH) {
+            const double p1 = V.gpH[(s1 / V.nE) % V.npH], p2 = V.gpH[(s2 / V.nE) % V.npH];
+            x = kLn10 * (p1 - p2) * (double)(walker_nprot(V, w1) - walker_nprot(V, w2));
+        } else if (dim == CPH_DIM_E) {
+            const double e1 = V.gE[s1 % V.nE], e2 = V.gE[s2 % V.nE];
+            x = kFaraday / (kBoltzmann * T1) * (e1 - e2) * (double)(walker_nelec(V, w1) - walker_nelec(V, w2));
+        } else {
+            x = (1.0 / (kBoltzmann * T1) - 1.0 / (kBoltzmann * T2)) * (walker_energy(V, w1) - walker_energy(V, w2));
+        }
+        const U4 u = draw(V.seed, (uint32_t)s1, (uint32_t)dim, t, kRngExchange);
+        const double lnu = log(unit_open(u.a));
+        const int acc = lnu < x ? 1 : 0;
+        rec.x = x;
+        rec.lnu = lnu;
+        rec.accepted = acc;
+        V.ex_rec[idx] = rec;
+        atomicAdd((unsigned long long*)&V.stats[2 * dim], 1ull);
+        if (acc) {
+            atomicAdd((unsigned long long*)&V.stats[2 * dim + 1], 1ull);
+            V.walker_at[s1] = w2;
+            V.walker_at[s2] = w1;
+            V.slot_of[w1] = s2;
+            V.slot_of[w2] = s1;
+            if (dim == CPH_DIM_T) {
+                V.vscale[w1] = sqrt(T2 / T1);
+                V.vscale[w2] = sqrt(T1 / T2);
+            }
+        }
+    }
+    if (tid == 0) *V.ex_n = total;
+}
+
+// =====================================================================
+// Set-up kernels (FP64)
+// =====================================================================
+// U_ref of one (site, state): U_el of the site's atoms alone in the starting
+// geometry with their own Born radii.
+__global__ void k_site_ref(View V, const double* __restrict__ x0, const int* __restrict__ jobs_site,
+                           const int* __restrict__ jobs_state, const int* __restrict__ site_sys,
+                           int n_jobs) {
+    const int job = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job >= n_jobs) return;
+    const int g = jobs_site[job], st = jobs_state[job];
+    const int s = site_sys[g], P = V.sys_poff[s];
+    const int nat = V.site_nat[g], ao = V.site_aoff[g], qo = V.site_qoff[g];
+    double R[kMaxSiteAtoms];
+    for (int m = 0; m < nat; ++m) {
+        const int am = V.site_atoms[ao + m];
+        const double rt = V.rt[P + am];
+        double sum = 0.0;
+        for (int n = 0; n < nat; ++n) {
+            if (n == m) continue;
+            const int an = V.site_atoms[ao + n];
+            double d0 = x0[3 * (P + am)] - x0[3 * (P + an)], d1 = x0[3 * (P + am) + 1] - x0[3 * (P + an) + 1],
+                   d2 = x0[3 * (P + am) + 2] - x0[3 * (P + an) + 2];
+            const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            sum += hct(r, 1.0 / r, rt, 1.0 / rt, V.sc[P + an]);
+        }
+        const double psi = 0.5 * rt * sum;
+        const double th = tanh(psi * (V.alpha + psi * (-V.beta + psi * V.gamma)));
+        R[m] = 1.0 / (1.0 / rt - th / V.rho[P + am]);
+    }
+    double U = 0.0;
+    for (int m = 0; m < nat; ++m) {
+        const double qm = V.site_q[qo + st * nat + m];
+        U += -0.5 * V.tau * kCoulomb * qm * qm / R[m];
+        const int am = V.site_atoms[ao + m];
+        for (int n = m + 1; n < nat; ++n) {
+            const int an = V.site_atoms[ao + n];
+            const double qn = V.site_q[qo + st * nat + n];
+            double d0 = x0[3 * (P + am)] - x0[3 * (P + an)], d1 = x0[3 * (P + am) + 1] - x0[3 * (P + an) + 1],
+                   d2 = x0[3 * (P + am) + 2] - x0[3 * (P + an) + 2];
+            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const double RR = R[m] * R[n];
+            U += -V.tau * kCoulomb * qm * qn / sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+            bool ex = false;
+            for (int e = V.excl_off[P + am]; e < V.excl_off[P + am + 1]; ++e)
+                if (V.excl_j[e] == an) ex = true;
+            if (!ex) U += kCoulomb * V.inv_eps_in * qm * qn / sqrt(r2);
+        }
+    }
+    ((double*)V.site_uref)[V.site_noff[g] + st] = U;
+}
+
+__global__ void k_charges_from_states(View V) {
+    // q of every site atom from the walker's site states
+    const int w = blockIdx.x;
+    const int s = V.w_sys[w], A = V.w_off[w], so = V.w_site_off[w];
+    for (int g = V.sys_site_off[s], k = 0; g < V.sys_site_off[s + 1]; ++g, ++k) {
+        const int st = V.site_state[so + k];
+        const int nat = V.site_nat[g];
+        for (int m = threadIdx.x; m < nat; m += blockDim.x)
+            V.q[A + V.site_atoms[V.site_aoff[g] + m]] = V.site_q[V.site_qoff[g] + st * nat + m];
+    }
+}
+
+__global__ void k_counts(View V, int* np, int* ne) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= V.W) return;
+    np[w] = walker_nprot(V, w);
+    ne[w] = walker_nelec(V, w);
+}
+
+} // namespace cph
+
+// =====================================================================
+// Host side
+// =====================================================================
+using namespace cph;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    ~DevBuf() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+};
+
+} // namespace
+
+struct cph_engine {
+    std::string err = "no error";
+    View V{};
+    DevBuf mem;
+    int precision = CPH_PREC_FP32;
+    int launch_mode = 0; // 0 batched, 1 per replica
+    int mc_ph = 0, mc_redox = 0, ex_every = 0;
+    long long h_step = 0;
+    int n_sys = 0;
+    std::vector<int> h_sys_n, h_w_sys, h_w_off, h_w_site_off, h_sys_site_off;
+    std::vector<int> h_site_nst, h_site_kind;
+    int n_site_states = 0;
+    Item* d_items = nullptr;
+    int n_items = 0;
+    std::vector<int> item_w_off; // per-walker item ranges (items grouped by walker, per-replica mode)
+    Item* d_items_by_w = nullptr;
+    int ex_cap = 0;
+    int mc_kinds_last = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_period = 0;
+    ~cph_engine() {
+        for (auto& g : graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+namespace {
+
+} // namespace
+
+// shared with the differentiable-energy translation unit
+void cph_internal_set_error(const std::string& m) { g_last_error = m; }
+
+namespace {
+
+int fail(cph_engine* e, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (e) e->err = buf;
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t ce_ = (call);                                                             \
+        if (ce_ != cudaSuccess)                                                               \
+            return fail(E, ce_ == cudaErrorMemoryAllocation ? CPH_E_OOM : CPH_E_CUDA,         \
+                        "%s failed: %s", #call, cudaGetErrorString(ce_));                      \
+    } while (0)
+
+template <class T>
+int upload(cph_engine* E, const std::vector<T>& h, T** d) {
+    size_t n = std::max<size_t>(1, h.size());
+    void* p = nullptr;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    E->mem.ptrs.push_back(p);
+    if (!h.empty()) CK(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *d = (T*)p;
+    return CPH_OK;
+}
+
+template <class T>
+int alloc0(cph_engine* E, size_t n, T** d) {
+    void* p = nullptr;
+    CK(cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T)));
+    E->mem.ptrs.push_back(p);
+    CK(cudaMemset(p, 0, std::max<size_t>(1, n) * sizeof(T)));
+    *d = (T*)p;
+    return CPH_OK;
+}
+
+#define TRY(x)                     \
+    do {                           \
+        int rc_ = (x);             \
+        if (rc_ != CPH_OK) return rc_; \
+    } while (0)
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// ---- launch helpers
+int launch_born(cph_engine* E, const Item* items, int n, bool zero_energy, cudaStream_t st) {
+    if (n <= 0) return CPH_OK;
+    if (E->precision == CPH_PREC_FP32)
+        k_born<float><<<n, kTile, 0, st>>>(items, E->V, zero_energy ? 1 : 0);
+    else
+        k_born<double><<<n, kTile, 0, st>>>(items, E->V, zero_energy ? 1 : 0);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int launch_gb(cph_engine* E, const Item* items, int n, bool energy, cudaStream_t st) {
+    if (n <= 0) return CPH_OK;
+    if (E->precision == CPH_PREC_FP32) {
+        if (energy) k_gb<float, true><<<n, kTile, 0, st>>>(items, E->V);
+        else k_gb<float, false><<<n, kTile, 0, st>>>(items, E->V);
+    } else {
+        if (energy) k_gb<double, true><<<n, kTile, 0, st>>>(items, E->V);
+        else k_gb<double, false><<<n, kTile, 0, st>>>(items, E->V);
+    }
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int launch_chain(cph_engine* E, const Item* items, int n, bool energy, cudaStream_t st) {
+    if (n <= 0) return CPH_OK;
+    if (E->precision == CPH_PREC_FP32) {
+        if (energy) k_chain<float, true><<<n, kTile, 0, st>>>(items, E->V);
+        else k_chain<float, false><<<n, kTile, 0, st>>>(items, E->V);
+    } else {
+        if (energy) k_chain<double, true><<<n, kTile, 0, st>>>(items, E->V);
+        else k_chain<double, false><<<n, kTile, 0, st>>>(items, E->V);
+    }
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+// The three pair passes (plus bonded terms) for every walker.
+int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, int s_off,
+                  int mc_kinds);
+
+int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
+    const int W = E->V.W;
+    int first = 1;
+    for (int kind : {CPH_SITE_PH, CPH_SITE_REDOX}) {
+        const int bit = (kind == CPH_SITE_PH) ? CPH_MC_PH : CPH_MC_REDOX;
+        if (!(kinds & bit)) continue;
+        if (E->launch_mode == 0) {
+            if (E->precision == CPH_PREC_FP32)
+                k_mc<float><<<W, kMcThreads, 0, st>>>(E->V, kind, s_off, first, 0);
+            else
+                k_mc<double><<<W, kMcThreads, 0, st>>>(E->V, kind, s_off, first, 0);
+        } else {
+            for (int w = 0; w < W; ++w) {
+                if (E->precision == CPH_PREC_FP32)
+                    k_mc<float><<<1, kMcThreads, 0, st>>>(E->V, kind, s_off, first, w);
+                else
+                    k_mc<double><<<1, kMcThreads, 0, st>>>(E->V, kind, s_off, first, w);
+            }
+        }
+        first = 0;
+        CK(cudaGetLastError());
+    }
+    E->mc_kinds_last = kinds;
+    return CPH_OK;
+}
+
+int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, int s_off,
+                  int mc_kinds) {
+    if (E->launch_mode == 0) {
+        TRY(launch_born(E, E->d_items, E->n_items, energy, st));
+        if (mc_between && mc_kinds) TRY(launch_mc(E, mc_kinds, s_off, st));
+        TRY(launch_gb(E, E->d_items, E->n_items, energy, st));
+        TRY(launch_chain(E, E->d_items, E->n_items, energy, st));
+    } else {
+        const int W = E->V.W;
+        for (int w = 0; w < W; ++w)
+            TRY(launch_born(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
+        if (mc_between && mc_kinds) TRY(launch_mc(E, mc_kinds, s_off, st));
+        for (int w = 0; w < W; ++w)
+            TRY(launch_gb(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
+        for (int w = 0; w < W; ++w)
+            TRY(launch_chain(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
+    }
+    return CPH_OK;
+}
+
+int launch_langevin(cph_engine* E, int s_off, cudaStream_t st) {
+    const int bs = 256;
+    auto one = [&](int a0, int n) {
+        if (E->precision == CPH_PREC_FP32)
+            k_langevin<float><<<(n + bs - 1) / bs, bs, 0, st>>>(E->V, s_off, a0, n);
+        else
+            k_langevin<double><<<(n + bs - 1) / bs, bs, 0, st>>>(E->V, s_off, a0, n);
+    };
+    if (E->launch_mode == 0) {
+        one(0, E->V.total_atoms);
+    } else {
+        for (int w = 0; w < E->V.W; ++w) one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w]);
+    }
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int launch_exchange(cph_engine* E, int dim, int s_off, cudaStream_t st) {
+    k_exchange<<<1, kExThreads, 0, st>>>(E->V, dim, s_off);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int launch_tick(cph_engine* E, long long n, cudaStream_t st) {
+    k_tick<<<1, 1, 0, st>>>(E->V.step, n);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+// Schedule of global step t (see cph_run in cphremd.h).
+int enqueue_step(cph_engine* E, long long t, int s_off, bool full_schedule, cudaStream_t st) {
+    int kinds = 0;
+    bool exch = false;
+    if (full_schedule && t > 0) {
+        if (E->mc_ph > 0 && t % E->mc_ph == 0) kinds |= CPH_MC_PH;
+        if (E->mc_redox > 0 && t % E->mc_redox == 0) kinds |= CPH_MC_REDOX;
+        exch = E->ex_every > 0 && t % E->ex_every == 0;
+    }
+    TRY(launch_forces(E, exch, st, true, s_off, kinds));
+    if (exch) TRY(launch_exchange(E, CPH_DIM_NEXT, s_off, st));
+    TRY(launch_langevin(E, s_off, st));
+    return CPH_OK;
+}
+
+long long gcdll(long long a, long long b) { return b ? gcdll(b, a % b) : a; }
+
+int schedule_period(const cph_engine* E) {
+    long long p = 1;
+    for (int v : {E->mc_ph, E->mc_redox, E->ex_every})
+        if (v > 0) p = p / gcdll(p, v) * v;
+    return (int)std::min<long long>(p, 1 << 20);
+}
+
+int get_graph(cph_engine* E, cudaGraphExec_t* out) {
+    const int mode = E->launch_mode;
+    if (E->graph[mode]) {
+        *out = E->graph[mode];
+        return CPH_OK;
+    }
+    if (!E->cap_stream) CK(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
+    const int P = E->graph_period;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = CPH_OK;
+    // the captured period starts at a step t with t % P == 1 (t > 0 throughout)
+    for (int s = 0; s < P && rc == CPH_OK; ++s) rc = enqueue_step(E, 1 + s, s, true, E->cap_stream);
+    if (rc == CPH_OK) rc = launch_tick(E, P, E->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(E->cap_stream, &g);
+    if (rc != CPH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(E, CPH_E_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(E, CPH_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+    E->graph[mode] = ex;
+    *out = ex;
+    return CPH_OK;
+}
+
+} // namespace
+
+// =====================================================================
+// C ABI
+// =====================================================================
+extern "C" {
+
+const char* cph_last_error(const cph_engine* e) { return e ? e->err.c_str() : g_last_error.c_str(); }
+
+int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* grid,
+                    const cph_run_params* p, uint64_t seed, cph_engine** out) {
+    if (!out) return fail(nullptr, CPH_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!sys || n_sys < 1 || !grid || !p) return fail(nullptr, CPH_E_INVALID, "missing descriptor");
+    if (p->precision != CPH_PREC_FP32 && p->precision != CPH_PREC_FP64)
+        return fail(nullptr, CPH_E_INVALID, "unknown precision %d", p->precision);
+    if (!(p->dt > 0) || !(p->gamma_ln >= 0) || !(p->gb.eps_in > 0) || !(p->gb.eps_out > 0))
+        return fail(nullptr, CPH_E_INVALID, "dt, gamma_ln, eps_in, eps_out must be positive");
+    if (p->mc_ph_every < 0 || p->mc_redox_every < 0 || p->exchange_every < 0)
+        return fail(nullptr, CPH_E_INVALID, "negative interval");
+    if (grid->nE < 1 || grid->npH < 1 || grid->nT < 1 || !grid->E || !grid->pH || !grid->T ||
+        !grid->system_of_slot)
+        return fail(nullptr, CPH_E_INVALID, "bad grid");
+    if (grid->n_order < 1 || grid->n_order > 3) return fail(nullptr, CPH_E_INVALID, "n_order must be 1..3");
+    for (int k = 0; k < grid->n_order; ++k)
+        if (grid->order[k] < 0 || grid->order[k] > 2) return fail(nullptr, CPH_E_INVALID, "bad order entry");
+    for (int k = 0; k < grid->nT; ++k)
+        if (!(grid->T[k] > 0)) return fail(nullptr, CPH_E_INVALID, "temperatures must be positive");
+    const int W = grid->nE * grid->npH * grid->nT;
+    for (int w = 0; w < W; ++w)
+        if (grid->system_of_slot[w] < 0 || grid->system_of_slot[w] >= n_sys)
+            return fail(nullptr, CPH_E_INVALID, "system_of_slot[%d] out of range", w);
+
+    // ---- validate systems and build per-system host tables
+    std::vector<int> sys_n(n_sys), sys_poff(n_sys + 1, 0), sys_site_off(n_sys + 1, 0);
+    std::vector<double> rho, rt, sc, sigh, sqe, mass, x0;
+    std::vector<int> excl_off(1, 0), excl_j, bond_off(1, 0), bond_idx, bond_ij, ang_off(1, 0),
+        ang_idx, ang_ijk;
+    std::vector<double> bond_k, bond_r0, ang_k, ang_t0;
+    std::vector<int> site_kind, site_nat, site_aoff, site_atoms, site_nst, site_qoff, site_noff,
+        site_np, site_ne, site_sys, site_init;
+    std::vector<double> site_q, site_ref;
+    std::vector<int> mt_off(1, 0), mt_list, sys_st_off(n_sys + 1, 0);
+    const double off = p->gb.offset;
+    for (int s = 0; s < n_sys; ++s) {
+        const cph_system_desc& d = sys[s];
+        const int N = d.n_atoms;
+        if (N < 1 || N > 65536) return fail(nullptr, CPH_E_INVALID, "system %d: n_atoms %d out of 1..65536", s, N);
+        if (!d.x || !d.mass || !d.q || !d.rho || !d.screen || !d.sigma || !d.eps)
+            return fail(nullptr, CPH_E_INVALID, "system %d: missing per-atom array", s);
+        if (!finite_all(d.x, 3 * (size_t)N) || !finite_all(d.q, N) || (d.v && !finite_all(d.v, 3 * (size_t)N)))
+            return fail(nullptr, CPH_E_INVALID, "system %d: non-finite positions, velocities or charges", s);
+        sys_n[s] = N;
+        sys_poff[s + 1] = sys_poff[s] + N;
+        for (int a = 0; a < N; ++a) {
+            if (!(d.mass[a] > 0)) return fail(nullptr, CPH_E_INVALID, "system %d atom %d: mass must be > 0", s, a);
+            if (!(d.rho[a] > off)) return fail(nullptr, CPH_E_INVALID, "system %d atom %d: rho must exceed the offset", s, a);
+            if (!(d.screen[a] >= 0) || !(d.sigma[a] >= 0) || !(d.eps[a] >= 0))
+                return fail(nullptr, CPH_E_INVALID, "system %d atom %d: negative screen, sigma or eps", s, a);
+            rho.push_back(d.rho[a]);
+            rt.push_back(d.rho[a] - off);
+            sc.push_back(d.screen[a] * (d.rho[a] - off));
+            sigh.push_back(0.5 * d.sigma[a]);
+            sqe.push_back(std::sqrt(d.eps[a]));
+            mass.push_back(d.mass[a]);
+            for (int c = 0; c < 3; ++c) x0.push_back(d.x[3 * a + c]);
+        }
+        // exclusions: 1-2 and 1-3 through the bond graph, plus the extra list
+        std::vector<std::vector<int>> nb(N);
+        if (d.n_bonds < 0 || (d.n_bonds > 0 && (!d.bonds || !d.bond_k || !d.bond_r0)))
+            return fail(nullptr, CPH_E_INVALID, "system %d: bad bond arrays", s);
+        const int bond_base = (int)bond_k.size();
+        for (int b = 0; b < d.n_bonds; ++b) {
+            int i = d.bonds[2 * b], j = d.bonds[2 * b + 1];
+            if (i < 0 || j < 0 || i >= N || j >= N || i == j)
+                return fail(nullptr, CPH_E_INVALID, "system %d: bond %d has bad atoms", s, b);
+            nb[i].push_back(j);
+            nb[j].push_back(i);
+            bond_ij.push_back(i);
+            bond_ij.push_back(j);
+            bond_k.push_back(d.bond_k[b]);
+            bond_r0.push_back(d.bond_r0[b]);
+        }
+        std::vector<std::set<int>> ex(N);
+        for (int i = 0; i < N; ++i)
+            for (int j : nb[i]) {
+                ex[i].insert(j);
+                for (int k : nb[j])
+                    if (k != i) ex[i].insert(k);
+            }
+        if (d.n_excl < 0 || (d.n_excl > 0 && !d.excl)) return fail(nullptr, CPH_E_INVALID, "system %d: bad exclusion list", s);
+        for (int e = 0; e < d.n_excl; ++e) {
+            int i = d.excl[2 * e], j = d.excl[2 * e + 1];
+            if (i < 0 || j < 0 || i >= N || j >= N || i == j)
+                return fail(nullptr, CPH_E_INVALID, "system %d: exclusion %d has bad atoms", s, e);
+            ex[i].insert(j);
+            ex[j].insert(i);
+        }
+        for (int i = 0; i < N; ++i) {
+            for (int j : ex[i]) excl_j.push_back(j);
+            excl_off.push_back((int)excl_j.size());
+        }
+        // bonded term lists per atom
+        std::vector<std::vector<int>> bt(N), at(N);
+        for (int b = 0; b < d.n_bonds; ++b) {
+            bt[d.bonds[2 * b]].push_back(bond_base + b);
+            bt[d.bonds[2 * b + 1]].push_back(bond_base + b);
+        }
+        if (d.n_angles < 0 || (d.n_angles > 0 && (!d.angles || !d.angle_k || !d.angle_t0)))
+            return fail(nullptr, CPH_E_INVALID, "system %d: bad angle arrays", s);
+        const int ang_base = (int)ang_k.size();
+        for (int a = 0; a < d.n_angles; ++a) {
+            int i = d.angles[3 * a], j = d.angles[3 * a + 1], k = d.angles[3 * a + 2];
+            if (i < 0 || j < 0 || k < 0 || i >= N || j >= N || k >= N || i == j || j == k || i == k)
+                return fail(nullptr, CPH_E_INVALID, "system %d: angle %d has bad atoms", s, a);
+            ang_ijk.push_back(i);
+            ang_ijk.push_back(j);
+            ang_ijk.push_back(k);
+            ang_k.push_back(d.angle_k[a]);
+            ang_t0.push_back(d.angle_t0[a]);
+            at[i].push_back(ang_base + a);
+            at[j].push_back(ang_base + a);
+            at[k].push_back(ang_base + a);
+        }
+        for (int i = 0; i < N; ++i) {
+            for (int b : bt[i]) bond_idx.push_back(b);
+            bond_off.push_back((int)bond_idx.size());
+            for (int a : at[i]) ang_idx.push_back(a);
+            ang_off.push_back((int)ang_idx.size());
+        }
+        // masked j-tiles per i-tile: self and excluded partners
+        const int nt = (N + kTile - 1) / kTile;
+        sys_st_off[s + 1] = sys_st_off[s] + nt;
+        for (int it = 0; it < nt; ++it) {
+            std::set<int> tiles;
+            for (int i = it * kTile; i < std::min(N, (it + 1) * kTile); ++i) {
+                tiles.insert(i / kTile);
+                for (int j : ex[i]) tiles.insert(j / kTile);
+            }
+            for (int jt : tiles) mt_list.push_back(jt);
+            mt_off.push_back((int)mt_list.size());
+        }
+        // sites
+        if (d.n_sites < 0 || (d.n_sites > 0 && !d.sites)) return fail(nullptr, CPH_E_INVALID, "system %d: bad site list", s);
+        std::vector<char> used(N, 0);
+        for (int k = 0; k < d.n_sites; ++k) {
+            const cph_site_desc& sd = d.sites[k];
+            if (sd.kind != CPH_SITE_PH && sd.kind != CPH_SITE_REDOX)
+                return fail(nullptr, CPH_E_INVALID, "system %d site %d: bad kind", s, k);
+            if (sd.n_atoms < 1 || sd.n_atoms > kMaxSiteAtoms || !sd.atoms || !sd.q || !sd.n_prot || !sd.n_elec)
+                return fail(nullptr, CPH_E_INVALID, "system %d site %d: n_atoms must be 1..%d with all arrays", s, k, kMaxSiteAtoms);
+            if (sd.n_states < 2 || sd.n_states > 8 || sd.init_state < 0 || sd.init_state >= sd.n_states)
+                return fail(nullptr, CPH_E_INVALID, "system %d site %d: n_states must be 2..8 and init_state valid", s, k);
+            if (!finite_all(sd.q, (size_t)sd.n_states * sd.n_atoms) || !std::isfinite(sd.ref))
+                return fail(nullptr, CPH_E_INVALID, "system %d site %d: non-finite charges or reference", s, k);
+            site_kind.push_back(sd.kind);
+            site_nat.push_back(sd.n_atoms);
+            site_aoff.push_back((int)site_atoms.size());
+            site_nst.push_back(sd.n_states);
+            site_qoff.push_back((int)site_q.size());
+            site_noff.push_back((int)site_np.size());
+            site_ref.push_back(sd.ref);
+            site_sys.push_back(s);
+            site_init.push_back(sd.init_state);
+            for (int m = 0; m < sd.n_atoms; ++m) {
+                int a = sd.atoms[m];
+                if (a < 0 || a >= N || used[a])
+                    return fail(nullptr, CPH_E_INVALID, "system %d site %d: atom %d invalid or shared", s, k, a);
+                used[a] = 1;
+                site_atoms.push_back(a);
+            }
+            for (int q = 0; q < sd.n_states * sd.n_atoms; ++q) site_q.push_back(sd.q[q]);
+            for (int st = 0; st < sd.n_states; ++st) {
+                site_np.push_back(sd.n_prot[st]);
+                site_ne.push_back(sd.n_elec[st]);
+            }
+        }
+        sys_site_off[s + 1] = sys_site_off[s] + d.n_sites;
+    }
+
+    // ---- walkers
+    std::vector<int> w_sys(W), w_off(W + 1, 0), w_site_off(W + 1, 0), a_walker;
+    for (int w = 0; w < W; ++w) {
+        w_sys[w] = grid->system_of_slot[w];
+        w_off[w + 1] = w_off[w] + sys_n[w_sys[w]];
+        w_site_off[w + 1] = w_site_off[w] + (sys_site_off[w_sys[w] + 1] - sys_site_off[w_sys[w]]);
+    }
+    const long long total_ll = w_off[W];
+    if (total_ll > (1ll << 30)) return fail(nullptr, CPH_E_INVALID, "too many atoms in total");
+    const int total = (int)total_ll;
+    a_walker.resize(total);
+    std::vector<double> hx(3 * (size_t)total), hv(3 * (size_t)total, 0.0), hq(total);
+    std::vector<int> hstate(w_site_off[W]);
+    for (int w = 0; w < W; ++w) {
+        const cph_system_desc& d = sys[w_sys[w]];
+        for (int a = 0; a < d.n_atoms; ++a) {
+            a_walker[w_off[w] + a] = w;
+            hq[w_off[w] + a] = d.q[a];
+            for (int c = 0; c < 3; ++c) {
+                hx[3 * (size_t)(w_off[w] + a) + c] = d.x[3 * a + c];
+                if (d.v) hv[3 * (size_t)(w_off[w] + a) + c] = d.v[3 * a + c];
+            }
+        }
+        for (int k = 0; k < d.n_sites; ++k) {
+            const cph_site_desc& sd = d.sites[k];
+            hstate[w_site_off[w] + k] = sd.init_state;
+            for (int m = 0; m < sd.n_atoms; ++m) hq[w_off[w] + sd.atoms[m]] = sd.q[sd.init_state * sd.n_atoms + m];
+        }
+    }
+    // work items, largest systems first
+    std::vector<Item> items, items_by_w;
+    std::vector<int> item_w_off(W + 1, 0);
+    for (int w = 0; w < W; ++w) {
+        const int s = w_sys[w], N = sys_n[s];
+        for (int it = 0; it * kTile < N; ++it) items_by_w.push_back(Item{w, it * kTile, sys_st_off[s] + it, 0});
+        item_w_off[w + 1] = (int)items_by_w.size();
+    }
+    items = items_by_w;
+    std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+        return sys_n[w_sys[a.w]] > sys_n[w_sys[b.w]];
+    });
+
+    cph_engine* E = new cph_engine();
+    std::unique_ptr<cph_engine> guard(E);
+    E->precision = p->precision;
+    E->mc_ph = p->mc_ph_every;
+    E->mc_redox = p->mc_redox_every;
+    E->ex_every = p->exchange_every;
+    E->n_sys = n_sys;
+    E->h_sys_n = sys_n;
+    E->h_w_sys = w_sys;
+    E->h_w_off = w_off;
+    E->h_w_site_off = w_site_off;
+    E->h_sys_site_off = sys_site_off;
+    E->h_site_nst = site_nst;
+    E->h_site_kind = site_kind;
+    E->n_site_states = (int)site_np.size();
+    E->item_w_off = item_w_off;
+    E->n_items = (int)items.size();
+    E->graph_period = schedule_period(E);
+    View& V = E->V;
+    V.W = W;
+    V.total_atoms = total;
+    std::vector<int> sys_poff_v(sys_poff.begin(), sys_poff.end());
+    int* d;
+    double* dd;
+    TRY(upload(E, w_sys, &d)); V.w_sys = d;
+    TRY(upload(E, w_off, &d)); V.w_off = d;
+    TRY(upload(E, a_walker, &d)); V.a_walker = d;
+    TRY(upload(E, w_site_off, &d)); V.w_site_off = d;
+    TRY(upload(E, sys_n, &d)); V.sys_n = d;
+    TRY(upload(E, sys_poff_v, &d)); V.sys_poff = d;
+    TRY(upload(E, sys_site_off, &d)); V.sys_site_off = d;
+    TRY(upload(E, rho, &dd)); V.rho = dd;
+    TRY(upload(E, rt, &dd)); V.rt = dd;
+    TRY(upload(E, sc, &dd)); V.sc = dd;
+    TRY(upload(E, sigh, &dd)); V.sigh = dd;
+    TRY(upload(E, sqe, &dd)); V.sqe = dd;
+    TRY(upload(E, mass, &dd)); V.mass = dd;
+    TRY(upload(E, excl_off, &d)); V.excl_off = d;
+    TRY(upload(E, excl_j, &d)); V.excl_j = d;
+    TRY(upload(E, bond_off, &d)); V.bond_off = d;
+    TRY(upload(E, bond_idx, &d)); V.bond_idx = d;
+    TRY(upload(E, bond_ij, &d)); V.bond_ij = d;
+    TRY(upload(E, bond_k, &dd)); V.bond_k = dd;
+    TRY(upload(E, bond_r0, &dd)); V.bond_r0 = dd;
+    TRY(upload(E, ang_off, &d)); V.ang_off = d;
+    TRY(upload(E, ang_idx, &d)); V.ang_idx = d;
+    TRY(upload(E, ang_ijk, &d)); V.ang_ijk = d;
+    TRY(upload(E, ang_k, &dd)); V.ang_k = dd;
+    TRY(upload(E, ang_t0, &dd)); V.ang_t0 = dd;
+    TRY(upload(E, mt_off, &d)); V.mt_off = d;
+    TRY(upload(E, mt_list, &d)); V.mt_list = d;
+    TRY(upload(E, site_kind, &d)); V.site_kind = d;
+    TRY(upload(E, site_nat, &d)); V.site_nat = d;
+    TRY(upload(E, site_aoff, &d)); V.site_aoff = d;
+    TRY(upload(E, site_atoms, &d)); V.site_atoms = d;
+    TRY(upload(E, site_nst, &d)); V.site_nst = d;
+    TRY(upload(E, site_qoff, &d)); V.site_qoff = d;
+    TRY(upload(E, site_noff, &d)); V.site_noff = d;
+    TRY(upload(E, site_q, &dd)); V.site_q = dd;
+    TRY(upload(E, site_np, &d)); V.site_np = d;
+    TRY(upload(E, site_ne, &d)); V.site_ne = d;
+    TRY(upload(E, site_ref, &dd)); V.site_ref = dd;
+    TRY(alloc0(E, site_np.size(), &dd)); V.site_uref = dd;
+    TRY(upload(E, hx, &dd)); V.x = dd;
+    TRY(upload(E, hv, &dd)); V.v = dd;
+    TRY(upload(E, hq, &dd)); V.q = dd;
+    TRY(alloc0(E, total, &dd)); V.psi = dd;
+    TRY(alloc0(E, total, &dd)); V.R = dd;
+    TRY(alloc0(E, total, &dd)); V.dRdpsi = dd;
+    TRY(alloc0(E, total, &dd)); V.c = dd;
+    TRY(alloc0(E, 3 * (size_t)total, &dd)); V.Fd = dd;
+    TRY(alloc0(E, 3 * (size_t)total, &dd)); V.F = dd;
+    long long* dl;
+    TRY(alloc0(E, (size_t)W * kEAcc, &dl)); V.eacc = dl;
+    std::vector<int> ident(W);
+    std::iota(ident.begin(), ident.end(), 0);
+    TRY(upload(E, ident, &d)); V.slot_of = d;
+    TRY(upload(E, ident, &d)); V.walker_at = d;
+    TRY(upload(E, hstate, &d)); V.site_state = d;
+    std::vector<double> ones(W, 1.0);
+    TRY(upload(E, ones, &dd)); V.vscale = dd;
+    TRY(alloc0(E, 1, &dl)); V.step = dl;
+    TRY(alloc0(E, 1, &d)); V.status = d;
+    TRY(alloc0(E, 4, &d)); V.ex_state = d;
+    TRY(alloc0(E, 10, &dl)); V.stats = dl;
+    cph_mc_record* dm;
+    {
+        void* pm = nullptr;
+        CK(cudaMalloc(&pm, std::max<size_t>(1, w_site_off[W]) * sizeof(cph_mc_record)));
+        E->mem.ptrs.push_back(pm);
+        CK(cudaMemset(pm, 0xff, std::max<size_t>(1, w_site_off[W]) * sizeof(cph_mc_record)));
+        dm = (cph_mc_record*)pm;
+    }
+    V.mc_rec = dm;
+    E->ex_cap = W; // pairs per attempt <= slots / 2
+    {
+        void* pe = nullptr;
+        CK(cudaMalloc(&pe, std::max<size_t>(1, E->ex_cap) * sizeof(cph_exchange_record)));
+        E->mem.ptrs.push_back(pe);
+        V.ex_rec = (cph_exchange_record*)pe;
+    }
+    TRY(alloc0(E, 1, &d)); V.ex_n = d;
+    std::vector<double> gE(grid->E, grid->E + grid->nE), gpH(grid->pH, grid->pH + grid->npH),
+        gT(grid->T, grid->T + grid->nT);
+    TRY(upload(E, gE, &dd)); V.gE = dd;
+    TRY(upload(E, gpH, &dd)); V.gpH = dd;
+    TRY(upload(E, gT, &dd)); V.gT = dd;
+    V.nE = grid->nE;
+    V.npH = grid->npH;
+    V.nT = grid->nT;
+    V.n_order = grid->n_order;
+    for (int k = 0; k < 3; ++k) V.order[k] = k < grid->n_order ? grid->order[k] : 0;
+    V.tau = 1.0 / p->gb.eps_in - 1.0 / p->gb.eps_out;
+    V.inv_eps_in = 1.0 / p->gb.eps_in;
+    V.sqrt_k = std::sqrt(kCoulomb);
+    V.alpha = p->gb.alpha;
+    V.beta = p->gb.beta;
+    V.gamma = p->gb.gamma;
+    V.offset = p->gb.offset;
+    V.dt = p->dt;
+    V.gamma_ln = p->gamma_ln;
+    V.seed = seed;
+    Item* di;
+    TRY(upload(E, items, &di)); E->d_items = di;
+    TRY(upload(E, items_by_w, &di)); E->d_items_by_w = di;
+
+    // reference energies of every (site, state)
+    if (!site_np.empty()) {
+        std::vector<int> js, jst;
+        for (size_t g = 0; g < site_nst.size(); ++g)
+            for (int st = 0; st < site_nst[g]; ++st) {
+                js.push_back((int)g);
+                jst.push_back(st);
+            }
+        double* dx0;
+        int *djs, *djst, *dss;
+        TRY(upload(E, x0, &dx0));
+        TRY(upload(E, js, &djs));
+        TRY(upload(E, jst, &djst));
+        TRY(upload(E, site_sys, &dss));
+        const int nj = (int)js.size();
+        k_site_ref<<<(nj + 63) / 64, 64>>>(E->V, dx0, djs, djst, dss, nj);
+        CK(cudaGetLastError());
+    }
+    CK(cudaDeviceSynchronize());
+    *out = guard.release();
+    return CPH_OK;
+}
+
+void cph_destroy(cph_engine* e) { delete e; }
+
+int cph_num_walkers(const cph_engine* e) { return e ? e->V.W : CPH_E_INVALID; }
+int cph_total_atoms(const cph_engine* e) { return e ? e->V.total_atoms : CPH_E_INVALID; }
+
+int cph_walker_offsets(const cph_engine* e, int* offsets) {
+    if (!e || !offsets) return fail(nullptr, CPH_E_INVALID, "NULL argument");
+    std::copy(e->h_w_off.begin(), e->h_w_off.end(), offsets);
+    return CPH_OK;
+}
+
+int cph_site_offsets(const cph_engine* e, int* offsets) {
+    if (!e || !offsets) return fail(nullptr, CPH_E_INVALID, "NULL argument");
+    std::copy(e->h_w_site_off.begin(), e->h_w_site_off.end(), offsets);
+    return CPH_OK;
+}
+
+int cph_set_launch_mode(cph_engine* e, int mode) {
+    if (!e || (mode != CPH_LAUNCH_BATCHED && mode != CPH_LAUNCH_PER_REPLICA))
+        return fail(e, CPH_E_INVALID, "bad launch mode");
+    e->launch_mode = mode;
+    return CPH_OK;
+}
+
+int cph_evaluate(cph_engine* e, void* stream) {
+    if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
+    return launch_forces(e, true, (cudaStream_t)stream, false, 0, 0);
+}
+
+int cph_time_passes(cph_engine* e, int reps, double* ms, void* stream) {
+    if (!e || !ms || reps < 1) return fail(e, CPH_E_INVALID, "bad arguments");
+    cph_engine* E = e;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[4];
+    for (auto& x : ev) CK(cudaEventCreate(&x));
+    double acc[3] = {0, 0, 0};
+    int rc = CPH_OK;
+    for (int r = 0; r < reps && rc == CPH_OK; ++r) {
+        cudaEventRecord(ev[0], st);
+        if (e->launch_mode == 0) {
+            rc = launch_born(e, e->d_items, e->n_items, false, st);
+            cudaEventRecord(ev[1], st);
+            if (rc == CPH_OK) rc = launch_gb(e, e->d_items, e->n_items, false, st);
+            cudaEventRecord(ev[2], st);
+            if (rc == CPH_OK) rc = launch_chain(e, e->d_items, e->n_items, false, st);
+        } else {
+            const int W = e->V.W;
+            for (int w = 0; w < W && rc == CPH_OK; ++w)
+                rc = launch_born(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
+            cudaEventRecord(ev[1], st);
+            for (int w = 0; w < W && rc == CPH_OK; ++w)
+                rc = launch_gb(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
+            cudaEventRecord(ev[2], st);
+            for (int w = 0; w < W && rc == CPH_OK; ++w)
+                rc = launch_chain(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
+        }
+        cudaEventRecord(ev[3], st);
+        cudaError_t ce = cudaEventSynchronize(ev[3]);
+        if (ce != cudaSuccess && rc == CPH_OK) rc = fail(e, CPH_E_CUDA, "timing: %s", cudaGetErrorString(ce));
+        for (int k = 0; k < 3 && rc == CPH_OK; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (rc != CPH_OK) return rc;
+    for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+    return CPH_OK;
+}
+
+int cph_step_replicas(cph_engine* e, int64_t n_steps, void* stream) {
+    if (!e || n_steps < 0) return fail(e, CPH_E_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t s = 0; s < n_steps; ++s) TRY(enqueue_step(e, e->h_step + s, (int)s, false, st));
+    if (n_steps) TRY(launch_tick(e, n_steps, st));
+    e->h_step += n_steps;
+    return CPH_OK;
+}
+
+int cph_mc_titrate(cph_engine* e, int kind, void* stream) {
+    if (!e || kind < 1 || kind > 3) return fail(e, CPH_E_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (e->launch_mode == 0) TRY(launch_born(e, e->d_items, e->n_items, false, st));
+    else
+        for (int w = 0; w < e->V.W; ++w)
+            TRY(launch_born(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st));
+    TRY(launch_mc(e, kind, 0, st));
+    return CPH_OK;
+}
+
+int cph_attempt_exchanges(cph_engine* e, int dim, void* stream) {
+    if (!e || dim < -1 || dim > 2) return fail(e, CPH_E_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    cph_engine* E = e;
+    // energies at the current state (needed for T; cheap to keep uniform)
+    TRY(launch_forces(e, true, st, false, 0, 0));
+    TRY(launch_exchange(e, dim, 0, st));
+    const int n = e->V.total_atoms, bs = 256;
+    k_vscale<<<(n + bs - 1) / bs, bs, 0, st>>>(e->V);
+    k_vscale_reset<<<(e->V.W + bs - 1) / bs, bs, 0, st>>>(e->V);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int cph_run(cph_engine* e, int64_t n_steps, void* stream) {
+    if (!e || n_steps < 0) return fail(e, CPH_E_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    cph_engine* E = e;
+    const int P = e->graph_period;
+    int64_t done = 0;
+    int64_t direct = 0; // steps launched directly since the last tick
+    while (done < n_steps) {
+        const long long t = e->h_step;
+        if (P > 1 && t % P == 1 && n_steps - done >= P) {
+            if (direct) {
+                TRY(launch_tick(e, direct, st));
+                direct = 0;
+            }
+            cudaGraphExec_t g;
+            TRY(get_graph(e, &g));
+            CK(cudaGraphLaunch(g, st));
+            e->h_step += P;
+            done += P;
+            e->mc_kinds_last = (e->mc_ph > 0 ? CPH_MC_PH : 0) | (e->mc_redox > 0 ? CPH_MC_REDOX : 0);
+        } else {
+            TRY(enqueue_step(e, t, (int)direct, true, st));
+            ++direct;
+            ++e->h_step;
+            ++done;
+        }
+    }
+    if (direct) TRY(launch_tick(e, direct, st));
+    return CPH_OK;
+}
+
+#define SYNC_OR_FAIL(e, stream)                                                                 \
+    do {                                                                                        \
+        cph_engine* E = (e);                                                                    \
+        CK(cudaStreamSynchronize((cudaStream_t)(stream)));                                      \
+    } while (0)
+
+static int copy_out(cph_engine* e, void* dst, const void* src, size_t bytes, void* stream) {
+    if (!e || !dst) return fail(e, CPH_E_INVALID, "NULL argument");
+    cph_engine* E = e;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return CPH_OK;
+}
+
+static int copy_in(cph_engine* e, void* dst, const void* src, size_t bytes, void* stream) {
+    if (!e || !src) return fail(e, CPH_E_INVALID, "NULL argument");
+    cph_engine* E = e;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+    return CPH_OK;
+}
+
+int cph_get_energies(cph_engine* e, double* out, void* stream) {
+    if (!e || !out) return fail(e, CPH_E_INVALID, "NULL argument");
+    std::vector<long long> h((size_t)e->V.W * kEAcc);
+    TRY(copy_out(e, h.data(), e->V.eacc, h.size() * sizeof(long long), stream));
+    for (int w = 0; w < e->V.W; ++w) {
+        long long tot = 0;
+        for (int t = 0; t < kEAcc; ++t) {
+            out[w * CPH_NTERMS + t] = (double)h[w * kEAcc + t] / kScaleE;
+            tot += h[w * kEAcc + t];
+        }
+        out[w * CPH_NTERMS + CPH_E_TOTAL] = (double)tot / kScaleE;
+    }
+    return CPH_OK;
+}
+
+int cph_get_forces(cph_engine* e, double* out, void* stream) {
+    return copy_out(e, out, e ? e->V.F : nullptr, 3 * sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_get_born_radii(cph_engine* e, double* out, void* stream) {
+    return copy_out(e, out, e ? e->V.R : nullptr, sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_get_positions(cph_engine* e, double* out, void* stream) {
+    return copy_out(e, out, e ? e->V.x : nullptr, 3 * sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_set_positions(cph_engine* e, const double* in, void* stream) {
+    if (e && in && !finite_all(in, 3 * (size_t)e->V.total_atoms)) return fail(e, CPH_E_INVALID, "non-finite positions");
+    return copy_in(e, e ? e->V.x : nullptr, in, 3 * sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_get_velocities(cph_engine* e, double* out, void* stream) {
+    return copy_out(e, out, e ? e->V.v : nullptr, 3 * sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_set_velocities(cph_engine* e, const double* in, void* stream) {
+    if (e && in && !finite_all(in, 3 * (size_t)e->V.total_atoms)) return fail(e, CPH_E_INVALID, "non-finite velocities");
+    return copy_in(e, e ? e->V.v : nullptr, in, 3 * sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_get_charges(cph_engine* e, double* out, void* stream) {
+    return copy_out(e, out, e ? e->V.q : nullptr, sizeof(double) * (e ? e->V.total_atoms : 0), stream);
+}
+int cph_get_site_states(cph_engine* e, int* out, void* stream) {
+    return copy_out(e, out, e ? e->V.site_state : nullptr, sizeof(int) * (e ? e->h_w_site_off.back() : 0), stream);
+}
+int cph_set_site_states(cph_engine* e, const int* in, void* stream) {
+    if (!e || !in) return fail(e, CPH_E_INVALID, "NULL argument");
+    for (int w = 0; w < e->V.W; ++w) {
+        const int s = e->h_w_sys[w];
+        for (int g = e->h_sys_site_off[s], k = 0; g < e->h_sys_site_off[s + 1]; ++g, ++k) {
+            int st = in[e->h_w_site_off[w] + k];
+            if (st < 0 || st >= e->h_site_nst[g]) return fail(e, CPH_E_INVALID, "walker %d site %d: bad state %d", w, k, st);
+        }
+    }
+    TRY(copy_in(e, e->V.site_state, in, sizeof(int) * e->h_w_site_off.back(), stream));
+    cph_engine* E = e;
+    k_charges_from_states<<<e->V.W, 64, 0, (cudaStream_t)stream>>>(e->V);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return CPH_OK;
+}
+int cph_get_counts(cph_engine* e, int* n_prot, int* n_elec, void* stream) {
+    if (!e || !n_prot || !n_elec) return fail(e, CPH_E_INVALID, "NULL argument");
+    cph_engine* E = e;
+    int* tmp = nullptr;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMalloc(&tmp, 2 * sizeof(int) * e->V.W));
+    k_counts<<<(e->V.W + 127) / 128, 128, 0, (cudaStream_t)stream>>>(e->V, tmp, tmp + e->V.W);
+    cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+    if (ce == cudaSuccess) ce = cudaMemcpy(n_prot, tmp, sizeof(int) * e->V.W, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(n_elec, tmp + e->V.W, sizeof(int) * e->V.W, cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    if (ce != cudaSuccess) return fail(e, CPH_E_CUDA, "counts: %s", cudaGetErrorString(ce));
+    return CPH_OK;
+}
+int cph_get_condition_map(cph_engine* e, int* slot_of_walker, void* stream) {
+    return copy_out(e, slot_of_walker, e ? e->V.slot_of : nullptr, sizeof(int) * (e ? e->V.W : 0), stream);
+}
+int cph_set_condition_map(cph_engine* e, const int* slot_of_walker, void* stream) {
+    if (!e || !slot_of_walker) return fail(e, CPH_E_INVALID, "NULL argument");
+    const int W = e->V.W;
+    std::vector<int> inv(W, -1);
+    for (int w = 0; w < W; ++w) {
+        int s = slot_of_walker[w];
+        if (s < 0 || s >= W || inv[s] >= 0) return fail(e, CPH_E_INVALID, "condition map is not a permutation");
+        if (e->h_w_sys[w] != e->h_w_sys[s]) return fail(e, CPH_E_INVALID, "walker %d cannot sit at slot %d of another system", w, s);
+        inv[s] = w;
+    }
+    TRY(copy_in(e, e->V.slot_of, slot_of_walker, sizeof(int) * W, stream));
+    TRY(copy_in(e, e->V.walker_at, inv.data(), sizeof(int) * W, stream));
+    return CPH_OK;
+}
+int cph_get_accept_stats(cph_engine* e, int64_t* out, void* stream) {
+    return copy_out(e, out, e ? e->V.stats : nullptr, 10 * sizeof(long long), stream);
+}
+int cph_get_reference_energies(cph_engine* e, double* out) {
+    return copy_out(e, out, e ? e->V.site_uref : nullptr, sizeof(double) * (e ? e->n_site_states : 0), nullptr);
+}
+int cph_get_mc_records(cph_engine* e, cph_mc_record* out, int max, int* n_out, void* stream) {
+    if (!e || !out || !n_out) return fail(e, CPH_E_INVALID, "NULL argument");
+    const int n = std::min(max, e->h_w_site_off.back());
+    *n_out = n;
+    return copy_out(e, out, e->V.mc_rec, sizeof(cph_mc_record) * n, stream);
+}
+int cph_get_exchange_records(cph_engine* e, cph_exchange_record* out, int max, int* n_out, void* stream) {
+    if (!e || !out || !n_out) return fail(e, CPH_E_INVALID, "NULL argument");
+    int n = 0;
+    TRY(copy_out(e, &n, e->V.ex_n, sizeof(int), stream));
+    n = std::min(n, std::min(max, e->ex_cap));
+    *n_out = n;
+    return copy_out(e, out, e->V.ex_rec, sizeof(cph_exchange_record) * n, stream);
+}
+int64_t cph_get_step(const cph_engine* e) { return e ? e->h_step : -1; }
+int cph_set_step(cph_engine* e, int64_t step) {
+    if (!e || step < 0) return fail(e, CPH_E_INVALID, "bad arguments");
+    long long s = step;
+    TRY(copy_in(e, e->V.step, &s, sizeof s, nullptr));
+    e->h_step = step;
+    return CPH_OK;
+}
+int cph_status(cph_engine* e, void* stream) {
+    if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
+    int st = 0;
+    TRY(copy_out(e, &st, e->V.status, sizeof(int), stream));
+    if (st) return fail(e, CPH_E_NONFINITE, "non-finite %s produced", (st & 2) ? "position" : "force");
+    return CPH_OK;
+}
+
+} // extern "C"

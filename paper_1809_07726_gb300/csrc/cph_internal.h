@@ -1,0 +1,69 @@
+// Internal layout shared by the engine's translation units (not part of the ABI).
+//
+// Device memory layout (SoA over "global atoms"; atom a of walker w is global
+// atom w_off[w] + a; per-system parameters are indexed sys_poff[s] + a):
+//   x, v, F, Fd      double [3 * total_atoms]   xyz interleaved
+//   q                double [total_atoms]        current charges (MC changes them)
+//   psi, R, dRdpsi   double [total_atoms]        Born-radius pass results
+//   c                double [total_atoms]        dE/dR dR/dpsi rt/2 (chain-rule weights)
+//   rho, rt, sc      double [system atoms]       intrinsic radius, rho - offset, screen*rt
+//   sigh, sqe, mass  double [system atoms]       sigma/2, sqrt(eps), mass
+//   eacc             int64  [W * 5]              fixed-point (2^32) energy terms per walker
+#pragma once
+#include <cstdint>
+#include "../../include/cphremd.h"
+
+namespace cph {
+
+struct Item {
+    int w;  // walker
+    int i0; // first atom of the i-tile
+    int st; // (system, i-tile) index into the masked-tile table
+    int pad;
+};
+
+struct View {
+    // walkers
+    int W, total_atoms;
+    const int* w_sys;
+    const int* w_off;
+    const int* a_walker;
+    const int* w_site_off;
+    // systems
+    const int* sys_n;
+    const int* sys_poff;
+    const int* sys_site_off;
+    const double *rho, *rt, *sc, *sigh, *sqe, *mass;
+    const int *excl_off, *excl_j;
+    const int *bond_off, *bond_idx, *bond_ij;
+    const double *bond_k, *bond_r0;
+    const int *ang_off, *ang_idx, *ang_ijk;
+    const double *ang_k, *ang_t0;
+    const int *mt_off, *mt_list;
+    // sites (global site index g = sys_site_off[s] + k)
+    const int *site_kind, *site_nat, *site_aoff, *site_atoms, *site_nst, *site_qoff, *site_noff;
+    const double* site_q;
+    const int *site_np, *site_ne;
+    const double *site_ref, *site_uref;
+    // dynamic state
+    double *x, *v, *q, *psi, *R, *dRdpsi, *c, *Fd, *F;
+    long long* eacc;
+    int *slot_of, *walker_at, *site_state;
+    double* vscale;
+    long long* step;
+    int* status;
+    int* ex_state; // [0] exchange events, [1..3] attempts along E, pH, T
+    long long* stats; // [10]
+    cph_mc_record* mc_rec;
+    cph_exchange_record* ex_rec;
+    int* ex_n;
+    // grid
+    const double *gE, *gpH, *gT;
+    int nE, npH, nT, n_order;
+    int order[3];
+    // parameters
+    double tau, inv_eps_in, sqrt_k, alpha, beta, gamma, offset, dt, gamma_ln;
+    unsigned long long seed;
+};
+
+} // namespace cph

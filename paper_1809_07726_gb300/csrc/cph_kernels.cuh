@@ -1,0 +1,572 @@
+// Engine kernels: the per-step pair passes over every walker of the replica
+// grid, bonded terms, Langevin integration, Monte-Carlo titration sweeps and
+// replica exchanges.  Host code lives in cph_engine.cu.
+//
+// Work decomposition of the three pair passes.  Every walker's atoms are cut
+// into i-tiles of kTile atoms; one CTA of kTile threads owns one i-tile, one
+// thread one atom i.  The CTA sweeps all j of its walker in tiles of kTile
+// staged in shared memory and read back as broadcasts, so every ordered pair
+// (i, j) is evaluated by the owner of i: no atomics, no cross-thread
+// reductions, and the result of an atom does not depend on the launch shape
+// (batched and per-replica launches agree bit for bit).  Positions are made
+// relative to the i-tile's first atom in FP64 before rounding to FP32, so
+// close pairs keep full FP32 precision in their separation.  In FP32 mode a
+// j-tile's partial sums are FP32 and are added into int64 fixed-point
+// accumulators (scales 2^32 and 2^40); in FP64 mode everything is FP64.
+//
+// Tiles in which some atom i of the CTA meets itself or an excluded partner
+// are listed per (system, i-tile) at set-up; only those run the masked loop.
+#pragma once
+#include "cph_device.cuh"
+#include "cph_internal.h"
+
+namespace cph {
+
+constexpr int kTile = 128;
+constexpr float kFarF = 1.0e4f;
+
+template <class Real>
+struct alignas(sizeof(Real) * 4) J4 {
+    Real x, y, z, w;
+};
+
+template <class Real>
+struct alignas(sizeof(Real) * 2) J2 {
+    Real x, y;
+};
+
+// Per-walker energy accumulators (fixed point 2^32): GB, Coulomb, LJ, bond, angle.
+constexpr int kEAcc = 5;
+
+template <class T>
+__device__ inline T block_sum_128(T v, T* red) {
+    // deterministic fixed-order reduction over 128 threads
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0) s = red[0] + red[1] + red[2] + red[3];
+    return s;
+}
+
+// Build the exclusion / self masks of atom i for the j-tile starting at j0.
+__device__ inline void tile_masks(const View& V, int P, int i, bool vi, int j0, uint32_t ex[4],
+                                  uint32_t self[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ex[q] = self[q] = 0u;
+    if (!vi) return;
+    int d = i - j0;
+    if (d >= 0 && d < kTile) {
+        self[d >> 5] |= 1u << (d & 31);
+        ex[d >> 5] |= 1u << (d & 31);
+    }
+    for (int e = V.excl_off[P + i]; e < V.excl_off[P + i + 1]; ++e) {
+        int dj = V.excl_j[e] - j0;
+        if (dj >= 0 && dj < kTile) ex[dj >> 5] |= 1u << (dj & 31);
+    }
+}
+
+// ------------------------------------------------------------- pass 1: Born radii
+// psi_i = rt_i/2 sum_{j != i} H(r_ij, rt_i, s_j); R_i = 1/(1/rt_i - tanh(theta)/rho_i)
+// with theta = alpha psi - beta psi^2 + gamma psi^3, finalised in FP64.
+template <class Real>
+__global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, View V,
+                                                int zero_energy) {
+    using Pr = Prec<Real>;
+    __shared__ J4<Real> sj[kTile];
+    const Item it = items[blockIdx.x];
+    const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
+    const int tid = threadIdx.x;
+    const int i = it.i0 + tid;
+    const bool vi = i < N;
+    if (it.i0 == 0) {
+        if (zero_energy && tid < kEAcc) V.eacc[w * kEAcc + tid] = 0;
+        if (tid == kEAcc) V.vscale[w] = 1.0;
+    }
+    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
+                 cz = V.x[3 * (A + it.i0) + 2];
+    Real xi = Real(-kFarF), yi = Real(-kFarF), zi = Real(-kFarF), rti = Real(1);
+    if (vi) {
+        xi = Real(V.x[3 * (A + i)] - cx);
+        yi = Real(V.x[3 * (A + i) + 1] - cy);
+        zi = Real(V.x[3 * (A + i) + 2] - cz);
+        rti = Real(V.rt[P + i]);
+    }
+    const Real irti = Real(1) / rti;
+    typename Pr::Acc acc = 0;
+    int mp = V.mt_off[it.st];
+    const int me = V.mt_off[it.st + 1];
+    int next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+    for (int j0 = 0, jt = 0; j0 < N; j0 += kTile, ++jt) {
+        __syncthreads();
+        {
+            const int j = j0 + tid;
+            J4<Real> v;
+            if (j < N) {
+                v.x = Real(V.x[3 * (A + j)] - cx);
+                v.y = Real(V.x[3 * (A + j) + 1] - cy);
+                v.z = Real(V.x[3 * (A + j) + 2] - cz);
+                v.w = Real(V.sc[P + j]);
+            } else {
+                v.x = v.y = v.z = Real(kFarF);
+                v.w = Real(0);
+            }
+            sj[tid] = v;
+        }
+        __syncthreads();
+        Real part = 0;
+        if (jt != next) {
+#pragma unroll 4
+            for (int k = 0; k < kTile; ++k) {
+                const J4<Real> b = sj[k];
+                const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                const Real rinv = Pr::rsqrt(r2);
+                part += hct(r2 * rinv, rinv, rti, irti, b.w);
+            }
+        } else {
+            ++mp;
+            next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+            const int dself = i - j0;
+            for (int k = 0; k < kTile; ++k) {
+                const J4<Real> b = sj[k];
+                const bool self = (k == dself);
+                const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
+                Real r2 = dx * dx + dy * dy + dz * dz;
+                r2 = self ? Real(1) : r2;
+                const Real rinv = Pr::rsqrt(r2);
+                const Real h = hct(r2 * rinv, rinv, rti, irti, b.w);
+                part += self ? Real(0) : h;
+            }
+        }
+        Pr::add(acc, part, Real(kScaleH));
+    }
+    if (vi) {
+        const double sumH = Pr::value(acc, kScaleH);
+        const double rt = V.rt[P + i], rho = V.rho[P + i];
+        const double psi = 0.5 * rt * sumH;
+        const double th = tanh(psi * (V.alpha + psi * (-V.beta + psi * V.gamma)));
+        const double R = 1.0 / (1.0 / rt - th / rho);
+        V.psi[A + i] = psi;
+        V.R[A + i] = R;
+        V.dRdpsi[A + i] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) / rho;
+    }
+}
+
+// ------------------------------------------- pass 2: GB + Coulomb + LJ pair pass
+// Owner i accumulates the direct force, dE_GB/dR_i and (optionally) its share
+// of the energies; the epilogue turns dE/dR_i into c_i = dE/dR_i dR_i/dpsi_i rt_i/2.
+template <class Real, bool ENERGY>
+__global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, View V) {
+    using Pr = Prec<Real>;
+    using Acc = typename Pr::Acc;
+    __shared__ J4<Real> sa[kTile];
+    __shared__ J4<Real> sb[kTile];
+    __shared__ long long red[4];
+    const Item it = items[blockIdx.x];
+    const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
+    const int tid = threadIdx.x;
+    const int i = it.i0 + tid;
+    const bool vi = i < N;
+    const Real sqk = Real(V.sqrt_k);
+    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
+                 cz = V.x[3 * (A + it.i0) + 2];
+    Real xi = Real(-kFarF), yi = Real(-kFarF), zi = Real(-kFarF);
+    Real qi = 0, Ri = 1, iRi = 1, sgi = 0, sei = 0;
+    if (vi) {
+        xi = Real(V.x[3 * (A + i)] - cx);
+        yi = Real(V.x[3 * (A + i) + 1] - cy);
+        zi = Real(V.x[3 * (A + i) + 2] - cz);
+        qi = Real(V.q[A + i]) * sqk;
+        Ri = Real(V.R[A + i]);
+        iRi = Real(1.0 / V.R[A + i]);
+        sgi = Real(V.sigh[P + i]);
+        sei = Real(V.sqe[P + i]);
+    }
+    const Real tau = Real(V.tau), iei = Real(V.inv_eps_in);
+    Acc fx = 0, fy = 0, fz = 0, adr = 0, egb = 0, ec = 0, elj = 0;
+    int mp = V.mt_off[it.st];
+    const int me = V.mt_off[it.st + 1];
+    int next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+    for (int j0 = 0, jt = 0; j0 < N; j0 += kTile, ++jt) {
+        __syncthreads();
+        {
+            const int j = j0 + tid;
+            J4<Real> a, b;
+            if (j < N) {
+                a.x = Real(V.x[3 * (A + j)] - cx);
+                a.y = Real(V.x[3 * (A + j) + 1] - cy);
+                a.z = Real(V.x[3 * (A + j) + 2] - cz);
+                a.w = Real(V.q[A + j]) * sqk;
+                b.x = Real(V.R[A + j]);
+                b.y = Real(1.0 / V.R[A + j]);
+                b.z = Real(V.sigh[P + j]);
+                b.w = Real(V.sqe[P + j]);
+            } else {
+                a.x = a.y = a.z = Real(kFarF);
+                a.w = 0;
+                b.x = b.y = Real(1);
+                b.z = b.w = 0;
+            }
+            sa[tid] = a;
+            sb[tid] = b;
+        }
+        __syncthreads();
+        Real px = 0, py = 0, pz = 0, pdr = 0;
+        KSum<Real> pgb, pc, plj;
+        if (jt != next) {
+#pragma unroll 2
+            for (int k = 0; k < kTile; ++k) {
+                const J4<Real> a = sa[k];
+                const J4<Real> b = sb[k];
+                const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                const Real rinv = Pr::rsqrt(r2);
+                const Real rinv2 = rinv * rinv;
+                const Real qq = qi * a.w;
+                const Real D = Real(0.25) * r2 * (iRi * b.y);
+                const Real e = Pr::expm(D);
+                const Real fi = Pr::rsqrt(r2 + (Ri * b.x) * e);
+                const Real qf3 = qq * fi * fi * fi;
+                pdr += qf3 * b.x * e * (Real(1) + D);
+                const Real sig = sgi + b.z;
+                const Real sr2 = sig * sig * rinv2;
+                const Real sr6 = sr2 * sr2 * sr2;
+                const Real ep = sei * b.w;
+                const Real fs = iei * qq * rinv * rinv2 + Real(4) * ep * sr6 * (Real(12) * sr6 - Real(6)) * rinv2
+                              - tau * qf3 * (Real(1) - Real(0.25) * e);
+                px += fs * dx;
+                py += fs * dy;
+                pz += fs * dz;
+                if (ENERGY) {
+                    pgb.add(qq * fi);
+                    pc.add(qq * rinv);
+                    plj.add(ep * sr6 * (sr6 - Real(1)));
+                }
+            }
+        } else {
+            ++mp;
+            next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+            uint32_t mex[4], mself[4];
+            tile_masks(V, P, i, vi, j0, mex, mself);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                const uint32_t me_ = mex[q4], ms_ = mself[q4];
+                for (int kk = 0; kk < 32; ++kk) {
+                    const int k = q4 * 32 + kk;
+                    const bool self = (ms_ >> kk) & 1u;
+                    const bool ex = (me_ >> kk) & 1u;
+                    const J4<Real> a = sa[k];
+                    const J4<Real> b = sb[k];
+                    const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                    Real r2 = dx * dx + dy * dy + dz * dz;
+                    r2 = self ? Real(1) : r2;
+                    const Real g = self ? Real(0) : Real(1);
+                    const Real nb = ex ? Real(0) : Real(1);
+                    const Real rinv = Pr::rsqrt(r2);
+                    const Real rinv2 = rinv * rinv;
+                    const Real qq = qi * a.w;
+                    const Real D = Real(0.25) * r2 * (iRi * b.y);
+                    const Real e = Pr::expm(D);
+                    const Real fi = Pr::rsqrt(r2 + (Ri * b.x) * e);
+                    const Real qf3 = g * qq * fi * fi * fi;
+                    pdr += qf3 * b.x * e * (Real(1) + D);
+                    const Real sig = sgi + b.z;
+                    const Real sr2 = sig * sig * rinv2;
+                    const Real sr6 = sr2 * sr2 * sr2;
+                    const Real ep = nb * sei * b.w;
+                    const Real fs = nb * iei * qq * rinv * rinv2
+                                  + Real(4) * ep * sr6 * (Real(12) * sr6 - Real(6)) * rinv2
+                                  - tau * qf3 * (Real(1) - Real(0.25) * e);
+                    px += fs * dx;
+                    py += fs * dy;
+                    pz += fs * dz;
+                    if (ENERGY) {
+                        pgb.add(g * qq * fi);
+                        pc.add(nb * qq * rinv);
+                        plj.add(ep * sr6 * (sr6 - Real(1)));
+                    }
+                }
+            }
+        }
+        Pr::add(fx, px, Real(kScaleE));
+        Pr::add(fy, py, Real(kScaleE));
+        Pr::add(fz, pz, Real(kScaleE));
+        Pr::add(adr, pdr, Real(kScaleE));
+        if (ENERGY) {
+            Pr::add(egb, pgb.value(), Real(kScaleE));
+            Pr::add(ec, pc.value(), Real(kScaleE));
+            Pr::add(elj, plj.value(), Real(kScaleE));
+        }
+    }
+    if (vi) {
+        const double q = V.q[A + i] * V.sqrt_k;
+        const double R = V.R[A + i];
+        const double dEdR = 0.5 * V.tau * (Pr::value(adr, kScaleE) + q * q / (R * R));
+        V.c[A + i] = dEdR * V.dRdpsi[A + i] * 0.5 * V.rt[P + i];
+        V.Fd[3 * (A + i)] = Pr::value(fx, kScaleE);
+        V.Fd[3 * (A + i) + 1] = Pr::value(fy, kScaleE);
+        V.Fd[3 * (A + i) + 2] = Pr::value(fz, kScaleE);
+    }
+    if (ENERGY) {
+        long long e0 = 0, e1 = 0, e2 = 0;
+        if (vi) {
+            const double q = V.q[A + i] * V.sqrt_k;
+            const double R = V.R[A + i];
+            e0 = __double2ll_rn(-0.5 * V.tau * (Pr::value(egb, kScaleE) + q * q / R) * kScaleE);
+            e1 = __double2ll_rn(0.5 * V.inv_eps_in * Pr::value(ec, kScaleE) * kScaleE);
+            e2 = __double2ll_rn(2.0 * Pr::value(elj, kScaleE) * kScaleE);
+        }
+        long long t0 = block_sum_128(e0, red);
+        long long t1 = block_sum_128(e1, red);
+        long long t2 = block_sum_128(e2, red);
+        if (tid == 0) {
+            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 0], (unsigned long long)t0);
+            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 1], (unsigned long long)t1);
+            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 2], (unsigned long long)t2);
+        }
+    }
+}
+
+// Bonded forces on atom i (system-local index li) and its owned energy
+// shares (a bond or angle is owned by its first atom).
+__device__ inline void bonded_atom(const View& V, int A, int P, int li, double F[3], double& eb,
+                                   double& ea) {
+    const double* x = V.x;
+    for (int e = V.bond_off[P + li]; e < V.bond_off[P + li + 1]; ++e) {
+        const int b = V.bond_idx[e];
+        const int ia = V.bond_ij[2 * b], ib = V.bond_ij[2 * b + 1];
+        const int o = (ia == li) ? ib : ia;
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + li) + c] - x[3 * (A + o) + c];
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double dr = r - V.bond_r0[b];
+        const double g = 2.0 * V.bond_k[b] * dr / r;
+        for (int c = 0; c < 3; ++c) F[c] -= g * d[c];
+        if (ia == li) eb += V.bond_k[b] * dr * dr;
+    }
+    for (int e = V.ang_off[P + li]; e < V.ang_off[P + li + 1]; ++e) {
+        const int a = V.ang_idx[e];
+        const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
+        double u[3], v[3];
+        for (int c = 0; c < 3; ++c) {
+            u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
+            v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
+        }
+        const double ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double rv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (ru * rv);
+        cs = fmin(1.0, fmax(-1.0, cs));
+        const double th = acos(cs);
+        const double dth = th - V.ang_t0[a];
+        const double k = -2.0 * V.ang_k[a] * dth / sqrt(fmax(1e-300, 1.0 - cs * cs)); // dE/dcos
+        double gi[3], gk[3];
+        for (int c = 0; c < 3; ++c) {
+            gi[c] = k * (v[c] / (ru * rv) - cs * u[c] / (ru * ru));
+            gk[c] = k * (u[c] / (ru * rv) - cs * v[c] / (rv * rv));
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (li == ia) F[c] -= gi[c];
+            if (li == ic) F[c] -= gk[c];
+            if (li == ib) F[c] += gi[c] + gk[c];
+        }
+        if (ia == li) ea += V.ang_k[a] * dth * dth;
+    }
+}
+
+// ------------------------------------------ pass 3: chain rule through Born radii
+// F_i -= sum_j (c_i dH(r; rt_i, s_j)/dr + c_j dH(r; rt_j, s_i)/dr) (x_i - x_j)/r,
+// then the direct pair force and the bonded terms are added: F is the total force.
+template <class Real, bool ENERGY>
+__global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items, View V) {
+    using Pr = Prec<Real>;
+    using Acc = typename Pr::Acc;
+    __shared__ J4<Real> sa[kTile];
+    __shared__ J2<Real> sb[kTile];
+    __shared__ long long red[4];
+    const Item it = items[blockIdx.x];
+    const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
+    const int tid = threadIdx.x;
+    const int i = it.i0 + tid;
+    const bool vi = i < N;
+    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
+                 cz = V.x[3 * (A + it.i0) + 2];
+    Real xi = Real(-kFarF), yi = Real(-kFarF), zi = Real(-kFarF), ci = 0, si = 0, rti = 1;
+    if (vi) {
+        xi = Real(V.x[3 * (A + i)] - cx);
+        yi = Real(V.x[3 * (A + i) + 1] - cy);
+        zi = Real(V.x[3 * (A + i) + 2] - cz);
+        ci = Real(V.c[A + i]);
+        si = Real(V.sc[P + i]);
+        rti = Real(V.rt[P + i]);
+    }
+    Acc fx = 0, fy = 0, fz = 0;
+    int mp = V.mt_off[it.st];
+    const int me = V.mt_off[it.st + 1];
+    int next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+    for (int j0 = 0, jt = 0; j0 < N; j0 += kTile, ++jt) {
+        __syncthreads();
+        {
+            const int j = j0 + tid;
+            J4<Real> a;
+            J2<Real> b;
+            if (j < N) {
+                a.x = Real(V.x[3 * (A + j)] - cx);
+                a.y = Real(V.x[3 * (A + j) + 1] - cy);
+                a.z = Real(V.x[3 * (A + j) + 2] - cz);
+                a.w = Real(V.c[A + j]);
+                b.x = Real(V.sc[P + j]);
+                b.y = Real(V.rt[P + j]);
+            } else {
+                a.x = a.y = a.z = Real(kFarF);
+                a.w = 0;
+                b.x = 0;
+                b.y = 1;
+            }
+            sa[tid] = a;
+            sb[tid] = b;
+        }
+        __syncthreads();
+        Real px = 0, py = 0, pz = 0;
+        if (jt != next) {
+#pragma unroll 4
+            for (int k = 0; k < kTile; ++k) {
+                const J4<Real> a = sa[k];
+                const J2<Real> b = sb[k];
+                const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                const Real rinv = Pr::rsqrt(r2);
+                const Real r = r2 * rinv;
+                const Real g = ci * hct_dr(r, rinv, rti, b.x) + a.w * hct_dr(r, rinv, b.y, si);
+                const Real t = -g * rinv;
+                px += t * dx;
+                py += t * dy;
+                pz += t * dz;
+            }
+        } else {
+            ++mp;
+            next = mp < me ? V.mt_list[mp] : 0x7fffffff;
+            const int dself = i - j0;
+            for (int k = 0; k < kTile; ++k) {
+                const J4<Real> a = sa[k];
+                const J2<Real> b = sb[k];
+                const bool self = (k == dself);
+                const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                Real r2 = dx * dx + dy * dy + dz * dz;
+                r2 = self ? Real(1) : r2;
+                const Real rinv = Pr::rsqrt(r2);
+                const Real r = r2 * rinv;
+                const Real g = ci * hct_dr(r, rinv, rti, b.x) + a.w * hct_dr(r, rinv, b.y, si);
+                const Real t = self ? Real(0) : -g * rinv;
+                px += t * dx;
+                py += t * dy;
+                pz += t * dz;
+            }
+        }
+        Pr::add(fx, px, Real(kScaleE));
+        Pr::add(fy, py, Real(kScaleE));
+        Pr::add(fz, pz, Real(kScaleE));
+    }
+    double eb = 0.0, ea = 0.0;
+    if (vi) {
+        double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE),
+                       V.Fd[3 * (A + i) + 1] + Pr::value(fy, kScaleE),
+                       V.Fd[3 * (A + i) + 2] + Pr::value(fz, kScaleE)};
+        bonded_atom(V, A, P, i, F, eb, ea);
+        V.F[3 * (A + i)] = F[0];
+        V.F[3 * (A + i) + 1] = F[1];
+        V.F[3 * (A + i) + 2] = F[2];
+        if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(V.status, 1);
+    }
+    if (ENERGY) {
+        long long t0 = block_sum_128(__double2ll_rn(eb * kScaleE), red);
+        long long t1 = block_sum_128(__double2ll_rn(ea * kScaleE), red);
+        if (tid == 0) {
+            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 3], (unsigned long long)t0);
+            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 4], (unsigned long long)t1);
+        }
+    }
+}
+
+// ------------------------------------------------------------ Langevin step
+// v' = [(1 - g dt/2) v + dt A F/m + sqrt(2 g kB T A dt/m) z] / (1 + g dt/2),
+// x' = x + dt v', with T the temperature of the walker's current slot and z
+// three normals from one Philox draw (Box-Muller on words (0,1) and (2,3)).
+template <class Real>
+__device__ inline void normals3(uint64_t seed, uint32_t idx, uint32_t stream, uint64_t step,
+                                Real z[3]);
+
+template <>
+__device__ inline void normals3<double>(uint64_t seed, uint32_t idx, uint32_t stream,
+                                        uint64_t step, double z[3]) {
+    U4 u = draw(seed, idx, stream, step, kRngLangevin);
+    const double r0 = sqrt(-2.0 * log(unit_open(u.a)));
+    const double r1 = sqrt(-2.0 * log(unit_open(u.c)));
+    double sn, cs;
+    sincospi(2.0 * unit_open(u.b), &sn, &cs);
+    z[0] = r0 * cs;
+    z[1] = r0 * sn;
+    z[2] = r1 * cospi(2.0 * unit_open(u.d));
+}
+
+template <>
+__device__ inline void normals3<float>(uint64_t seed, uint32_t idx, uint32_t stream,
+                                       uint64_t step, float z[3]) {
+    U4 u = draw(seed, idx, stream, step, kRngLangevin);
+    const float r0 = sqrtf(-2.0f * logf((float)unit_open(u.a)));
+    const float r1 = sqrtf(-2.0f * logf((float)unit_open(u.c)));
+    float sn, cs;
+    sincospif(2.0f * (float)unit_open(u.b), &sn, &cs);
+    z[0] = r0 * cs;
+    z[1] = r0 * sn;
+    z[2] = r1 * cospif(2.0f * (float)unit_open(u.d));
+}
+
+template <class Real>
+__global__ void k_langevin(View V, int s_off, int a0, int n) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int a = a0 + l;
+    const int w = V.a_walker[a];
+    const int li = a - V.w_off[w];
+    const int P = V.sys_poff[V.w_sys[w]];
+    const uint64_t t = (uint64_t)(*V.step + s_off);
+    const int slot = V.slot_of[w];
+    const double T = V.gT[slot / (V.nE * V.npH)];
+    Real z[3];
+    normals3<Real>(V.seed, (uint32_t)li, (uint32_t)w, t, z);
+    const double m = V.mass[P + li];
+    const double sd = sqrt(2.0 * V.gamma_ln * kBoltzmann * T * kAccel * V.dt / m);
+    const double c1 = 1.0 - 0.5 * V.gamma_ln * V.dt, c2 = 1.0 / (1.0 + 0.5 * V.gamma_ln * V.dt);
+    const double vs = V.vscale[w];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double vn = (c1 * (V.v[3 * a + c] * vs) + V.dt * kAccel * V.F[3 * a + c] / m + sd * (double)z[c]) * c2;
+        V.v[3 * a + c] = vn;
+        const double xn = V.x[3 * a + c] + V.dt * vn;
+        V.x[3 * a + c] = xn;
+        ok = ok && isfinite(xn);
+    }
+    if (!ok) atomicOr(V.status, 2);
+}
+
+// velocities *= vscale[walker] (a stand-alone T exchange)
+__global__ void k_vscale(View V) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= V.total_atoms) return;
+    const double s = V.vscale[V.a_walker[a]];
+    for (int c = 0; c < 3; ++c) V.v[3 * a + c] *= s;
+}
+
+__global__ void k_vscale_reset(View V) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < V.W) V.vscale[w] = 1.0;
+}
+
+__global__ void k_tick(long long* step, long long n) { *step += n; }
+
+} // namespace cph

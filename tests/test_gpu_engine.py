@@ -1,0 +1,241 @@
+"""GPU parity of the engine's hot path against the FP64 oracle, through the C ABI.
+
+Bars (FP32 mode): force RMS relative error <= 1e-5 per walker, every energy
+term within 1e-6 relative, Born radii within 1e-6 relative.  FP64 mode: 1e-10.
+Sizes span several 128-atom tiles with ragged tails, several systems batched
+in one launch, and the full 384-walker 3D grid (sampled walkers)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_07726_gb300 import build, cphremd, synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_RMS = 1e-5
+ENERGY_REL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def _grid_for(systems, per_system=2):
+    sos = np.repeat(np.arange(len(systems)), per_system).astype(np.int32)
+    W = len(sos)
+    return synth.Grid(np.linspace(-0.3, -0.1, W), np.array([7.0]), np.array([300.0]), sos,
+                      order=("E",))
+
+
+def _compare_walker(eng, w, sysd, x, q, tol_f, tol_e, tol_r):
+    o = oracle.OSystem(sysd)
+    terms, Fo, Ro, _ = oracle.energy(o, x, q, oracle.GBParams())
+    sl = eng.walker_slice(w)
+    F = eng.forces()[sl]
+    R = eng.born_radii()[sl]
+    E = eng.energies()[w]
+    rms = np.sqrt(((F - Fo) ** 2).mean()) / np.sqrt((Fo ** 2).mean())
+    assert rms <= tol_f, f"walker {w}: force rms rel {rms:.3e}"
+    np.testing.assert_allclose(R, Ro, rtol=tol_r)
+    for t in range(6):
+        assert abs(E[t] - terms[t]) <= tol_e * abs(terms[t]) + 1e-9, (t, E[t], terms[t])
+    return rms
+
+
+@pytest.fixture(scope="module")
+def ragged_systems():
+    return [synth.make_system(700, 21, n_ph=3, ph_atoms=(6, 12), ph_states=(2, 4)),
+            synth.make_system(130, 22, n_ph=1),
+            synth.make_system(40, 23, n_ph=1, redox_atoms=8)]
+
+
+@pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, 1e-6),
+                                           (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11)])
+def test_evaluate_matches_oracle_ragged_batch(ragged_systems, prec, tf, te, tr):
+    grid = _grid_for(ragged_systems)
+    eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec)
+    eng.evaluate()
+    for w in range(grid.n_slots):
+        s = ragged_systems[grid.system_of_slot[w]]
+        _compare_walker(eng, w, s, s.x, s.q, tf, te, tr)
+
+
+def test_batched_equals_per_replica_bitwise(ragged_systems):
+    grid = _grid_for(ragged_systems)
+    a = cphremd.init_system(ragged_systems, grid, seed=3)
+    b = cphremd.init_system(ragged_systems, grid, seed=3)
+    b.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
+    a.run(25)
+    b.run(25)
+    for get in ("positions", "velocities", "forces", "born_radii", "site_states",
+                "condition_map"):
+        np.testing.assert_array_equal(getattr(a, get)(), getattr(b, get)())
+
+
+def test_runs_are_deterministic(ragged_systems):
+    grid = _grid_for(ragged_systems)
+    a = cphremd.init_system(ragged_systems, grid, seed=5)
+    b = cphremd.init_system(ragged_systems, grid, seed=5)
+    a.run(30)
+    b.run(30)
+    np.testing.assert_array_equal(a.positions(), b.positions())
+    np.testing.assert_array_equal(a.energies(), b.energies())
+
+
+def test_graph_replay_equals_direct_steps(ragged_systems):
+    """cph_run replays a captured CUDA graph for whole schedule periods; the
+    same steps launched one by one give identical results."""
+    grid = _grid_for(ragged_systems)
+    a = cphremd.init_system(ragged_systems, grid, seed=9, mc_ph_every=5, mc_redox_every=5,
+                            exchange_every=10)
+    b = cphremd.init_system(ragged_systems, grid, seed=9, mc_ph_every=5, mc_redox_every=5,
+                            exchange_every=10)
+    a.run(41)            # step 0 direct, then 4 graph periods of 10
+    for _ in range(41):  # one step per call: never a whole period
+        b.run(1)
+    for get in ("positions", "velocities", "site_states", "condition_map", "accept_stats"):
+        np.testing.assert_array_equal(getattr(a, get)(), getattr(b, get)())
+
+
+def test_full_3d_grid_sampled_walkers():
+    """The 384-walker E x T x pH grid over 500/2000/8000-atom systems in one
+    batched launch: one walker of each system against the oracle."""
+    systems, grid = synth.config_c4()
+    eng = cphremd.init_system(systems, grid, seed=4)
+    eng.evaluate()
+    for w in (0, 2 * 64 + 5, 5 * 64 + 63):
+        s = systems[grid.system_of_slot[w]]
+        _compare_walker(eng, w, s, s.x, s.q, FORCE_RMS, ENERGY_REL, 1e-6)
+
+
+def test_reference_energies_match_oracle(ragged_systems):
+    grid = _grid_for(ragged_systems)
+    eng = cphremd.init_system(ragged_systems, grid, seed=1)
+    got = eng.reference_energies()
+    want = np.concatenate([np.concatenate(oracle.reference_energies(oracle.OSystem(s), s,
+                                                                    oracle.GBParams()))
+                           for s in ragged_systems])
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-11)
+
+
+def _band(x, prec):
+    # decisions closer to the threshold than the exponent's error bound are
+    # logged, not failed: FP64 1e-9 max(1,|x|); FP32 2e-4 max(1,|x|) (see DESIGN)
+    return (1e-9 if prec == cphremd.PREC_FP64 else 2e-4) * max(1.0, abs(x))
+
+
+@pytest.mark.parametrize("prec", [cphremd.PREC_FP32, cphremd.PREC_FP64])
+def test_mc_sweep_matches_oracle(prec):
+    """One protonation + redox sweep on the 2400-atom system with 20 pH sites:
+    dU against the oracle's full recomputation, identical decisions."""
+    systems, grid = synth.config_c3()
+    grid = synth.Grid(grid.E[[0, 3, 5, 7]], grid.pH[[0, 4]], grid.T, np.zeros(8, np.int32),
+                      order=("E", "pH"))
+    eng = cphremd.init_system(systems, grid, seed=11, precision=prec)
+    eng.set_step(10)
+    eng.mc_titrate(cphremd.MC_BOTH)
+    recs = eng.mc_records()
+    W = oracle.Walkers(systems, grid, seed=11)
+    for w in range(grid.n_slots):
+        oracle.mc_sweep(W, w, "ph", 10)
+        oracle.mc_sweep(W, w, "redox", 10)
+    by_w = {}
+    for (w, k, a, b, dU, x, lnu, acc) in W.mc_log:
+        by_w.setdefault(w, []).append((k, a, b, dU, x, lnu, acc))
+    n_checked = n_band = 0
+    so = eng.site_offsets
+    for w, lst in by_w.items():
+        for (k, a, b, dU, x, lnu, acc) in lst:
+            r = recs[so[w] + k]
+            assert (r.walker, r.site, r.frm, r.to) == (w, k, a, b)
+            tol = (1e-9 if prec == cphremd.PREC_FP64 else 2e-6) * max(1.0, abs(dU)) + \
+                  (1e-9 if prec == cphremd.PREC_FP64 else 1e-4)
+            assert abs(r.dU - dU) <= tol, (w, k, r.dU, dU)
+            assert r.lnu == lnu
+            n_checked += 1
+            if abs(lnu - x) <= _band(x, prec):
+                n_band += 1
+                break  # later sites of this walker see different charges
+            assert bool(r.accepted) == bool(acc), (w, k, r.x, x, lnu)
+    assert n_checked >= 100 and n_band <= 2
+
+
+def test_exchange_attempts_match_oracle():
+    """pH and E exchanges (integer counts: exact exponents) and T exchanges
+    (energies from the engine vs the oracle) on an 4 x 2 x 3 grid."""
+    s = synth.make_system(300, 31, n_ph=6, ph_atoms=(6, 8), ph_states=(2, 3))
+    grid = synth.Grid(np.linspace(-0.28, -0.16, 4), np.array([4.0, 6.0]),
+                      np.array([300.0, 330.0, 363.0]), np.zeros(24, np.int32),
+                      order=("E", "pH", "T"))
+    eng = cphremd.init_system([s], grid, seed=13, precision=cphremd.PREC_FP64)
+    rng = np.random.default_rng(0)
+    so = eng.site_offsets
+    states = np.zeros(int(so[-1]), np.int32)
+    for w in range(24):
+        for k, st in enumerate(s.sites):
+            states[so[w] + k] = rng.integers(len(st.q))
+    eng.set_site_states(states)
+    x = eng.positions()
+    for w in range(24):
+        x[eng.walker_slice(w)] += rng.normal(0, 0.05, size=(s.n, 3))
+    eng.set_positions(x)
+    W = oracle.Walkers([s], grid, seed=13)
+    for w in range(24):
+        W.state[w] = states[so[w]:so[w + 1]].astype(np.int64)
+        q = s.q.copy()
+        for k, st in enumerate(s.sites):
+            q[st.atoms] = st.q[W.state[w][k]]
+        W.q[w] = q
+        W.x[w] = np.ascontiguousarray(x[eng.walker_slice(w)])
+        W.U[w] = oracle.energy(W.osys[0], W.x[w], q, forces=False)[0][5]
+    eng.set_step(100)
+    seen = 0
+    for dim in ("E", "pH", "T", "E", "pH", "T"):
+        eng.attempt_exchanges(cphremd.DIM_NAMES[dim])
+        recs = [r for r in eng.exchange_records() if r.accepted >= 0]
+        n0 = len(W.ex_log)
+        oracle.exchange_attempt(W, dim, 100)
+        ol = W.ex_log[n0:]
+        assert len(recs) == len(ol)
+        key = {(e[1], e[2]): e for e in ol}
+        for r in recs:
+            e = key[(r.slot_lo, r.slot_hi)]
+            assert (r.walker_lo, r.walker_hi) == (e[3], e[4])
+            assert r.lnu == e[6]
+            assert abs(r.x - e[5]) <= 1e-9 * max(1.0, abs(e[5]))
+            assert bool(r.accepted) == bool(e[7])
+            seen += 1
+        np.testing.assert_array_equal(eng.condition_map(), W.slot_of)
+    assert seen > 20
+
+
+def test_fp64_whole_schedule_matches_oracle():
+    """160-atom system, 8 walkers along E, FP64 mode: 120 steps of the full
+    schedule (MC every 10, exchange every 20) agree with the oracle to 1e-9 A."""
+    systems, grid = synth.config_c2()
+    eng = cphremd.init_system(systems, grid, seed=2, precision=cphremd.PREC_FP64,
+                              mc_ph_every=10, mc_redox_every=10, exchange_every=20)
+    W = oracle.Walkers(systems, grid, seed=2, mc_ph=10, mc_redox=10, exchange_every=20)
+    n = 120
+    eng.run(n)
+    oracle.run_schedule(W, n)
+    x = eng.positions()
+    for w in range(grid.n_slots):
+        np.testing.assert_allclose(x[eng.walker_slice(w)], W.x[w], rtol=0, atol=1e-9)
+    np.testing.assert_array_equal(eng.condition_map(), W.slot_of)
+    np.testing.assert_array_equal(eng.site_states(), np.concatenate(W.state))
+
+
+def test_fp32_langevin_step_matches_oracle():
+    """One MD step in FP32 mode from a shared state: positions to 1e-9 A."""
+    s = synth.make_system(260, 41, n_ph=1)
+    grid = synth.Grid(np.array([-0.2]), np.array([7.0]), np.array([310.0]), np.zeros(1, np.int32))
+    eng = cphremd.init_system([s], grid, seed=17)
+    eng.set_step(7)
+    eng.step_replicas(1)
+    W = oracle.Walkers([s], grid, seed=17)
+    W.t = 7
+    oracle.run_schedule(W, 1)
+    np.testing.assert_allclose(eng.positions(), W.x[0], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(eng.velocities(), W.v[0], rtol=2e-6, atol=2e-6)
