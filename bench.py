@@ -251,6 +251,11 @@ def run_gpu(args):
     step_peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(
         sum(v[0] for v in PASS_COST.values()), sum(v[1] for v in PASS_COST.values())) / 1e9
 
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "value": value, "ms_per_step": 1e3 * t_max / args.steps,
+                              "pass_ms": [float(x) for x in pass_ms], "clocks": clocks}), flush=True)
+        return
     # per-replica launches of the same steps
     pr = cphremd.init_system(systems, grid, seed=seed)
     pr.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
@@ -345,6 +350,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true",
+                    help="batched timing only (no per-replica, e2e or CPU legs); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -148,7 +148,7 @@ __device__ __forceinline__ HctClosed hct_closed(float r, float rt, float s) {
     HctClosed h;
     h.iL = U * iLU;
     h.iU = L * iLU;
-    h.lg = __logf(L * h.iU);
+    h.lg = logf(L * h.iU); // accurate log: near pairs dominate psi, keep them to ~1 ulp
     return h;
 }
 

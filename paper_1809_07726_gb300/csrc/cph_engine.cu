@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "cph_kernels.cuh"
+#include "cph_sym.cuh"
 
 namespace cph {
 
@@ -416,6 +417,10 @@ struct cph_engine {
     int n_items = 0;
     std::vector<int> item_w_off; // per-walker item ranges (items grouped by walker, per-replica mode)
     Item* d_items_by_w = nullptr;
+    SymItem* d_sym = nullptr;          // symmetric FP32 items, largest system first
+    SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
+    int n_sym = 0;
+    std::vector<int> sym_w_off;
     int ex_cap = 0;
     int mc_kinds_last = 0;
     cudaStream_t cap_stream = nullptr;
@@ -556,23 +561,70 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
     return CPH_OK;
 }
 
+// FP32: symmetric GB and chain passes (each unordered pair once), then the
+// per-atom finishing kernels; FP64: ordered passes (bonded terms in k_chain).
+int launch_sym_pair(cph_engine* E, const SymItem* items, int n, bool energy, int pass,
+                    cudaStream_t st) {
+    if (n <= 0) return CPH_OK;
+    if (pass == 0) k_born_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
+    else if (pass == 2) k_chain_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
+    else if (energy) k_gb_sym<true><<<n, kSymThreads, 0, st>>>(items, E->V);
+    else k_gb_sym<false><<<n, kSymThreads, 0, st>>>(items, E->V);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+int launch_atoms(cph_engine* E, int which, bool energy, int a0, int n, cudaStream_t st) {
+    const int bs = 256, g = (n + bs - 1) / bs;
+    if (n <= 0) return CPH_OK;
+    if (which == 2) {
+        k_fin_born<<<g, bs, 0, st>>>(E->V, a0, n, energy ? 1 : 0);
+    } else if (which == 0) {
+        if (energy) k_fin_c<true><<<g, bs, 0, st>>>(E->V, a0, n);
+        else k_fin_c<false><<<g, bs, 0, st>>>(E->V, a0, n);
+    } else {
+        if (energy) k_final_forces<true><<<g, bs, 0, st>>>(E->V, a0, n);
+        else k_final_forces<false><<<g, bs, 0, st>>>(E->V, a0, n);
+    }
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+// pass: 0 born, 1 GB (+ finish), 2 chain (+ finish with bonded terms)
+int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
+    const bool fp32 = E->precision == CPH_PREC_FP32;
+    const int W = E->V.W;
+    const int fin = pass == 0 ? 2 : (pass == 1 ? 0 : 1);
+    if (E->launch_mode == 0) {
+        if (!fp32) {
+            if (pass == 0) return launch_born(E, E->d_items, E->n_items, energy, st);
+            return pass == 1 ? launch_gb(E, E->d_items, E->n_items, energy, st)
+                             : launch_chain(E, E->d_items, E->n_items, energy, st);
+        }
+        TRY(launch_sym_pair(E, E->d_sym, E->n_sym, energy, pass, st));
+        return launch_atoms(E, fin, energy, 0, E->V.total_atoms, st);
+    }
+    for (int w = 0; w < W; ++w) {
+        const Item* it = E->d_items_by_w + E->item_w_off[w];
+        const int ni = E->item_w_off[w + 1] - E->item_w_off[w];
+        if (!fp32) {
+            if (pass == 0) TRY(launch_born(E, it, ni, energy, st));
+            else TRY(pass == 1 ? launch_gb(E, it, ni, energy, st) : launch_chain(E, it, ni, energy, st));
+        } else {
+            TRY(launch_sym_pair(E, E->d_sym_by_w + E->sym_w_off[w], E->sym_w_off[w + 1] - E->sym_w_off[w],
+                                energy, pass, st));
+            TRY(launch_atoms(E, fin, energy, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], st));
+        }
+    }
+    return CPH_OK;
+}
+
 int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, int s_off,
                   int mc_kinds) {
-    if (E->launch_mode == 0) {
-        TRY(launch_born(E, E->d_items, E->n_items, energy, st));
-        if (mc_between && mc_kinds) TRY(launch_mc(E, mc_kinds, s_off, st));
-        TRY(launch_gb(E, E->d_items, E->n_items, energy, st));
-        TRY(launch_chain(E, E->d_items, E->n_items, energy, st));
-    } else {
-        const int W = E->V.W;
-        for (int w = 0; w < W; ++w)
-            TRY(launch_born(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
-        if (mc_between && mc_kinds) TRY(launch_mc(E, mc_kinds, s_off, st));
-        for (int w = 0; w < W; ++w)
-            TRY(launch_gb(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
-        for (int w = 0; w < W; ++w)
-            TRY(launch_chain(E, E->d_items_by_w + E->item_w_off[w], E->item_w_off[w + 1] - E->item_w_off[w], energy, st));
-    }
+    TRY(launch_pass(E, 0, energy, st));
+    if (mc_between && mc_kinds) TRY(launch_mc(E, mc_kinds, s_off, st));
+    TRY(launch_pass(E, 1, energy, st));
+    TRY(launch_pass(E, 2, energy, st));
     return CPH_OK;
 }
 
@@ -701,6 +753,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         site_np, site_ne, site_sys, site_init;
     std::vector<double> site_q, site_ref;
     std::vector<int> mt_off(1, 0), mt_list, sys_st_off(n_sys + 1, 0);
+    std::vector<int> smt_off(1, 0), smt_list, sys_sst_off(n_sys + 1, 0);
     const double off = p->gb.offset;
     for (int s = 0; s < n_sys; ++s) {
         const cph_system_desc& d = sys[s];
@@ -800,6 +853,20 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
             for (int jt : tiles) mt_list.push_back(jt);
             mt_off.push_back((int)mt_list.size());
         }
+        // symmetric passes: masked 32-atom j-tiles per 256-atom i-tile (diagonal
+        // block, partners beyond j > i that are excluded)
+        const int nts = (N + kSymI - 1) / kSymI;
+        sys_sst_off[s + 1] = sys_sst_off[s] + nts;
+        for (int it = 0; it < nts; ++it) {
+            std::set<int> tiles;
+            const int i0 = it * kSymI, i1 = std::min(N, i0 + kSymI);
+            for (int jt = i0 / kSymJ; jt * kSymJ < i1; ++jt) tiles.insert(jt);
+            for (int i = i0; i < i1; ++i)
+                for (int j : ex[i])
+                    if (j > i) tiles.insert(j / kSymJ);
+            for (int jt : tiles) smt_list.push_back(jt);
+            smt_off.push_back((int)smt_list.size());
+        }
         // sites
         if (d.n_sites < 0 || (d.n_sites > 0 && !d.sites)) return fail(nullptr, CPH_E_INVALID, "system %d: bad site list", s);
         std::vector<char> used(N, 0);
@@ -879,6 +946,22 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
         return sys_n[w_sys[a.w]] > sys_n[w_sys[b.w]];
     });
+    std::vector<SymItem> sym, sym_by_w;
+    std::vector<int> sym_w_off(W + 1, 0);
+    for (int w = 0; w < W; ++w) {
+        const int s = w_sys[w], N = sys_n[s];
+        const int njt = (N + kSymJ - 1) / kSymJ;
+        for (int it = 0; it * kSymI < N; ++it) {
+            const int i0 = it * kSymI;
+            for (int jt = i0 / kSymJ; jt < njt; jt += kSymChunk)
+                sym_by_w.push_back(SymItem{w, i0, jt, std::min(njt, jt + kSymChunk), sys_sst_off[s] + it, 0});
+        }
+        sym_w_off[w + 1] = (int)sym_by_w.size();
+    }
+    sym = sym_by_w;
+    std::stable_sort(sym.begin(), sym.end(), [](const SymItem& a, const SymItem& b) {
+        return (a.jt1 - a.jt0) > (b.jt1 - b.jt0);
+    });
 
     cph_engine* E = new cph_engine();
     std::unique_ptr<cph_engine> guard(E);
@@ -897,6 +980,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     E->n_site_states = (int)site_np.size();
     E->item_w_off = item_w_off;
     E->n_items = (int)items.size();
+    E->n_sym = (int)sym.size();
+    E->sym_w_off = sym_w_off;
     E->graph_period = schedule_period(E);
     View& V = E->V;
     V.W = W;
@@ -931,6 +1016,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(upload(E, ang_t0, &dd)); V.ang_t0 = dd;
     TRY(upload(E, mt_off, &d)); V.mt_off = d;
     TRY(upload(E, mt_list, &d)); V.mt_list = d;
+    TRY(upload(E, smt_off, &d)); V.smt_off = d;
+    TRY(upload(E, smt_list, &d)); V.smt_list = d;
     TRY(upload(E, site_kind, &d)); V.site_kind = d;
     TRY(upload(E, site_nat, &d)); V.site_nat = d;
     TRY(upload(E, site_aoff, &d)); V.site_aoff = d;
@@ -952,6 +1039,10 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(alloc0(E, total, &dd)); V.c = dd;
     TRY(alloc0(E, 3 * (size_t)total, &dd)); V.Fd = dd;
     TRY(alloc0(E, 3 * (size_t)total, &dd)); V.F = dd;
+    long long* dfx;
+    TRY(alloc0(E, 3 * (size_t)total, &dfx)); V.Ffix = dfx;
+    TRY(alloc0(E, (size_t)total, &dfx)); V.dRfix = dfx;
+    TRY(alloc0(E, (size_t)total, &dfx)); V.Hfix = dfx;
     long long* dl;
     TRY(alloc0(E, (size_t)W * kEAcc, &dl)); V.eacc = dl;
     std::vector<int> ident(W);
@@ -1001,10 +1092,20 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.offset = p->gb.offset;
     V.dt = p->dt;
     V.gamma_ln = p->gamma_ln;
+    {
+        double smax = 0.0, rtmax = 0.0;
+        for (double v : sc) smax = std::max(smax, v);
+        for (double v : rt) rtmax = std::max(rtmax, v);
+        const double rfar = std::max(smax / (double)kHctXmax, smax + rtmax) * (1.0 + 1e-5);
+        V.rfar2 = (float)(rfar * rfar);
+    }
     V.seed = seed;
     Item* di;
     TRY(upload(E, items, &di)); E->d_items = di;
     TRY(upload(E, items_by_w, &di)); E->d_items_by_w = di;
+    SymItem* dsi;
+    TRY(upload(E, sym, &dsi)); E->d_sym = dsi;
+    TRY(upload(E, sym_by_w, &dsi)); E->d_sym_by_w = dsi;
 
     // reference energies of every (site, state)
     if (!site_np.empty()) {
@@ -1067,23 +1168,9 @@ int cph_time_passes(cph_engine* e, int reps, double* ms, void* stream) {
     double acc[3] = {0, 0, 0};
     int rc = CPH_OK;
     for (int r = 0; r < reps && rc == CPH_OK; ++r) {
-        cudaEventRecord(ev[0], st);
-        if (e->launch_mode == 0) {
-            rc = launch_born(e, e->d_items, e->n_items, false, st);
-            cudaEventRecord(ev[1], st);
-            if (rc == CPH_OK) rc = launch_gb(e, e->d_items, e->n_items, false, st);
-            cudaEventRecord(ev[2], st);
-            if (rc == CPH_OK) rc = launch_chain(e, e->d_items, e->n_items, false, st);
-        } else {
-            const int W = e->V.W;
-            for (int w = 0; w < W && rc == CPH_OK; ++w)
-                rc = launch_born(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
-            cudaEventRecord(ev[1], st);
-            for (int w = 0; w < W && rc == CPH_OK; ++w)
-                rc = launch_gb(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
-            cudaEventRecord(ev[2], st);
-            for (int w = 0; w < W && rc == CPH_OK; ++w)
-                rc = launch_chain(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st);
+        for (int p = 0; p < 3 && rc == CPH_OK; ++p) {
+            cudaEventRecord(ev[p], st);
+            rc = launch_pass(e, p, false, st);
         }
         cudaEventRecord(ev[3], st);
         cudaError_t ce = cudaEventSynchronize(ev[3]);
@@ -1112,10 +1199,7 @@ int cph_step_replicas(cph_engine* e, int64_t n_steps, void* stream) {
 int cph_mc_titrate(cph_engine* e, int kind, void* stream) {
     if (!e || kind < 1 || kind > 3) return fail(e, CPH_E_INVALID, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    if (e->launch_mode == 0) TRY(launch_born(e, e->d_items, e->n_items, false, st));
-    else
-        for (int w = 0; w < e->V.W; ++w)
-            TRY(launch_born(e, e->d_items_by_w + e->item_w_off[w], e->item_w_off[w + 1] - e->item_w_off[w], false, st));
+    TRY(launch_pass(e, 0, false, st));
     TRY(launch_mc(e, kind, 0, st));
     return CPH_OK;
 }

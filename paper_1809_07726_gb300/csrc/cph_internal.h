@@ -9,6 +9,7 @@
 //   rho, rt, sc      double [system atoms]       intrinsic radius, rho - offset, screen*rt
 //   sigh, sqe, mass  double [system atoms]       sigma/2, sqrt(eps), mass
 //   eacc             int64  [W * 5]              fixed-point (2^32) energy terms per walker
+//   Ffix, dRfix      int64  [3N], [N]            fixed-point (2^32) pair-force and dE/dR sums
 #pragma once
 #include <cstdint>
 #include "../../include/cphremd.h"
@@ -47,6 +48,8 @@ struct View {
     const double *site_ref, *site_uref;
     // dynamic state
     double *x, *v, *q, *psi, *R, *dRdpsi, *c, *Fd, *F;
+    long long *Ffix, *dRfix, *Hfix; // FP32 symmetric passes: fixed-point force, dE/dR, descreening sums
+    const int *smt_off, *smt_list; // masked 32-atom j-tiles per (system, 256-atom i-tile)
     long long* eacc;
     int *slot_of, *walker_at, *site_state;
     double* vscale;
@@ -63,6 +66,7 @@ struct View {
     int order[3];
     // parameters
     double tau, inv_eps_in, sqrt_k, alpha, beta, gamma, offset, dt, gamma_ln;
+    float rfar2; // pairs with r^2 >= rfar2 are in the series regime in both directions
     unsigned long long seed;
 };
 

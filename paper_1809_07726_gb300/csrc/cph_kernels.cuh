@@ -152,6 +152,10 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         const double R = 1.0 / (1.0 / rt - th / rho);
         V.psi[A + i] = psi;
         V.R[A + i] = R;
+        V.Ffix[3 * (A + i)] = 0;
+        V.Ffix[3 * (A + i) + 1] = 0;
+        V.Ffix[3 * (A + i) + 2] = 0;
+        V.dRfix[A + i] = 0;
         V.dRdpsi[A + i] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) / rho;
     }
 }
