@@ -291,6 +291,36 @@ int cph_gb_energy_backward(int n_rep, int n, const float* x, const float* q,
                            const double* dE, float* dx, float* dq, float* drho,
                            void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- GB energy without any device allocation
+ *
+ * Same result as cph_gb_energy, for callers that cannot allocate device
+ * memory themselves: plug-ins that run inside a host program which owns the
+ * whole device-memory budget, and loops in which the device-wide
+ * synchronisation of cudaMalloc / cudaFree is not acceptable.  The caller
+ * passes only the inputs and the output (same layout as cph_gb_energy); the
+ * scratch lives in a fixed array inside this library.  The paper has no
+ * counterpart: this is a deployment variant of the GB energy, not part of the
+ * method.
+ *
+ * Scratch: a file-scope device array of CPH_GB_NOALLOC_SCRATCH_BYTES (12 MiB),
+ * reserved on every GPU where the library's kernels are loaded and held until
+ * the process exits.  A call needs cph_gb_workspace_bytes(n_rep, n) bytes of
+ * it (about 72 bytes per replica-atom: roughly 170,000 replica-atoms, e.g. 20
+ * replicas of an 8000-atom system); a larger request returns CPH_E_INVALID
+ * and launches nothing.
+ * Set-up: the first call on a device looks up the array's device address on
+ * that device (the current device at the time of the call); make that first
+ * call before any stream capture on that device.
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents (whatever must start at zero is cleared by the kernels).
+ * Calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads -- race on the array and corrupt each other's
+ * results: serialise them.  No cudaMalloc, cudaFree or other allocating call
+ * is made. */
+#define CPH_GB_NOALLOC_SCRATCH_BYTES ((size_t)12 << 20)
+int cph_gb_energy_noalloc(int n_rep, int n, const float* x, const float* q, const float* rho,
+                          const float* screen, const cph_gb_params* gb, double* E, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -134,6 +134,7 @@ def lib():
                                vp], i),
             "cph_gb_energy_backward": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, vp,
                                         vp, vp, C.c_size_t, vp], i),
+            "cph_gb_energy_noalloc": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -413,6 +414,20 @@ def gb_energy_backward(x, q, rho, screen, dE, gb=None, workspace=None, stream=No
                                         C.byref(g), _dptr(dE), _dptr(dx), _dptr(dq),
                                         _dptr(drho), _dptr(ws), ws.numel(), _stream(stream)))
     return dx, dq, drho
+
+
+def gb_energy_noalloc(x, q, rho, screen, gb=None, stream=None):
+    """E_GB like gb_energy, without a workspace: the library's fixed scratch
+    array is used (see cph_gb_energy_noalloc in cphremd.h for its size limit and
+    the rule that overlapping calls race)."""
+    import torch
+    n_rep, n = q.shape
+    x, q, rho, screen = (t.contiguous() for t in (x, q, rho, screen))
+    E = torch.empty(n_rep, dtype=torch.float64, device=q.device)
+    g = gb or default_gb()
+    _check(lib().cph_gb_energy_noalloc(n_rep, n, _dptr(x), _dptr(q), _dptr(rho), _dptr(screen),
+                                       C.byref(g), _dptr(E), _stream(stream)))
+    return E
 
 
 def _workspace(n_rep, n, device):

@@ -20,6 +20,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "../../include/cphremd.h"
@@ -419,4 +420,49 @@ extern "C" int cph_gb_energy_backward(int n_rep, int n, const float* x, const fl
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return gfail(CPH_E_CUDA, std::string("cph_gb_energy_backward: ") + cudaGetErrorString(ce));
     return CPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cph_gb_energy_noalloc: the forward GB energy with its scratch in a fixed
+// file-scope device array instead of a caller workspace.  Host code only sees
+// a host-side stand-in for g_gb_noalloc_scratch: its device address is looked
+// up per device with cudaGetSymbolAddress (with that device current) and
+// cached; the kernels receive that address.
+namespace {
+static __device__ __align__(256) unsigned char g_gb_noalloc_scratch[CPH_GB_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+    int dev = -1;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return gfail(CPH_E_CUDA, std::string("cph_gb_energy_noalloc: cudaGetDevice: ") + cudaGetErrorString(ce));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return gfail(CPH_E_INVALID, "cph_gb_energy_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        ce = cudaGetSymbolAddress(&p, g_gb_noalloc_scratch);
+        if (ce != cudaSuccess || !p)
+            return gfail(CPH_E_CUDA, std::string("cph_gb_energy_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CPH_OK;
+}
+} // namespace
+
+extern "C" int cph_gb_energy_noalloc(int n_rep, int n, const float* x, const float* q, const float* rho,
+                                     const float* screen, const cph_gb_params* gb, double* E, void* stream) {
+    if (n_rep < 1 || n < 1) return gfail(CPH_E_INVALID, "cph_gb_energy_noalloc: bad sizes");
+    const size_t need = ws_bytes(n_rep, n);
+    if (need > CPH_GB_NOALLOC_SCRATCH_BYTES)
+        return gfail(CPH_E_INVALID, "cph_gb_energy_noalloc: n_rep * n too large: needs " + std::to_string(need) +
+                                        " bytes of scratch, the fixed array holds " +
+                                        std::to_string((size_t)CPH_GB_NOALLOC_SCRATCH_BYTES));
+    void* ws = nullptr;
+    int rc = noalloc_scratch(&ws);
+    if (rc != CPH_OK) return rc;
+    return cph_gb_energy(n_rep, n, x, q, rho, screen, gb, E, ws, CPH_GB_NOALLOC_SCRATCH_BYTES, stream);
 }
