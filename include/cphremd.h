@@ -233,6 +233,14 @@ int cph_run(cph_engine* e, int64_t n_steps, void* stream);
  * charges and site states are unchanged.  Synchronises `stream`. */
 int cph_time_passes(cph_engine* e, int reps, double* ms /* host [3] */, void* stream);
 
+/* Tile-shape autotuner: times the three pair passes at the current state for
+ * each candidate work-item size (j-tiles of 32 atoms per CTA: 8..128) and
+ * keeps the fastest; *chosen (may be NULL) receives it.  Derived per-atom
+ * quantities are rewritten as by cph_time_passes; results of later steps are
+ * bitwise the same whatever size is chosen (fixed-point sums).  FP64 mode has
+ * nothing to tune (*chosen = 0).  Synchronises `stream`. */
+int cph_autotune(cph_engine* e, void* stream, int* chosen);
+
 /* ---- getters and setters (host buffers; getters synchronise `stream`) */
 int cph_get_energies(cph_engine* e, double* out /* [W * CPH_NTERMS] */, void* stream);
 int cph_get_forces(cph_engine* e, double* out /* [total_atoms * 3] */, void* stream);

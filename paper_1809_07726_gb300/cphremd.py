@@ -129,6 +129,7 @@ def lib():
             "cph_set_step": ([vp, i64], i),
             "cph_status": ([vp, vp], i),
             "cph_time_passes": ([vp, i, vp, vp], i),
+            "cph_autotune": ([vp, vp, C.POINTER(C.c_int)], i),
             "cph_gb_workspace_bytes": ([i, i], C.c_size_t),
             "cph_gb_energy": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, C.c_size_t,
                                vp], i),
@@ -344,6 +345,12 @@ class Engine:
         ms = np.zeros(3)
         self._c(lib().cph_time_passes(self.ptr, int(reps), _p(ms), _stream(stream)))
         return ms
+
+    def autotune(self, stream=None):
+        """cph_autotune: pick the fastest work-item size; returns it."""
+        c = C.c_int(0)
+        self._c(lib().cph_autotune(self.ptr, _stream(stream), C.byref(c)))
+        return c.value
 
     def status(self, stream=None):
         self._c(lib().cph_status(self.ptr, _stream(stream)))

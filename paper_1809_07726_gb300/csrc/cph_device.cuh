@@ -88,6 +88,26 @@ __host__ __device__ inline double unit_open(uint32_t u) {
 __device__ inline long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
 __device__ inline long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
 
+// ---------------------------------------------- MUFU approximations (FP32)
+// Hand-written PTX for the special-function unit with denormals flushed: the
+// library's rsqrtf / expf wrappers add denormal handling around the same
+// approximation, and no operand of the pair loops comes near the denormal
+// range (distances >= ~1 A, exp(-D) underflowing to 0 is harmless).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float exp2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
 // ------------------------------------------------------------- HCT, FP32
 constexpr float kHctXmax = 0.35f;
 

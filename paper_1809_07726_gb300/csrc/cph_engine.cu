@@ -420,7 +420,8 @@ struct cph_engine {
     SymItem* d_sym = nullptr;          // symmetric FP32 items, largest system first
     SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
     int n_sym = 0;
-    std::vector<int> sym_w_off;
+    int sym_chunk = kSymChunk;         // j-tiles per symmetric work item (autotuned)
+    std::vector<int> sym_w_off, h_sys_sst_off;
     int ex_cap = 0;
     int mc_kinds_last = 0;
     cudaStream_t cap_stream = nullptr;
@@ -429,6 +430,8 @@ struct cph_engine {
     ~cph_engine() {
         for (auto& g : graph)
             if (g) cudaGraphExecDestroy(g);
+        if (d_sym) cudaFree(d_sym);
+        if (d_sym_by_w) cudaFree(d_sym_by_w);
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
@@ -712,6 +715,50 @@ int get_graph(cph_engine* E, cudaGraphExec_t* out) {
 
 } // namespace
 
+namespace {
+
+// Symmetric work items for j-tile chunks of `chunk` tiles: every walker's
+// 256-atom i-tiles against the 32-atom j-tiles from their first atom on.
+// Replaces the current item arrays and drops captured graphs (they hold the
+// old item pointers).
+int build_sym_items(cph_engine* E, int chunk) {
+    const int W = E->V.W;
+    std::vector<SymItem> sym, by_w;
+    std::vector<int> w_off(W + 1, 0);
+    for (int w = 0; w < W; ++w) {
+        const int s = E->h_w_sys[w], N = E->h_sys_n[s];
+        const int njt = (N + kSymJ - 1) / kSymJ;
+        for (int it = 0; it * kSymI < N; ++it) {
+            const int i0 = it * kSymI;
+            for (int jt = i0 / kSymJ; jt < njt; jt += chunk)
+                by_w.push_back(SymItem{w, i0, jt, std::min(njt, jt + chunk), E->h_sys_sst_off[s] + it, 0});
+        }
+        w_off[w + 1] = (int)by_w.size();
+    }
+    sym = by_w;
+    std::stable_sort(sym.begin(), sym.end(), [](const SymItem& a, const SymItem& b) {
+        return (a.jt1 - a.jt0) > (b.jt1 - b.jt0);
+    });
+    for (auto& g : E->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (E->d_sym) cudaFree(E->d_sym);
+    if (E->d_sym_by_w) cudaFree(E->d_sym_by_w);
+    E->d_sym = E->d_sym_by_w = nullptr;
+    CK(cudaMalloc(&E->d_sym, sizeof(SymItem) * std::max<size_t>(1, sym.size())));
+    CK(cudaMalloc(&E->d_sym_by_w, sizeof(SymItem) * std::max<size_t>(1, by_w.size())));
+    CK(cudaMemcpy(E->d_sym, sym.data(), sizeof(SymItem) * sym.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E->d_sym_by_w, by_w.data(), sizeof(SymItem) * by_w.size(), cudaMemcpyHostToDevice));
+    E->n_sym = (int)sym.size();
+    E->sym_w_off = w_off;
+    E->sym_chunk = chunk;
+    return CPH_OK;
+}
+
+} // namespace
+
 // =====================================================================
 // C ABI
 // =====================================================================
@@ -946,22 +993,6 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
         return sys_n[w_sys[a.w]] > sys_n[w_sys[b.w]];
     });
-    std::vector<SymItem> sym, sym_by_w;
-    std::vector<int> sym_w_off(W + 1, 0);
-    for (int w = 0; w < W; ++w) {
-        const int s = w_sys[w], N = sys_n[s];
-        const int njt = (N + kSymJ - 1) / kSymJ;
-        for (int it = 0; it * kSymI < N; ++it) {
-            const int i0 = it * kSymI;
-            for (int jt = i0 / kSymJ; jt < njt; jt += kSymChunk)
-                sym_by_w.push_back(SymItem{w, i0, jt, std::min(njt, jt + kSymChunk), sys_sst_off[s] + it, 0});
-        }
-        sym_w_off[w + 1] = (int)sym_by_w.size();
-    }
-    sym = sym_by_w;
-    std::stable_sort(sym.begin(), sym.end(), [](const SymItem& a, const SymItem& b) {
-        return (a.jt1 - a.jt0) > (b.jt1 - b.jt0);
-    });
 
     cph_engine* E = new cph_engine();
     std::unique_ptr<cph_engine> guard(E);
@@ -980,8 +1011,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     E->n_site_states = (int)site_np.size();
     E->item_w_off = item_w_off;
     E->n_items = (int)items.size();
-    E->n_sym = (int)sym.size();
-    E->sym_w_off = sym_w_off;
+    E->h_sys_sst_off = sys_sst_off;
     E->graph_period = schedule_period(E);
     View& V = E->V;
     V.W = W;
@@ -1103,9 +1133,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     Item* di;
     TRY(upload(E, items, &di)); E->d_items = di;
     TRY(upload(E, items_by_w, &di)); E->d_items_by_w = di;
-    SymItem* dsi;
-    TRY(upload(E, sym, &dsi)); E->d_sym = dsi;
-    TRY(upload(E, sym_by_w, &dsi)); E->d_sym_by_w = dsi;
+    TRY(build_sym_items(E, kSymChunk));
 
     // reference energies of every (site, state)
     if (!site_np.empty()) {
@@ -1184,6 +1212,33 @@ int cph_time_passes(cph_engine* e, int reps, double* ms, void* stream) {
     for (auto& x : ev) cudaEventDestroy(x);
     if (rc != CPH_OK) return rc;
     for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+    return CPH_OK;
+}
+
+int cph_autotune(cph_engine* e, void* stream, int* chosen) {
+    if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
+    if (e->precision != CPH_PREC_FP32) {
+        if (chosen) *chosen = 0;
+        return CPH_OK; // the FP64 passes have no tunable shape
+    }
+    cph_engine* E = e;
+    const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128};
+    double best = 1e300;
+    int best_c = e->sym_chunk;
+    for (int c : cand) {
+        TRY(build_sym_items(e, c));
+        double ms[3];
+        TRY(cph_time_passes(e, 1, ms, stream)); // warm-up
+        TRY(cph_time_passes(e, 2, ms, stream));
+        const double t = ms[0] + ms[1] + ms[2];
+        if (t < best) {
+            best = t;
+            best_c = c;
+        }
+    }
+    TRY(build_sym_items(e, best_c));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (chosen) *chosen = best_c;
     return CPH_OK;
 }
 
@@ -1391,7 +1446,8 @@ int cph_status(cph_engine* e, void* stream) {
     if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
     int st = 0;
     TRY(copy_out(e, &st, e->V.status, sizeof(int), stream));
-    if (st) return fail(e, CPH_E_NONFINITE, "non-finite %s produced", (st & 2) ? "position" : "force");
+    if (st)
+        return fail(e, CPH_E_NONFINITE, "non-finite value produced (flags %d: 1 force, 2 position, 4 pair sum)", st);
     return CPH_OK;
 }
 

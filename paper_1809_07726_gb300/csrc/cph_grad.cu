@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kT) k_born(GView g) {
                 const F4 b = sj[k];
                 const float dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                const float rinv = rsqrtf(r2);
+                const float rinv = rsqrt_ftz(r2);
                 part += hct(r2 * rinv, rinv, rti, irti, b.w);
             }
         } else {
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kT) k_born(GView g) {
                 const float dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
                 float r2 = dx * dx + dy * dy + dz * dz;
                 r2 = self ? 1.f : r2;
-                const float rinv = rsqrtf(r2);
+                const float rinv = rsqrt_ftz(r2);
                 const float h = hct(r2 * rinv, rinv, rti, irti, b.w);
                 part += self ? 0.f : h;
             }
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kT) k_pair(GView g) {
             r2 = self ? 1.f : r2;
             const float m = self ? 0.f : 1.f;
             const float D = 0.25f * r2 * (iRi * B.y);
-            const float e = __expf(-D);
-            const float fi = m * rsqrtf(r2 + (Ri * B.x) * e);
+            const float e = exp2_ftz(-D * kLog2e);
+            const float fi = m * rsqrt_ftz(r2 + (Ri * B.x) * e);
             pe.add(qi * A.w * fi);
             if (BACKWARD) {
                 const float qf3 = qi * A.w * fi * fi * fi;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kT) k_chain(GView g) {
             float r2 = dx * dx + dy * dy + dz * dz;
             r2 = self ? 1.f : r2;
             const float m = self ? 0.f : 1.f;
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_ftz(r2);
             const float r = r2 * rinv;
             const float gr = ci * hct_dr(r, rinv, rti, B.x) + A.w * hct_dr(r, rinv, B.y, si);
             const float t = m * gr * rinv;

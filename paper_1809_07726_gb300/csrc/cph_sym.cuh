@@ -39,8 +39,20 @@ struct SymItem {
     int w, i0, jt0, jt1, st, pad;
 };
 
-__device__ __forceinline__ void red_add(long long* p, float v) {
+// Non-finite partials would saturate in the float -> int64 conversion and
+// vanish into a finite-looking sum, so they are flagged before converting.
+__device__ __forceinline__ void red_add(long long* p, float v, int* status) {
+    if (!(fabsf(v) < 1e30f)) atomicOr(status, 4);
     atomicAdd((unsigned long long*)p, (unsigned long long)to_fixed(v, (float)kScaleE));
+}
+
+__device__ __forceinline__ void fix_add(long long* p, long long v) {
+    atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+
+__device__ __forceinline__ void red_add_h(long long* p, float v, int* status) {
+    if (!(fabsf(v) < 1e20f)) atomicOr(status, 4);
+    atomicAdd((unsigned long long*)p, (unsigned long long)to_fixed(v, (float)kScaleH));
 }
 
 // masks of one i atom for the j-tile at j0: bit jj of `skip` = pair not
@@ -76,7 +88,13 @@ __device__ __forceinline__ float hct_dr_series(float rinv2, float rinv, float s)
 
 // ====================================================== GB + Coulomb + LJ
 struct GbI {
-    float x, y, z, q, R, iR, sg, se;
+    float x, y, z;
+    float q;   // sqrt(k) q_i
+    float qc;  // sqrt(k) q_i / eps_in
+    float R;   // Born radius
+    float dk;  // log2(e) / (4 R_i): D log2(e) = r^2 dk_i / R_j
+    float sg;  // sigma_i / 2
+    float se4; // 4 sqrt(eps_i)
 };
 
 struct GbAcc {
@@ -104,22 +122,22 @@ __device__ __forceinline__ void gb_tile(const float4* sa, const float4* sb, int 
                 nb = ((nbm[u] >> jj) & 1u) ? 0.f : 1.f;
                 r2 = sk ? 1.f : r2;
             }
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_ftz(r2);
             const float rinv2 = rinv * rinv;
             const float qq = I[u].q * A.w;
-            const float D = 0.25f * r2 * (I[u].iR * B.y);
-            const float e = __expf(-D);
-            const float fi = rsqrtf(fmaf(I[u].R * B.x, e, r2));
+            const float D2 = r2 * (I[u].dk * B.y); // D log2(e), D = r^2 / (4 R_i R_j)
+            const float e = exp2_ftz(-D2);
+            const float fi = rsqrt_ftz(fmaf(I[u].R * B.x, e, r2));
             const float qf3 = (MASKED ? g * qq : qq) * fi * fi * fi;
-            const float t = qf3 * e * (1.f + D);
+            const float t = qf3 * e * fmaf(D2, kLn2, 1.f);
             a[u].dr = fmaf(t, B.x, a[u].dr);
             jacc.dr = fmaf(t, I[u].R, jacc.dr);
             const float sig = I[u].sg + B.z;
             const float sr2 = sig * sig * rinv2;
             const float sr6 = sr2 * sr2 * sr2;
-            const float ep = (MASKED ? nb * I[u].se : I[u].se) * B.w;
-            const float cq = MASKED ? nb * iei * qq : iei * qq;
-            const float fs = fmaf(cq, rinv, 4.f * ep * sr6 * fmaf(12.f, sr6, -6.f)) * rinv2
+            const float ep4 = (MASKED ? nb * I[u].se4 : I[u].se4) * B.w;
+            const float cq = (MASKED ? nb * I[u].qc : I[u].qc) * A.w;
+            const float fs = fmaf(cq, rinv, ep4 * sr6 * fmaf(12.f, sr6, -6.f)) * rinv2
                            - tau * qf3 * fmaf(-0.25f, e, 1.f);
             a[u].x = fmaf(fs, dx, a[u].x);
             a[u].y = fmaf(fs, dy, a[u].y);
@@ -130,7 +148,7 @@ __device__ __forceinline__ void gb_tile(const float4* sa, const float4* sb, int 
             if (ENERGY) {
                 egb.add((MASKED ? g * qq : qq) * fi);
                 ec.add(cq * rinv);
-                elj.add(ep * sr6 * (sr6 - 1.f));
+                elj.add(ep4 * sr6 * (sr6 - 1.f));
             }
         }
         const int src = (lane + 1) & 31;
@@ -142,9 +160,10 @@ __device__ __forceinline__ void gb_tile(const float4* sa, const float4* sb, int 
 }
 
 template <bool ENERGY>
-__global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restrict__ items, View V) {
+__global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __restrict__ items, View V) {
     __shared__ float4 sa[kSymJ], sb[kSymJ];
     __shared__ float red[4][kSymJ][4];
+    __shared__ long long sfx[kSymI][4]; // i-side fixed-point sums (each thread owns two rows)
     __shared__ double ered[kSymThreads / 32][3];
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
@@ -162,13 +181,17 @@ __global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restric
         I[u].x = vi[u] ? (float)(V.x[3 * (A + i)] - cx) : -kFarF;
         I[u].y = vi[u] ? (float)(V.x[3 * (A + i) + 1] - cy) : -kFarF;
         I[u].z = vi[u] ? (float)(V.x[3 * (A + i) + 2] - cz) : -kFarF;
-        I[u].q = vi[u] ? (float)V.q[A + i] * sqk : 0.f;
+        I[u].q = vi[u] ? (float)(V.q[A + i] * V.sqrt_k) : 0.f;
+        I[u].qc = vi[u] ? (float)(V.q[A + i] * V.sqrt_k * V.inv_eps_in) : 0.f;
         I[u].R = vi[u] ? (float)V.R[A + i] : 1.f;
-        I[u].iR = vi[u] ? (float)(1.0 / V.R[A + i]) : 1.f;
+        I[u].dk = vi[u] ? (float)(0.25 * 1.4426950408889634 / V.R[A + i]) : 1.f;
         I[u].sg = vi[u] ? (float)V.sigh[P + i] : 0.f;
-        I[u].se = vi[u] ? (float)V.sqe[P + i] : 0.f;
+        I[u].se4 = vi[u] ? (float)(4.0 * V.sqe[P + i]) : 0.f;
     }
-    GbAcc acc[2] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
     KSum<float> egb, ec, elj;
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
@@ -194,6 +217,7 @@ __global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restric
         }
         __syncthreads();
         GbAcc jacc = {0.f, 0.f, 0.f, 0.f};
+        GbAcc acc[2] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         uint32_t skip[2] = {0u, 0u}, nbm[2] = {0u, 0u};
         if (jt == next) {
             ++mp;
@@ -203,6 +227,14 @@ __global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restric
             gb_tile<true, ENERGY>(sa, sb, lane, I, acc, jacc, skip, nbm, tau, iei, egb, ec, elj);
         } else {
             gb_tile<false, ENERGY>(sa, sb, lane, I, acc, jacc, skip, nbm, tau, iei, egb, ec, elj);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) { // per-tile conversion: independent of the item's chunking
+            long long* row = sfx[warp * 64 + u * 32 + lane];
+            row[0] += to_fixed(acc[u].x, (float)kScaleE);
+            row[1] += to_fixed(acc[u].y, (float)kScaleE);
+            row[2] += to_fixed(acc[u].z, (float)kScaleE);
+            row[3] += to_fixed(acc[u].dr, (float)kScaleE);
         }
         // lane l now holds the partials of partner l: add the four warps' and send them
         red[warp][lane][0] = jacc.x;
@@ -215,17 +247,18 @@ __global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restric
             const float v = red[0][j][c] + red[1][j][c] + red[2][j][c] + red[3][j][c];
             if (j0 + j < N) {
                 long long* dst = (c < 3) ? &V.Ffix[3 * (A + j0 + j) + c] : &V.dRfix[A + j0 + j];
-                red_add(dst, v);
+                red_add(dst, v, V.status);
             }
         }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (vi[u]) {
-            red_add(&V.Ffix[3 * (A + ii[u])], acc[u].x);
-            red_add(&V.Ffix[3 * (A + ii[u]) + 1], acc[u].y);
-            red_add(&V.Ffix[3 * (A + ii[u]) + 2], acc[u].z);
-            red_add(&V.dRfix[A + ii[u]], acc[u].dr);
+            const long long* row = sfx[warp * 64 + u * 32 + lane];
+            fix_add(&V.Ffix[3 * (A + ii[u])], row[0]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], row[1]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], row[2]);
+            fix_add(&V.dRfix[A + ii[u]], row[3]);
         }
     }
     if (ENERGY) {
@@ -247,8 +280,8 @@ __global__ void __launch_bounds__(kSymThreads) k_gb_sym(const SymItem* __restric
         if (tid < 3) {
             double v = 0.0;
             for (int q = 0; q < kSymThreads / 32; ++q) v += ered[q][tid];
-            // GB pairs carry -tau; Coulomb already has 1/eps_in; LJ carries 4
-            const double scale = (tid == 0) ? -V.tau : (tid == 1 ? 1.0 : 4.0);
+            // GB pairs carry -tau; Coulomb already has 1/eps_in, LJ its factor 4
+            const double scale = (tid == 0) ? -V.tau : 1.0;
             atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + tid],
                       (unsigned long long)__double2ll_rn(scale * v * kScaleE));
         }
@@ -285,32 +318,44 @@ __device__ __forceinline__ void chain_tile(const float4* sa, const float2* sb, i
         const int jj = (lane + k) & (kSymJ - 1);
         const float4 A = sa[jj];
         const float2 B = sb[jj];
+        float dx[2], dy[2], dz[2], r2[2], rinv[2], g[2];
+        bool sk[2] = {false, false}, nr[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const float dx = I[u].x - A.x, dy = I[u].y - A.y, dz = I[u].z - A.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool sk = false;
+            dx[u] = I[u].x - A.x;
+            dy[u] = I[u].y - A.y;
+            dz[u] = I[u].z - A.z;
+            r2[u] = fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u]));
             if (MASKED) {
-                sk = (skip[u] >> jj) & 1u;
-                r2 = sk ? 1.f : r2;
+                sk[u] = (skip[u] >> jj) & 1u;
+                r2[u] = sk[u] ? 1.f : r2[u];
             }
-            const float rinv = rsqrtf(r2);
-            const float rinv2 = rinv * rinv;
-            float g;
-            if (r2 >= rfar2) {
-                g = I[u].c * hct_dr_series(rinv2, rinv, B.x) + A.w * hct_dr_series(rinv2, rinv, I[u].s);
-            } else {
-                const float r = r2 * rinv;
-                g = I[u].c * hct_dr(r, rinv, I[u].rt, B.x) + A.w * hct_dr(r, rinv, B.y, I[u].s);
+            rinv[u] = rsqrt_ftz(r2[u]);
+            const float rinv2 = rinv[u] * rinv[u];
+            g[u] = I[u].c * hct_dr_series(rinv2, rinv[u], B.x) + A.w * hct_dr_series(rinv2, rinv[u], I[u].s);
+            nr[u] = r2[u] < rfar2;
+        }
+        // closed forms only where some lane has a pair inside r_far (rare)
+        if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (nr[u]) {
+                    const float r = r2[u] * rinv[u];
+                    g[u] = I[u].c * hct_dr(r, rinv[u], I[u].rt, B.x) + A.w * hct_dr(r, rinv[u], B.y, I[u].s);
+                }
             }
-            if (MASKED) g = sk ? 0.f : g;
-            const float t = -g * rinv;
-            ax[u] = fmaf(t, dx, ax[u]);
-            ay[u] = fmaf(t, dy, ay[u]);
-            az[u] = fmaf(t, dz, az[u]);
-            jx = fmaf(-t, dx, jx);
-            jy = fmaf(-t, dy, jy);
-            jz = fmaf(-t, dz, jz);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float gg = g[u];
+            if (MASKED) gg = sk[u] ? 0.f : gg;
+            const float t = -gg * rinv[u];
+            ax[u] = fmaf(t, dx[u], ax[u]);
+            ay[u] = fmaf(t, dy[u], ay[u]);
+            az[u] = fmaf(t, dz[u], az[u]);
+            jx = fmaf(-t, dx[u], jx);
+            jy = fmaf(-t, dy[u], jy);
+            jz = fmaf(-t, dz[u], jz);
         }
         const int src = (lane + 1) & 31;
         jx = __shfl_sync(0xffffffffu, jx, src);
@@ -319,10 +364,11 @@ __device__ __forceinline__ void chain_tile(const float4* sa, const float2* sb, i
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads) k_chain_sym(const SymItem* __restrict__ items, View V) {
+__global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __restrict__ items, View V) {
     __shared__ float4 sa[kSymJ];
     __shared__ float2 sb[kSymJ];
     __shared__ float red[4][kSymJ][3];
+    __shared__ long long sfx[kSymI][3]; // i-side fixed-point sums (each thread owns two rows)
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -343,13 +389,17 @@ __global__ void __launch_bounds__(kSymThreads) k_chain_sym(const SymItem* __rest
         I[u].s = vi[u] ? (float)V.sc[P + i] : 0.f;
         I[u].rt = vi[u] ? (float)V.rt[P + i] : 1.f;
     }
-    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
     for (int jt = it.jt0; jt < it.jt1; ++jt) {
         const int j0 = jt * kSymJ;
+        float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
         __syncthreads();
         if (tid < kSymJ) {
             const int j = j0 + tid;
@@ -379,6 +429,13 @@ __global__ void __launch_bounds__(kSymThreads) k_chain_sym(const SymItem* __rest
         } else {
             chain_tile<false>(sa, sb, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            long long* row = sfx[warp * 64 + u * 32 + lane];
+            row[0] += to_fixed(ax[u], (float)kScaleE);
+            row[1] += to_fixed(ay[u], (float)kScaleE);
+            row[2] += to_fixed(az[u], (float)kScaleE);
+        }
         red[warp][lane][0] = jx;
         red[warp][lane][1] = jy;
         red[warp][lane][2] = jz;
@@ -386,15 +443,16 @@ __global__ void __launch_bounds__(kSymThreads) k_chain_sym(const SymItem* __rest
         if (tid < 3 * kSymJ) {
             const int j = tid / 3, c = tid % 3;
             const float v = red[0][j][c] + red[1][j][c] + red[2][j][c] + red[3][j][c];
-            if (j0 + j < N) red_add(&V.Ffix[3 * (A + j0 + j) + c], v);
+            if (j0 + j < N) red_add(&V.Ffix[3 * (A + j0 + j) + c], v, V.status);
         }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (vi[u]) {
-            red_add(&V.Ffix[3 * (A + ii[u])], ax[u]);
-            red_add(&V.Ffix[3 * (A + ii[u]) + 1], ay[u]);
-            red_add(&V.Ffix[3 * (A + ii[u]) + 2], az[u]);
+            const long long* row = sfx[warp * 64 + u * 32 + lane];
+            fix_add(&V.Ffix[3 * (A + ii[u])], row[0]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], row[1]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], row[2]);
         }
     }
 }
@@ -439,37 +497,46 @@ __device__ __forceinline__ void born_tile(const float4* sa, const float2* sb, in
         const int jj = (lane + k) & (kSymJ - 1);
         const float4 A = sa[jj];
         const float2 B = sb[jj];
+        float r2[2], rinv[2], hi[2], hj[2];
+        bool sk[2] = {false, false}, nr[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const float dx = I[u].x - A.x, dy = I[u].y - A.y, dz = I[u].z - A.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool sk = false;
+            r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (MASKED) {
-                sk = (skip[u] >> jj) & 1u;
-                r2 = sk ? 1.f : r2;
+                sk[u] = (skip[u] >> jj) & 1u;
+                r2[u] = sk[u] ? 1.f : r2[u];
             }
-            const float rinv = rsqrtf(r2);
-            float hi, hj;
-            if (r2 >= rfar2) {
-                hi = hct_series(rinv, B.x);
-                hj = hct_series(rinv, I[u].s);
-            } else {
-                const float r = r2 * rinv;
-                hi = hct(r, rinv, I[u].rt, I[u].irt, B.x);
-                hj = hct(r, rinv, A.w, B.y, I[u].s);
+            rinv[u] = rsqrt_ftz(r2[u]);
+            hi[u] = hct_series(rinv[u], B.x);
+            hj[u] = hct_series(rinv[u], I[u].s);
+            nr[u] = r2[u] < rfar2;
+        }
+        // closed forms only where some lane has a pair inside r_far (rare)
+        if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (nr[u]) {
+                    const float r = r2[u] * rinv[u];
+                    hi[u] = hct(r, rinv[u], I[u].rt, I[u].irt, B.x);
+                    hj[u] = hct(r, rinv[u], A.w, B.y, I[u].s);
+                }
             }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
             if (MASKED) {
-                hi = sk ? 0.f : hi;
-                hj = sk ? 0.f : hj;
+                hi[u] = sk[u] ? 0.f : hi[u];
+                hj[u] = sk[u] ? 0.f : hj[u];
             }
-            ah[u] += hi;
-            jh += hj;
+            ah[u] += hi[u];
+            jh += hj[u];
         }
         jh = __shfl_sync(0xffffffffu, jh, (lane + 1) & 31);
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads) k_born_sym(const SymItem* __restrict__ items, View V) {
+__global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __restrict__ items, View V) {
     __shared__ float4 sa[kSymJ];
     __shared__ float2 sb[kSymJ];
     __shared__ float red[4][kSymJ];
@@ -493,7 +560,7 @@ __global__ void __launch_bounds__(kSymThreads) k_born_sym(const SymItem* __restr
         I[u].rt = vi[u] ? (float)V.rt[P + i] : 1.f;
         I[u].irt = vi[u] ? (float)(1.0 / V.rt[P + i]) : 1.f;
     }
-    float ah[2] = {0.f, 0.f};
+    long long hx[2] = {0, 0}; // i-side fixed-point sums
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
@@ -518,6 +585,7 @@ __global__ void __launch_bounds__(kSymThreads) k_born_sym(const SymItem* __restr
         }
         __syncthreads();
         float jh = 0.f;
+        float ah[2] = {0.f, 0.f};
         uint32_t skip[2] = {0u, 0u};
         if (jt == next) {
             ++mp;
@@ -529,19 +597,19 @@ __global__ void __launch_bounds__(kSymThreads) k_born_sym(const SymItem* __restr
         } else {
             born_tile<false>(sa, sb, lane, I, ah, jh, skip, rfar2);
         }
+        hx[0] += to_fixed(ah[0], (float)kScaleH);
+        hx[1] += to_fixed(ah[1], (float)kScaleH);
         red[warp][lane] = jh;
         __syncthreads();
         if (tid < kSymJ) {
             const float v = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
             if (j0 + tid < N)
-                atomicAdd((unsigned long long*)&V.Hfix[A + j0 + tid],
-                          (unsigned long long)to_fixed(v, (float)kScaleH));
+                red_add_h(&V.Hfix[A + j0 + tid], v, V.status);
         }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-        if (vi[u])
-            atomicAdd((unsigned long long*)&V.Hfix[A + ii[u]], (unsigned long long)to_fixed(ah[u], (float)kScaleH));
+        if (vi[u]) fix_add(&V.Hfix[A + ii[u]], hx[u]);
 }
 
 // psi, R, dR/dpsi from the descreening sums (FP64); resets the accumulators

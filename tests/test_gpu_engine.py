@@ -250,3 +250,35 @@ def test_fp32_langevin_step_matches_oracle():
 
     assert rel_rms(eng.velocities(), W.v[0]) <= FORCE_RMS
     assert rel_rms(eng.positions() - s.x, W.x[0] - s.x) <= FORCE_RMS
+
+
+def test_nonfinite_state_is_reported_not_hidden():
+    """Two non-excluded atoms placed on the same point make the pair sums
+    non-finite; the fixed-point accumulators must not hide that: cph_status
+    reports CPH_E_NONFINITE (no fault, only arithmetic)."""
+    s = synth.make_system(300, 51, n_ph=1)
+    grid = synth.Grid(np.array([-0.2]), np.array([7.0]), np.array([300.0]), np.zeros(1, np.int32))
+    eng = cphremd.init_system([s], grid, seed=1)
+    eng.evaluate()
+    eng.status()
+    x = eng.positions()
+    x[200] = x[20]
+    eng.set_positions(x)
+    eng.evaluate()
+    with pytest.raises(cphremd.CphError) as ei:
+        eng.status()
+    assert ei.value.code == cphremd.E_NONFINITE
+
+
+def test_autotuned_tile_shape_changes_nothing_but_speed(ragged_systems):
+    """The autotuner only changes the work-item size; fixed-point sums make the
+    trajectory bitwise identical to the default shape."""
+    grid = _grid_for(ragged_systems)
+    a = cphremd.init_system(ragged_systems, grid, seed=21)
+    b = cphremd.init_system(ragged_systems, grid, seed=21)
+    chunk = a.autotune()
+    assert chunk in (8, 16, 24, 32, 48, 64, 96, 128)
+    a.run(20)
+    b.run(20)
+    np.testing.assert_array_equal(a.positions(), b.positions())
+    np.testing.assert_array_equal(a.forces(), b.forces())

@@ -1,0 +1,40 @@
+"""Multi-rank host logic of bench.py on CPU with the gloo backend (world
+size 2): every rank runs its own ensemble; the reported time is the max over
+ranks and the value counts every rank's replica-steps."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = bench.aggregate_max(1.5 + rank, world, "cpu")
+    out[rank] = t
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+    assert out[0] == out[1] == 2.5
+    import bench
+    assert bench.whole_job_value(world, 384, 10, 2.5) == pytest.approx(2 * 384 * 10 / 2.5)
