@@ -421,6 +421,7 @@ struct cph_engine {
     SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
     int n_sym = 0;
     int sym_chunk = kSymChunk;         // j-tiles per symmetric work item (autotuned)
+    int max_terms = 0;                 // largest bonds + angles count of any system
     std::vector<int> sym_w_off, h_sys_sst_off;
     int ex_cap = 0;
     int mc_kinds_last = 0;
@@ -586,14 +587,22 @@ int launch_atoms(cph_engine* E, int which, bool energy, int a0, int n, cudaStrea
         if (energy) k_fin_c<true><<<g, bs, 0, st>>>(E->V, a0, n);
         else k_fin_c<false><<<g, bs, 0, st>>>(E->V, a0, n);
     } else {
-        if (energy) k_final_forces<true><<<g, bs, 0, st>>>(E->V, a0, n);
-        else k_final_forces<false><<<g, bs, 0, st>>>(E->V, a0, n);
+        k_final_forces<<<g, bs, 0, st>>>(E->V, a0, n);
     }
     CK(cudaGetLastError());
     return CPH_OK;
 }
 
-// pass: 0 born, 1 GB (+ finish), 2 chain (+ finish with bonded terms)
+int launch_bonded(cph_engine* E, bool energy, int w0, int nw, cudaStream_t st) {
+    if (E->max_terms <= 0 || nw <= 0) return CPH_OK;
+    dim3 grid((E->max_terms + kBondedThreads - 1) / kBondedThreads, nw);
+    if (energy) k_bonded_terms<true><<<grid, kBondedThreads, 0, st>>>(E->V, w0);
+    else k_bonded_terms<false><<<grid, kBondedThreads, 0, st>>>(E->V, w0);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+// pass: 0 born, 1 GB (+ finish), 2 chain (+ bonded terms, finish)
 int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
     const bool fp32 = E->precision == CPH_PREC_FP32;
     const int W = E->V.W;
@@ -605,6 +614,7 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
                              : launch_chain(E, E->d_items, E->n_items, energy, st);
         }
         TRY(launch_sym_pair(E, E->d_sym, E->n_sym, energy, pass, st));
+        if (pass == 2) TRY(launch_bonded(E, energy, 0, E->V.W, st));
         return launch_atoms(E, fin, energy, 0, E->V.total_atoms, st);
     }
     for (int w = 0; w < W; ++w) {
@@ -616,6 +626,7 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
         } else {
             TRY(launch_sym_pair(E, E->d_sym_by_w + E->sym_w_off[w], E->sym_w_off[w + 1] - E->sym_w_off[w],
                                 energy, pass, st));
+            if (pass == 2) TRY(launch_bonded(E, energy, w, 1, st));
             TRY(launch_atoms(E, fin, energy, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], st));
         }
     }
@@ -801,6 +812,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     std::vector<double> site_q, site_ref;
     std::vector<int> mt_off(1, 0), mt_list, sys_st_off(n_sys + 1, 0);
     std::vector<int> smt_off(1, 0), smt_list, sys_sst_off(n_sys + 1, 0);
+    std::vector<int> sys_bond_off(n_sys + 1, 0), sys_ang_off(n_sys + 1, 0);
     const double off = p->gb.offset;
     for (int s = 0; s < n_sys; ++s) {
         const cph_system_desc& d = sys[s];
@@ -882,6 +894,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
             at[j].push_back(ang_base + a);
             at[k].push_back(ang_base + a);
         }
+        sys_bond_off[s + 1] = (int)bond_k.size();
+        sys_ang_off[s + 1] = (int)ang_k.size();
         for (int i = 0; i < N; ++i) {
             for (int b : bt[i]) bond_idx.push_back(b);
             bond_off.push_back((int)bond_idx.size());
@@ -1044,6 +1058,20 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(upload(E, ang_ijk, &d)); V.ang_ijk = d;
     TRY(upload(E, ang_k, &dd)); V.ang_k = dd;
     TRY(upload(E, ang_t0, &dd)); V.ang_t0 = dd;
+    TRY(upload(E, sys_bond_off, &d)); V.sys_bond_off = d;
+    TRY(upload(E, sys_ang_off, &d)); V.sys_ang_off = d;
+    {
+        std::vector<long long> tf_off(W + 1, 0);
+        for (int w = 0; w < W; ++w) {
+            const int s = w_sys[w];
+            const int nb = sys_bond_off[s + 1] - sys_bond_off[s], na = sys_ang_off[s + 1] - sys_ang_off[s];
+            tf_off[w + 1] = tf_off[w] + 6LL * nb + 9LL * na;
+            E->max_terms = std::max(E->max_terms, nb + na);
+        }
+        long long* dtf;
+        TRY(upload(E, tf_off, &dtf)); V.w_tf_off = dtf;
+        TRY(alloc0(E, (size_t)tf_off[W], &dd)); V.tforce = dd;
+    }
     TRY(upload(E, mt_off, &d)); V.mt_off = d;
     TRY(upload(E, mt_list, &d)); V.mt_list = d;
     TRY(upload(E, smt_off, &d)); V.smt_off = d;

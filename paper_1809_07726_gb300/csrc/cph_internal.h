@@ -39,6 +39,9 @@ struct View {
     const int *bond_off, *bond_idx, *bond_ij;
     const double *bond_k, *bond_r0;
     const int *ang_off, *ang_idx, *ang_ijk;
+    const int *sys_bond_off, *sys_ang_off; // per-system ranges of the bond / angle arrays
+    const long long* w_tf_off;             // per-walker offset into tforce (doubles)
+    double* tforce;                        // per-term bonded forces: bonds [2][3], angles [3][3]
     const double *ang_k, *ang_t0;
     const int *mt_off, *mt_list;
     // sites (global site index g = sys_site_off[s] + k)

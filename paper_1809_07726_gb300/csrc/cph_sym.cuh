@@ -33,7 +33,8 @@ namespace cph {
 constexpr int kSymThreads = 128;
 constexpr int kSymI = 256;    // atoms per i-tile (two per thread)
 constexpr int kSymJ = 32;     // atoms per j-tile
-constexpr int kSymChunk = 48; // j-tiles per work item at most
+constexpr int kSymChunk = 48; // j-tiles per work item at most (default; autotuned)
+constexpr int kSymG = 4;      // j-tiles staged per barrier (one atom per thread)
 
 struct SymItem {
     int w, i0, jt0, jt1, st, pad;
@@ -161,8 +162,8 @@ __device__ __forceinline__ void gb_tile(const float4* sa, const float4* sb, int 
 
 template <bool ENERGY>
 __global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymJ], sb[kSymJ];
-    __shared__ float red[4][kSymJ][4];
+    __shared__ float4 sa[kSymG * kSymJ], sb[kSymG * kSymJ];
+    __shared__ float red[kSymG][4][kSymJ][4];
     __shared__ long long sfx[kSymI][4]; // i-side fixed-point sums (each thread owns two rows)
     __shared__ double ered[kSymThreads / 32][3];
     const SymItem it = items[blockIdx.x];
@@ -197,11 +198,11 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __rest
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-    for (int jt = it.jt0; jt < it.jt1; ++jt) {
-        const int j0 = jt * kSymJ;
+    for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
+        const int ng = min(kSymG, it.jt1 - g0);
         __syncthreads();
-        if (tid < kSymJ) {
-            const int j = j0 + tid;
+        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
+            const int j = g0 * kSymJ + tid;
             float4 a, b;
             if (j < N) {
                 a = make_float4((float)(V.x[3 * (A + j)] - cx), (float)(V.x[3 * (A + j) + 1] - cy),
@@ -216,38 +217,45 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __rest
             sb[tid] = b;
         }
         __syncthreads();
-        GbAcc jacc = {0.f, 0.f, 0.f, 0.f};
-        GbAcc acc[2] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-        uint32_t skip[2] = {0u, 0u}, nbm[2] = {0u, 0u};
-        if (jt == next) {
-            ++mp;
-            next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+        for (int g = 0; g < ng; ++g) {
+            const int jt = g0 + g, j0 = jt * kSymJ;
+            GbAcc jacc = {0.f, 0.f, 0.f, 0.f};
+            GbAcc acc[2] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            uint32_t skip[2] = {0u, 0u}, nbm[2] = {0u, 0u};
+            if (jt == next) {
+                ++mp;
+                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm[u]);
-            gb_tile<true, ENERGY>(sa, sb, lane, I, acc, jacc, skip, nbm, tau, iei, egb, ec, elj);
-        } else {
-            gb_tile<false, ENERGY>(sa, sb, lane, I, acc, jacc, skip, nbm, tau, iei, egb, ec, elj);
-        }
+                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm[u]);
+                gb_tile<true, ENERGY>(sa + g * kSymJ, sb + g * kSymJ, lane, I, acc, jacc, skip, nbm, tau,
+                                      iei, egb, ec, elj);
+            } else {
+                gb_tile<false, ENERGY>(sa + g * kSymJ, sb + g * kSymJ, lane, I, acc, jacc, skip, nbm, tau,
+                                       iei, egb, ec, elj);
+            }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) { // per-tile conversion: independent of the item's chunking
-            long long* row = sfx[warp * 64 + u * 32 + lane];
-            row[0] += to_fixed(acc[u].x, (float)kScaleE);
-            row[1] += to_fixed(acc[u].y, (float)kScaleE);
-            row[2] += to_fixed(acc[u].z, (float)kScaleE);
-            row[3] += to_fixed(acc[u].dr, (float)kScaleE);
+            for (int u = 0; u < 2; ++u) { // per-tile conversion: independent of the item's chunking
+                long long* row = sfx[warp * 64 + u * 32 + lane];
+                row[0] += to_fixed(acc[u].x, (float)kScaleE);
+                row[1] += to_fixed(acc[u].y, (float)kScaleE);
+                row[2] += to_fixed(acc[u].z, (float)kScaleE);
+                row[3] += to_fixed(acc[u].dr, (float)kScaleE);
+            }
+            // lane l now holds the partials of partner l of this tile
+            red[g][warp][lane][0] = jacc.x;
+            red[g][warp][lane][1] = jacc.y;
+            red[g][warp][lane][2] = jacc.z;
+            red[g][warp][lane][3] = jacc.dr;
         }
-        // lane l now holds the partials of partner l: add the four warps' and send them
-        red[warp][lane][0] = jacc.x;
-        red[warp][lane][1] = jacc.y;
-        red[warp][lane][2] = jacc.z;
-        red[warp][lane][3] = jacc.dr;
         __syncthreads();
-        {
-            const int j = tid >> 2, c = tid & 3;
-            const float v = red[0][j][c] + red[1][j][c] + red[2][j][c] + red[3][j][c];
-            if (j0 + j < N) {
-                long long* dst = (c < 3) ? &V.Ffix[3 * (A + j0 + j) + c] : &V.dRfix[A + j0 + j];
-                red_add(dst, v, V.status);
+        // add the four warps' partials of every staged partner and send them
+        for (int v = tid; v < ng * kSymJ * 4; v += kSymThreads) {
+            const int g = v / (kSymJ * 4), j = (v >> 2) & (kSymJ - 1), c = v & 3;
+            const float sum = red[g][0][j][c] + red[g][1][j][c] + red[g][2][j][c] + red[g][3][j][c];
+            const int jg = (g0 + g) * kSymJ + j;
+            if (jg < N) {
+                long long* dst = (c < 3) ? &V.Ffix[3 * (A + jg) + c] : &V.dRfix[A + jg];
+                red_add(dst, sum, V.status);
             }
         }
     }
@@ -365,9 +373,9 @@ __device__ __forceinline__ void chain_tile(const float4* sa, const float2* sb, i
 }
 
 __global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymJ];
-    __shared__ float2 sb[kSymJ];
-    __shared__ float red[4][kSymJ][3];
+    __shared__ float4 sa[kSymG * kSymJ];
+    __shared__ float2 sb[kSymG * kSymJ];
+    __shared__ float red[kSymG][4][kSymJ][3];
     __shared__ long long sfx[kSymI][3]; // i-side fixed-point sums (each thread owns two rows)
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
@@ -397,12 +405,11 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __r
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-    for (int jt = it.jt0; jt < it.jt1; ++jt) {
-        const int j0 = jt * kSymJ;
-        float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
+    for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
+        const int ng = min(kSymG, it.jt1 - g0);
         __syncthreads();
-        if (tid < kSymJ) {
-            const int j = j0 + tid;
+        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
+            const int j = g0 * kSymJ + tid;
             float4 a;
             float2 b;
             if (j < N) {
@@ -417,33 +424,38 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __r
             sb[tid] = b;
         }
         __syncthreads();
-        float jx = 0.f, jy = 0.f, jz = 0.f;
-        uint32_t skip[2] = {0u, 0u};
-        if (jt == next) {
-            ++mp;
-            next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-            uint32_t nbm;
+        for (int g = 0; g < ng; ++g) {
+            const int jt = g0 + g, j0 = jt * kSymJ;
+            float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
+            float jx = 0.f, jy = 0.f, jz = 0.f;
+            uint32_t skip[2] = {0u, 0u};
+            if (jt == next) {
+                ++mp;
+                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+                uint32_t nbm;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
-            chain_tile<true>(sa, sb, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
-        } else {
-            chain_tile<false>(sa, sb, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
-        }
+                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
+                chain_tile<true>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
+            } else {
+                chain_tile<false>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
+            }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            long long* row = sfx[warp * 64 + u * 32 + lane];
-            row[0] += to_fixed(ax[u], (float)kScaleE);
-            row[1] += to_fixed(ay[u], (float)kScaleE);
-            row[2] += to_fixed(az[u], (float)kScaleE);
+            for (int u = 0; u < 2; ++u) {
+                long long* row = sfx[warp * 64 + u * 32 + lane];
+                row[0] += to_fixed(ax[u], (float)kScaleE);
+                row[1] += to_fixed(ay[u], (float)kScaleE);
+                row[2] += to_fixed(az[u], (float)kScaleE);
+            }
+            red[g][warp][lane][0] = jx;
+            red[g][warp][lane][1] = jy;
+            red[g][warp][lane][2] = jz;
         }
-        red[warp][lane][0] = jx;
-        red[warp][lane][1] = jy;
-        red[warp][lane][2] = jz;
         __syncthreads();
-        if (tid < 3 * kSymJ) {
-            const int j = tid / 3, c = tid % 3;
-            const float v = red[0][j][c] + red[1][j][c] + red[2][j][c] + red[3][j][c];
-            if (j0 + j < N) red_add(&V.Ffix[3 * (A + j0 + j) + c], v, V.status);
+        for (int v = tid; v < ng * kSymJ * 3; v += kSymThreads) {
+            const int g = v / (kSymJ * 3), rem = v % (kSymJ * 3), j = rem / 3, c = rem % 3;
+            const float sum = red[g][0][j][c] + red[g][1][j][c] + red[g][2][j][c] + red[g][3][j][c];
+            const int jg = (g0 + g) * kSymJ + j;
+            if (jg < N) red_add(&V.Ffix[3 * (A + jg) + c], sum, V.status);
         }
     }
 #pragma unroll
@@ -457,28 +469,111 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __r
     }
 }
 
-// total force: fixed-point pair forces + bonded terms (FP64); bonded energies
+// Bonded terms, one thread per (walker, term), FP64: each bond or angle is
+// evaluated once and its forces on its two or three atoms are stored in the
+// per-term buffer (the atoms gather them in a fixed order in k_final_forces,
+// so the sum stays deterministic); energies per walker in fixed point.
+constexpr int kBondedThreads = 256;
+
 template <bool ENERGY>
+__global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0) {
+    __shared__ double re[kBondedThreads / 32][2];
+    const int w = w0 + blockIdx.y;
+    const int s = V.w_sys[w], A = V.w_off[w];
+    const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0;
+    const int a0 = V.sys_ang_off[s], na = V.sys_ang_off[s + 1] - a0;
+    const int t = blockIdx.x * kBondedThreads + threadIdx.x;
+    double* buf = V.tforce + V.w_tf_off[w];
+    const double* x = V.x;
+    double eb = 0.0, ea = 0.0;
+    if (t < nb) {
+        const int b = b0 + t;
+        const int i = V.bond_ij[2 * b], j = V.bond_ij[2 * b + 1];
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + i) + c] - x[3 * (A + j) + c];
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double dr = r - V.bond_r0[b];
+        const double g = 2.0 * V.bond_k[b] * dr / r;
+        for (int c = 0; c < 3; ++c) {
+            buf[6 * t + c] = -g * d[c];
+            buf[6 * t + 3 + c] = g * d[c];
+        }
+        eb = V.bond_k[b] * dr * dr;
+    } else if (t < nb + na) {
+        const int la = t - nb, a = a0 + la;
+        const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
+        double u[3], v[3];
+        for (int c = 0; c < 3; ++c) {
+            u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
+            v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
+        }
+        const double ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double rv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (ru * rv);
+        cs = fmin(1.0, fmax(-1.0, cs));
+        const double th = acos(cs);
+        const double dth = th - V.ang_t0[a];
+        const double k = -2.0 * V.ang_k[a] * dth / sqrt(fmax(1e-300, 1.0 - cs * cs)); // dE/dcos
+        double* o = buf + 6 * (size_t)nb + 9 * (size_t)la;
+        for (int c = 0; c < 3; ++c) {
+            const double gi = k * (v[c] / (ru * rv) - cs * u[c] / (ru * ru));
+            const double gk = k * (u[c] / (ru * rv) - cs * v[c] / (rv * rv));
+            o[c] = -gi;
+            o[3 + c] = gi + gk;
+            o[6 + c] = -gk;
+        }
+        ea = V.ang_k[a] * dth * dth;
+    }
+    if (ENERGY) {
+#pragma unroll
+        for (int of = 16; of > 0; of >>= 1) {
+            eb += __shfl_down_sync(0xffffffffu, eb, of);
+            ea += __shfl_down_sync(0xffffffffu, ea, of);
+        }
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        if (lane == 0) {
+            re[wp][0] = eb;
+            re[wp][1] = ea;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            double v = 0.0;
+            for (int q = 0; q < kBondedThreads / 32; ++q) v += re[q][threadIdx.x];
+            if (v != 0.0)
+                atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 3 + threadIdx.x],
+                          (unsigned long long)__double2ll_rn(v * kScaleE));
+        }
+    }
+}
+
+// total force: fixed-point pair forces + the atom's bonded-term forces
 __global__ void k_final_forces(View V, int a0, int n) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
-    const int A = V.w_off[w], li = a - A, P = V.sys_poff[V.w_sys[w]];
+    const int s = V.w_sys[w];
+    const int A = V.w_off[w], li = a - A, P = V.sys_poff[s];
     double F[3] = {(double)V.Ffix[3 * a] / kScaleE, (double)V.Ffix[3 * a + 1] / kScaleE,
                    (double)V.Ffix[3 * a + 2] / kScaleE};
-    double eb = 0.0, ea = 0.0;
-    bonded_atom(V, A, P, li, F, eb, ea);
+    const double* buf = V.tforce + V.w_tf_off[w];
+    const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0, an0 = V.sys_ang_off[s];
+    for (int e = V.bond_off[P + li]; e < V.bond_off[P + li + 1]; ++e) {
+        const int b = V.bond_idx[e];
+        const int role = (V.bond_ij[2 * b] == li) ? 0 : 1;
+        const double* o = buf + 6 * (b - b0) + 3 * role;
+        for (int c = 0; c < 3; ++c) F[c] += o[c];
+    }
+    for (int e = V.ang_off[P + li]; e < V.ang_off[P + li + 1]; ++e) {
+        const int ag = V.ang_idx[e];
+        const int role = (V.ang_ijk[3 * ag] == li) ? 0 : ((V.ang_ijk[3 * ag + 1] == li) ? 1 : 2);
+        const double* o = buf + 6 * (size_t)nb + 9 * (size_t)(ag - an0) + 3 * role;
+        for (int c = 0; c < 3; ++c) F[c] += o[c];
+    }
     V.F[3 * a] = F[0];
     V.F[3 * a + 1] = F[1];
     V.F[3 * a + 2] = F[2];
     if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(V.status, 1);
-    if (ENERGY) {
-        if (eb != 0.0)
-            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 3], (unsigned long long)__double2ll_rn(eb * kScaleE));
-        if (ea != 0.0)
-            atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 4], (unsigned long long)__double2ll_rn(ea * kScaleE));
-    }
 }
 
 // ========================================================= Born radii
@@ -537,9 +632,9 @@ __device__ __forceinline__ void born_tile(const float4* sa, const float2* sb, in
 }
 
 __global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymJ];
-    __shared__ float2 sb[kSymJ];
-    __shared__ float red[4][kSymJ];
+    __shared__ float4 sa[kSymG * kSymJ];
+    __shared__ float2 sb[kSymG * kSymJ];
+    __shared__ float red[kSymG][4][kSymJ];
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -565,11 +660,11 @@ __global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __re
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-    for (int jt = it.jt0; jt < it.jt1; ++jt) {
-        const int j0 = jt * kSymJ;
+    for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
+        const int ng = min(kSymG, it.jt1 - g0);
         __syncthreads();
-        if (tid < kSymJ) {
-            const int j = j0 + tid;
+        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
+            const int j = g0 * kSymJ + tid;
             float4 a;
             float2 b;
             if (j < N) {
@@ -584,27 +679,31 @@ __global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __re
             sb[tid] = b;
         }
         __syncthreads();
-        float jh = 0.f;
-        float ah[2] = {0.f, 0.f};
-        uint32_t skip[2] = {0u, 0u};
-        if (jt == next) {
-            ++mp;
-            next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-            uint32_t nbm;
+        for (int g = 0; g < ng; ++g) {
+            const int jt = g0 + g, j0 = jt * kSymJ;
+            float jh = 0.f;
+            float ah[2] = {0.f, 0.f};
+            uint32_t skip[2] = {0u, 0u};
+            if (jt == next) {
+                ++mp;
+                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+                uint32_t nbm;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
-            born_tile<true>(sa, sb, lane, I, ah, jh, skip, rfar2);
-        } else {
-            born_tile<false>(sa, sb, lane, I, ah, jh, skip, rfar2);
+                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
+                born_tile<true>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ah, jh, skip, rfar2);
+            } else {
+                born_tile<false>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ah, jh, skip, rfar2);
+            }
+            hx[0] += to_fixed(ah[0], (float)kScaleH);
+            hx[1] += to_fixed(ah[1], (float)kScaleH);
+            red[g][warp][lane] = jh;
         }
-        hx[0] += to_fixed(ah[0], (float)kScaleH);
-        hx[1] += to_fixed(ah[1], (float)kScaleH);
-        red[warp][lane] = jh;
         __syncthreads();
-        if (tid < kSymJ) {
-            const float v = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
-            if (j0 + tid < N)
-                red_add_h(&V.Hfix[A + j0 + tid], v, V.status);
+        if (tid < ng * kSymJ) {
+            const int g = tid / kSymJ, j = tid % kSymJ;
+            const float v = red[g][0][j] + red[g][1][j] + red[g][2][j] + red[g][3][j];
+            const int jg = g0 * kSymJ + tid;
+            if (jg < N) red_add_h(&V.Hfix[A + jg], v, V.status);
         }
     }
 #pragma unroll
