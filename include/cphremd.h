@@ -313,7 +313,7 @@ int cph_gb_energy_backward(int n_rep, int n, const float* x, const float* q,
  * Scratch: a file-scope device array of CPH_GB_NOALLOC_SCRATCH_BYTES (12 MiB),
  * reserved on every GPU where the library's kernels are loaded and held until
  * the process exits.  A call needs cph_gb_workspace_bytes(n_rep, n) bytes of
- * it (about 72 bytes per replica-atom: roughly 170,000 replica-atoms, e.g. 20
+ * it (about 88 bytes per replica-atom: roughly 140,000 replica-atoms, e.g. 17
  * replicas of an 8000-atom system); a larger request returns CPH_E_INVALID
  * and launches nothing.
  * Set-up: the first call on a device looks up the array's device address on
