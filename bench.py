@@ -190,6 +190,37 @@ def run_reference(args):
 
 # -------------------------------------------------------------------- GPU arm
 
+def backward_leg(dev, stream, barrier, sm_mhz, n_eval=5):
+    """a9: GB-energy backward w.r.t. x, q, rho for 128 replicas of an 8000-atom
+    system (Born radii recomputed), CUDA events on the launching stream."""
+    import torch
+
+    from paper_1809_07726_gb300 import cphremd, synth
+    s5, x5, q5, rho5 = synth.config_c5()
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    xt, qt, rt, st5 = f32(x5), f32(q5), f32(rho5), f32(s5.screen)
+    ws = cphremd._workspace(q5.shape[0], q5.shape[1], dev)
+    up = torch.ones(q5.shape[0], dtype=torch.float64, device=dev)
+    for _ in range(2):
+        cphremd.gb_energy_backward(xt, qt, rt, st5, up, workspace=ws)
+    barrier()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(n_eval):
+        cphremd.gb_energy_backward(xt, qt, rt, st5, up, workspace=ws)
+    b1.record(stream)
+    barrier()
+    bw_ms = b0.elapsed_time(b1) / n_eval
+    bw_pairs = q5.shape[0] * q5.shape[1] * (q5.shape[1] - 1) // 2
+    bw_achieved = bw_pairs / (bw_ms / 1e3) / 1e9
+    bw_peak = N_SM * (sm_mhz or 2070.0) * 1e6 * pairs_per_clk_per_sm(*BACKWARD_COST) / 1e9
+    return {"workload": "GB energy backward w.r.t. x, q, rho: 128 replicas x 8000 atoms",
+            "ms_per_eval": bw_ms, "evals_per_s": q5.shape[0] / (bw_ms / 1e3),
+            "pair_evals_per_s": bw_pairs / (bw_ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": bw_achieved, "peak": bw_peak,
+                         "unit": "Gpair/s", "frac": bw_achieved / bw_peak}}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -309,33 +340,7 @@ def run_gpu(args):
     e2e_value = W * n_e2e / e2e_s
     del e2
 
-    # a9: GB-energy backward, 128 replicas of an 8000-atom system
-    from paper_1809_07726_gb300 import synth
-    s5, x5, q5, rho5 = synth.config_c5()
-    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
-    xt, qt, rt, st5 = f32(x5), f32(q5), f32(rho5), f32(s5.screen)
-    ws = cphremd._workspace(q5.shape[0], q5.shape[1], dev)
-    up = torch.ones(q5.shape[0], dtype=torch.float64, device=dev)
-    for _ in range(2):
-        cphremd.gb_energy_backward(xt, qt, rt, st5, up, workspace=ws)
-    barrier()
-    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_bw = 5
-    b0.record(stream)
-    for _ in range(n_bw):
-        cphremd.gb_energy_backward(xt, qt, rt, st5, up, workspace=ws)
-    b1.record(stream)
-    barrier()
-    bw_ms = b0.elapsed_time(b1) / n_bw
-    bw_pairs = q5.shape[0] * q5.shape[1] * (q5.shape[1] - 1) // 2
-    bw_achieved = bw_pairs / (bw_ms / 1e3) / 1e9
-    bw_peak = N_SM * (clocks["sm_mhz"] or 2070.0) * 1e6 * pairs_per_clk_per_sm(*BACKWARD_COST) / 1e9
-    backward = {"workload": "GB energy backward w.r.t. x, q, rho: 128 replicas x 8000 atoms",
-                "ms_per_eval": bw_ms, "evals_per_s": q5.shape[0] / (bw_ms / 1e3),
-                "pair_evals_per_s": bw_pairs / (bw_ms / 1e3),
-                "roofline": {"bound": "alu", "achieved": bw_achieved, "peak": bw_peak,
-                             "unit": "Gpair/s", "frac": bw_achieved / bw_peak}}
-    del xt, qt, rt, ws
+    backward = backward_leg(dev, stream, barrier, clocks["sm_mhz"])
 
     if rank != 0:
         if world > 1:
@@ -397,6 +402,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--leg", default="all", choices=["all", "backward"],
+                    help="backward: time only the GB-energy backward leg (128 x 8000)")
     ap.add_argument("--quick", action="store_true",
                     help="batched timing only (no per-replica, e2e or CPU legs); for profiling")
     args = ap.parse_args()
@@ -404,6 +411,15 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg == "backward":
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1809_07726_gb300 import build
+        build.build()
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"leg": "backward", **backward_leg(dev, torch.cuda.current_stream(dev),
+                                                             torch.cuda.synchronize, None)}),
+              flush=True)
     else:
         run_gpu(args)
 

@@ -11,10 +11,10 @@
 //                    + (s^2/(4r))(1/L^2 - 1/U^2)  [+ 2(1/rt - 1/L) if rt < s - r]
 //   When the spheres are disjoint (L = r - s) H depends on r and x = s/r only:
 //   H = (1/r) (x/(1 - x^2) - atanh x) = (1/r) sum_{k>=1} 2k/(2k+1) x^(2k+1).
-//   The FP32 path evaluates that series (Horner in x^2, nine terms) whenever
-//   x <= 0.35: it needs no transcendental, and it avoids the cancellation of
-//   the closed form (whose terms are O(x) while H is O(x^3)).  Nine terms
-//   leave a relative truncation error below 1e-8 at x = 0.35.
+//   The FP32 path evaluates that series (a degree-5 polynomial in x^2, fitted
+//   on the interval) whenever x <= 0.35: it needs no transcendental, and it
+//   avoids the cancellation of the closed form (whose terms are O(x) while H
+//   is O(x^3)).  The fits stay within 2e-8 relative error.
 //   Derivatives: in every branch the L- and U-dependence of H cancels (the
 //   integrand vanishes on the moving boundary), so
 //     dH/dr  = -(1/4)(1/L^2 - 1/U^2)(1 + s^2/r^2) - ln(L/U)/(2 r^2)
@@ -111,45 +111,39 @@ constexpr float kLn2 = 0.6931471805599453f;
 // ------------------------------------------------------------- HCT, FP32
 constexpr float kHctXmax = 0.35f;
 
-// sum_{k=1..9} 2k/(2k+1) y^(k-1)
-__device__ __forceinline__ float hct_series_h(float y) {
-    float p = 18.f / 19.f;
-    p = fmaf(p, y, 16.f / 17.f);
-    p = fmaf(p, y, 14.f / 15.f);
-    p = fmaf(p, y, 12.f / 13.f);
-    p = fmaf(p, y, 10.f / 11.f);
-    p = fmaf(p, y, 8.f / 9.f);
-    p = fmaf(p, y, 6.f / 7.f);
-    p = fmaf(p, y, 4.f / 5.f);
-    p = fmaf(p, y, 2.f / 3.f);
+// Far-pair polynomials in y = (s/r)^2 on [0, 0.35^2]: degree-5 near-minimax
+// fits (Chebyshev, relative error) of the series
+//   P(y) = sum 2k/(2k+1) y^(k-1),  Q(y) = sum 2k(2k+2)/(2k+1) y^(k-1),
+//   S(y) = sum 2k y^(k-1) = 2/(1-y)^2,
+// with max relative errors 3.5e-9, 1.4e-8 and 1.8e-8 (gen_hct_poly.py derives
+// the coefficients).
+__device__ __forceinline__ float hct_series_h(float y) { // P
+    float p = 1.361160215f;
+    p = fmaf(p, y, 0.8443080909f);
+    p = fmaf(p, y, 0.8931260308f);
+    p = fmaf(p, y, 0.8570198603f);
+    p = fmaf(p, y, 0.8000012903f);
+    p = fmaf(p, y, 0.6666666645f);
     return p;
 }
 
-// sum_{k=1..9} 2k(2k+2)/(2k+1) y^(k-1)
-__device__ __forceinline__ float hct_series_dr(float y) {
-    float p = 360.f / 19.f;
-    p = fmaf(p, y, 288.f / 17.f);
-    p = fmaf(p, y, 224.f / 15.f);
-    p = fmaf(p, y, 168.f / 13.f);
-    p = fmaf(p, y, 120.f / 11.f);
-    p = fmaf(p, y, 80.f / 9.f);
-    p = fmaf(p, y, 48.f / 7.f);
-    p = fmaf(p, y, 24.f / 5.f);
-    p = fmaf(p, y, 8.f / 3.f);
+__device__ __forceinline__ float hct_series_dr(float y) { // Q
+    float p = 20.1395503f;
+    p = fmaf(p, y, 9.836372412f);
+    p = fmaf(p, y, 8.959016539f);
+    p = fmaf(p, y, 6.855114687f);
+    p = fmaf(p, y, 4.800021136f);
+    p = fmaf(p, y, 2.666666631f);
     return p;
 }
 
-// sum_{k=1..9} 2k y^(k-1)
-__device__ __forceinline__ float hct_series_ds(float y) {
-    float p = 18.f;
-    p = fmaf(p, y, 16.f);
-    p = fmaf(p, y, 14.f);
-    p = fmaf(p, y, 12.f);
-    p = fmaf(p, y, 10.f);
-    p = fmaf(p, y, 8.f);
-    p = fmaf(p, y, 6.f);
-    p = fmaf(p, y, 4.f);
-    p = fmaf(p, y, 2.f);
+__device__ __forceinline__ float hct_series_ds(float y) { // S
+    float p = 18.77114444f;
+    p = fmaf(p, y, 8.994253274f);
+    p = fmaf(p, y, 8.065659941f);
+    p = fmaf(p, y, 5.998104684f);
+    p = fmaf(p, y, 4.0000197f);
+    p = fmaf(p, y, 1.999999967f);
     return p;
 }
 
