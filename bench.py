@@ -132,7 +132,10 @@ def whole_job_value(world, walkers, steps, t_max):
 
 
 def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
-    n = 4 + 1  # born, gb, chain, langevin + the step-counter tick of a one-step cph_run
+    # batched FP32 step: Born-radii pair kernel + finish, GB pair kernel + finish,
+    # chain pair kernel + bonded terms + force finish, observables, Langevin,
+    # and the step-counter tick of a one-step cph_run
+    n = 2 + 2 + 3 + 1 + 1 + 1
     if t > 0:
         n += int(t % mc_ph == 0) + int(t % mc_redox == 0) + int(t % ex_every == 0)
     return n

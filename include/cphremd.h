@@ -273,6 +273,53 @@ int cph_status(cph_engine* e, void* stream);
  * computed them: cph_evaluate, cph_attempt_exchanges, or a cph_run step that
  * attempted an exchange. */
 
+/* ---- sampling observables
+ *
+ * The analysis of the "E,pH-REMD at 300 K" results fits E0 with eq (2) to the
+ * cumulative fraction of reduced species at every (E, pH) condition, and
+ * Figure 7 counts how long each replica spent at every (E, T, pH)
+ * combination.  The engine accumulates both on the device: every MD step
+ * (cph_run and cph_step_replicas) takes one sample after the step's MC sweeps
+ * and exchange attempt, i.e. with the charges and condition the step's
+ * dynamics then runs at.
+ *
+ * Occupancy rows: condition slot s holds, at any time, a walker of system
+ * system_of_slot[s] (exchanges never mix systems), so row
+ * cph_site_offsets()[s] + k counts the samples in which site k of the walker
+ * at slot s was in each state, CPH_MAX_STATES int64 columns per row (columns
+ * >= the site's n_states stay 0).  Every row sums to the sample count.
+ * Visits: [W * W] int64, walker-major: visits[w * W + s] = samples in which
+ * walker w sat at slot s; every row and every column sums to the sample
+ * count.  Counts are exact integers, independent of launch shape. */
+#define CPH_MAX_STATES 8
+int cph_get_occupancy(cph_engine* e, int64_t* out /* [site_offsets[W] * CPH_MAX_STATES] */,
+                      int64_t* n_samples /* may be NULL */, void* stream);
+int cph_get_visits(cph_engine* e, int64_t* out /* [W * W] */, void* stream);
+/* Per occupancy row: the sampled fraction protonated (pH site) or reduced
+ * (redox site), sum_state count(state) * (n(state) - n_min) / (n_max - n_min)
+ * / n_samples with n = protons (pH) or electrons (redox) of each state; a
+ * site whose states all carry the same n gives 0.  CPH_E_STATE when no
+ * sample has been taken yet. */
+int cph_get_fractions(cph_engine* e, double* out /* [site_offsets[W]] */, void* stream);
+/* Zero the occupancy, the visits and the sample count (starts a new
+ * accumulation window, e.g. after equilibration). */
+int cph_reset_observables(cph_engine* e, void* stream);
+
+/* Least-squares Hill fit of a titration curve (host only, no GPU needed):
+ * minimises sum_i (f_i - f(x_i))^2 over (x0, n_hill) with
+ *   CPH_FIT_PH:    eq (1), f(pH) = 1 / (1 + 10^(n_hill (pH - pKa))), x0 = pKa;
+ *   CPH_FIT_REDOX: eq (2), f(E) = 1 / (1 + exp(n_hill v F (E - E0) / (kB T))),
+ *                  x0 = E0 in volts, v electrons, T kelvin.
+ * x[n_pts], f[n_pts] host arrays, 0 <= f <= 1.  Started from the linear Hill
+ * plot regression, refined by Levenberg-Marquardt.  *rss (may be NULL) gets
+ * the residual sum of squares.  CPH_E_INVALID for fewer than two distinct x,
+ * f outside [0, 1], a curve with no value strictly inside (0, 1), T <= 0 or
+ * v <= 0 (redox), or no convergence in 500 iterations. */
+#define CPH_FIT_PH 1
+#define CPH_FIT_REDOX 2
+int cph_fit_hill(int kind, int n_pts, const double* x, const double* f, double T, double v,
+                 double* x0, double* n_hill, double* rss);
+
 /* ---- differentiable GB energy (device buffers, caller-owned) */
 
 /* E_GB of n_rep independent configurations of one n-atom system (no Coulomb,

@@ -11,7 +11,9 @@ Layout:
   this module   ctypes bindings, 1-2/1-3 exclusions from the bond graph, the
                 isolated-site reference energies, the C(pH,E)MD Monte-Carlo
                 sweep, the Metropolis exchanges along E, pH and T, the step
-                schedule, and the closed forms of eqs (1), (2), (6)-(8).
+                schedule, the closed forms of eqs (1), (2), (6)-(8), and
+                the sampling observables (per-condition fractions, Hill fits
+                of eqs (1) and (2); counters in run.py).
 
 Readings of the paper where it is silent (it prints no GB formula, MC move set,
 integrator or constant): the OBC "igb=2" model with HCT descreening, constants
@@ -309,6 +311,49 @@ def eq8_sum_pka(E, e0_prot, e0_deprot, pka_red, T, v=1.0):
     num = np.exp(-v * b * e0_prot) + np.exp(-b * E)
     den = np.exp(-v * b * e0_deprot) + np.exp(-b * E)
     return np.sum(pka_red) + np.log10(num / den)
+
+
+# ------------------------------------------------------ sampling observables
+
+def site_fractions(W):
+    """Per condition slot s, per site k of the walker sitting there: the
+    sampled fraction protonated (pH site) or reduced (redox site), i.e. the
+    mean over samples of (n(state) - n_min) / (n_max - n_min), n = protons or
+    electrons of the state.  Returns a list over slots of arrays [n_sites]."""
+    out = []
+    for s, occ in enumerate(W.occ):
+        sysd = W.systems[W.sys_of[s]]
+        fr = np.zeros(len(sysd.sites))
+        for k, st in enumerate(sysd.sites):
+            n = np.asarray(st.n_prot if st.kind == "ph" else st.n_elec, np.float64)
+            if n.max() > n.min():
+                w = (n - n.min()) / (n.max() - n.min())
+                fr[k] = sum(occ[k, t] * w[t] for t in range(len(n))) / W.n_obs
+        out.append(fr)
+    return out
+
+
+def fit_hill(kind, x, f, T=300.0, v=1.0):
+    """Least-squares fit of eq (1) (kind "pH": f = 1/(1 + 10^(n (pH - pKa))))
+    or eq (2) (kind "redox": f = 1/(1 + exp(n v F (E - E0)/(kB T)))) to the
+    fractions f at x.  Minimises the sum of squared fraction residuals with
+    scipy's Levenberg-Marquardt, started from a straight-line fit of the Hill
+    plot.  Returns (x0, n, rss)."""
+    from scipy.optimize import least_squares
+
+    x = np.asarray(x, np.float64)
+    f = np.asarray(f, np.float64)
+
+    def model(p):
+        return f_prot(x, p[0], p[1]) if kind == "pH" else f_red(x, p[0], T, v, p[1])
+
+    c = LN10 if kind == "pH" else v * FARADAY / (KB * T)
+    inside = (f > 0) & (f < 1)
+    fc = np.clip(f[inside], 1e-6, 1 - 1e-6)
+    slope, icpt = np.polyfit(x[inside], np.log((1 - fc) / fc) / c, 1)
+    res = least_squares(lambda p: f - model(p), [-icpt / slope, slope], method="lm",
+                        xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    return float(res.x[0]), float(res.x[1]), float(np.sum(res.fun ** 2))
 
 
 from .run import (Walkers, exchange_attempt, exchange_exponent, mc_sweep,  # noqa: E402,F401

@@ -12,7 +12,11 @@ Schedule of global step t (x_t are the positions after t MD steps):
      dimension of the user order (one dimension per attempt, nearest
      neighbours that share the other two conditions; multidimensional REMD
      section);
-  5. Langevin step to x_{t+1} at the walker's current temperature.
+  5. one sample of the observables: the state of every site of every walker
+     is counted at the walker's current condition, and the walker's visit to
+     that condition (the per-condition fractions that eqs (1) and (2) are
+     fitted to in the results, and Figure 7's visitation counts);
+  6. Langevin step to x_{t+1} at the walker's current temperature.
 """
 from __future__ import annotations
 
@@ -79,6 +83,12 @@ class Walkers:
         self.mc_log = []
         self.ex_log = []
         self.threads = 1
+        # observables: occ[s][k, state] samples of site k at condition slot s,
+        # visits[w, s] samples of walker w at slot s, n_obs samples taken
+        self.occ = [np.zeros((len(self.systems[self.sys_of[s]].sites), 8), np.int64)
+                    for s in range(ns)]
+        self.visits = np.zeros((ns, ns), np.int64)
+        self.n_obs = 0
 
     # -- conditions of a walker
     def cond(self, w):
@@ -252,6 +262,13 @@ def run_schedule(W: Walkers, n_steps: int, walkers=None):
             dim = W.grid.order[W.n_events % len(W.grid.order)]
             W.n_events += 1
             exchange_attempt(W, dim, t)
+
+        for w in ws:
+            s = int(W.slot_of[w])
+            W.visits[w, s] += 1
+            for k, st in enumerate(W.state[w]):
+                W.occ[s][k, st] += 1
+        W.n_obs += 1
 
         def step(w):
             o = W.osys[W.sys_of[w]]

@@ -1,6 +1,6 @@
 """In-tree build of libcphremd.so for sm_103a (nvcc, no cmake).
 
-The two translation units compile in parallel; the CUDA runtime is linked
+The translation units compile in parallel; the CUDA runtime is linked
 statically so the library only needs the driver at run time."""
 from __future__ import annotations
 
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcphremd.so")
-SOURCES = ["cph_engine.cu", "cph_grad.cu"]
+SOURCES = ["cph_engine.cu", "cph_grad.cu", "cph_analysis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -22,6 +22,8 @@ MC_PH, MC_REDOX, MC_BOTH = 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_REPLICA = 0, 1
 NTERMS = 6
+MAX_STATES = 8
+FIT_PH, FIT_REDOX = 1, 2
 TERMS = ("gb", "coul", "lj", "bond", "angle", "total")
 DIM_NAMES = {"E": DIM_E, "pH": DIM_PH, "T": DIM_T}
 
@@ -122,6 +124,12 @@ def lib():
             "cph_get_condition_map": ([vp, vp, vp], i),
             "cph_set_condition_map": ([vp, vp, vp], i),
             "cph_get_accept_stats": ([vp, vp, vp], i),
+            "cph_get_occupancy": ([vp, vp, vp, vp], i),
+            "cph_get_visits": ([vp, vp, vp], i),
+            "cph_get_fractions": ([vp, vp, vp], i),
+            "cph_reset_observables": ([vp, vp], i),
+            "cph_fit_hill": ([i, i, vp, vp, C.c_double, C.c_double, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_double)], i),
             "cph_get_reference_energies": ([vp, vp], i),
             "cph_get_mc_records": ([vp, vp, i, vp, vp], i),
             "cph_get_exchange_records": ([vp, vp, i, vp, vp], i),
@@ -295,6 +303,24 @@ class Engine:
     def accept_stats(self, stream=None):
         return self._get(lib().cph_get_accept_stats, (10,), np.int64, stream=stream)
 
+    # ---- sampling observables
+    def occupancy(self, stream=None):
+        """(counts [site rows, MAX_STATES] int64, samples): row
+        site_offsets[s] + k is site k of the walker at condition slot s."""
+        out = np.zeros((int(self.site_offsets[-1]), MAX_STATES), np.int64)
+        n = C.c_int64(0)
+        self._c(lib().cph_get_occupancy(self.ptr, _p(out), C.byref(n), _stream(stream)))
+        return out, int(n.value)
+
+    def visits(self, stream=None):
+        return self._get(lib().cph_get_visits, (self.W, self.W), np.int64, stream=stream)
+
+    def fractions(self, stream=None):
+        return self._get(lib().cph_get_fractions, (int(self.site_offsets[-1]),), stream=stream)
+
+    def reset_observables(self, stream=None):
+        self._c(lib().cph_reset_observables(self.ptr, _stream(stream)))
+
     def set_positions(self, x, stream=None):
         self._c(lib().cph_set_positions(self.ptr, _p(_f64(x).reshape(-1)), _stream(stream)))
 
@@ -357,6 +383,18 @@ class Engine:
 
     def walker_slice(self, w):
         return slice(int(self.offsets[w]), int(self.offsets[w + 1]))
+
+
+def fit_hill(kind, x, f, T=300.0, v=1.0):
+    """Least-squares fit of eq (1) (kind FIT_PH) or eq (2) (FIT_REDOX) to the
+    fractions f at x: returns (x0, n_hill, rss)."""
+    x, f = _f64(x).reshape(-1), _f64(f).reshape(-1)
+    if x.size != f.size:
+        raise ValueError("x and f differ in length")
+    x0, n, rss = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().cph_fit_hill(kind, x.size, _p(x), _p(f), float(T), float(v), C.byref(x0),
+                              C.byref(n), C.byref(rss)))
+    return x0.value, n.value, rss.value
 
 
 def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.0,

@@ -89,10 +89,12 @@ __device__ inline long long to_fixed(float v, float scale) { return __float2ll_r
 __device__ inline long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
 
 // ---------------------------------------------- MUFU approximations (FP32)
-// Hand-written PTX for the special-function unit with denormals flushed: the
-// library's rsqrtf / expf wrappers add denormal handling around the same
-// approximation, and no operand of the pair loops comes near the denormal
-// range (distances >= ~1 A, exp(-D) underflowing to 0 is harmless).
+// The PTX ISA's approximate reciprocal square root and base-2 exponential in
+// their flush-to-zero forms (rsqrt.approx.ftz.f32, ex2.approx.ftz.f32), written
+// as inline PTX.  No operand of the pair loops comes near the denormal range
+// (distances >= ~1 A; exp(-D) underflowing to 0 is harmless), so flushing
+// changes no result; accuracy is covered by the parity tests against the
+// FP64 oracle.
 __device__ __forceinline__ float rsqrt_ftz(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

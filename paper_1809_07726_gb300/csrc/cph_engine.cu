@@ -197,6 +197,26 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
 }
 
 // =====================================================================
+// Sampling observables: one sample per walker per MD step, taken after the
+// step's MC sweeps and exchange attempt.  slot_of is a permutation, so every
+// (slot, site) row and every (walker, slot) cell has one writer per step:
+// plain read-modify-writes, exact and in a fixed order.
+// =====================================================================
+__global__ void k_observe(View V) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= V.W) return;
+    const int s = V.slot_of[w];
+    V.visits[(long long)w * V.W + s] += 1;
+    // the walker at slot s belongs to the system of the walker that started
+    // there, so slot s's rows are laid out like walker s's sites
+    const int ws0 = V.w_site_off[w], n = V.w_site_off[w + 1] - ws0;
+    const long long row0 = V.w_site_off[s];
+    for (int k = 0; k < n; ++k)
+        V.occ[(row0 + k) * CPH_MAX_STATES + V.site_state[ws0 + k]] += 1;
+    if (w == 0) *V.n_obs += 1;
+}
+
+// =====================================================================
 // Replica exchange (one CTA): one attempt along one dimension.
 // =====================================================================
 __device__ inline int walker_nprot(const View& V, int w) {
@@ -411,7 +431,7 @@ struct cph_engine {
     long long h_step = 0;
     int n_sys = 0;
     std::vector<int> h_sys_n, h_w_sys, h_w_off, h_w_site_off, h_sys_site_off;
-    std::vector<int> h_site_nst, h_site_kind;
+    std::vector<int> h_site_nst, h_site_kind, h_site_noff, h_site_np, h_site_ne;
     int n_site_states = 0;
     Item* d_items = nullptr;
     int n_items = 0;
@@ -665,6 +685,13 @@ int launch_exchange(cph_engine* E, int dim, int s_off, cudaStream_t st) {
     return CPH_OK;
 }
 
+int launch_observe(cph_engine* E, cudaStream_t st) {
+    const int bs = 128;
+    k_observe<<<(E->V.W + bs - 1) / bs, bs, 0, st>>>(E->V);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
 int launch_tick(cph_engine* E, long long n, cudaStream_t st) {
     k_tick<<<1, 1, 0, st>>>(E->V.step, n);
     CK(cudaGetLastError());
@@ -682,6 +709,7 @@ int enqueue_step(cph_engine* E, long long t, int s_off, bool full_schedule, cuda
     }
     TRY(launch_forces(E, exch, st, true, s_off, kinds));
     if (exch) TRY(launch_exchange(E, CPH_DIM_NEXT, s_off, st));
+    TRY(launch_observe(E, st));
     TRY(launch_langevin(E, s_off, st));
     return CPH_OK;
 }
@@ -1022,6 +1050,9 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     E->h_sys_site_off = sys_site_off;
     E->h_site_nst = site_nst;
     E->h_site_kind = site_kind;
+    E->h_site_noff = site_noff;
+    E->h_site_np = site_np;
+    E->h_site_ne = site_ne;
     E->n_site_states = (int)site_np.size();
     E->item_w_off = item_w_off;
     E->n_items = (int)items.size();
@@ -1131,6 +1162,9 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         V.ex_rec = (cph_exchange_record*)pe;
     }
     TRY(alloc0(E, 1, &d)); V.ex_n = d;
+    TRY(alloc0(E, std::max<size_t>(1, (size_t)w_site_off[W] * CPH_MAX_STATES), &dl)); V.occ = dl;
+    TRY(alloc0(E, (size_t)W * W, &dl)); V.visits = dl;
+    TRY(alloc0(E, 1, &dl)); V.n_obs = dl;
     std::vector<double> gE(grid->E, grid->E + grid->nE), gpH(grid->pH, grid->pH + grid->npH),
         gT(grid->T, grid->T + grid->nT);
     TRY(upload(E, gE, &dd)); V.gE = dd;
@@ -1444,6 +1478,55 @@ int cph_set_condition_map(cph_engine* e, const int* slot_of_walker, void* stream
 }
 int cph_get_accept_stats(cph_engine* e, int64_t* out, void* stream) {
     return copy_out(e, out, e ? e->V.stats : nullptr, 10 * sizeof(long long), stream);
+}
+int cph_get_occupancy(cph_engine* e, int64_t* out, int64_t* n_samples, void* stream) {
+    if (!e || !out) return fail(e, CPH_E_INVALID, "NULL argument");
+    const size_t rows = (size_t)e->h_w_site_off.back();
+    if (rows) TRY(copy_out(e, out, e->V.occ, rows * CPH_MAX_STATES * sizeof(long long), stream));
+    if (n_samples) TRY(copy_out(e, n_samples, e->V.n_obs, sizeof(long long), stream));
+    return CPH_OK;
+}
+int cph_get_visits(cph_engine* e, int64_t* out, void* stream) {
+    if (!e || !out) return fail(e, CPH_E_INVALID, "NULL argument");
+    return copy_out(e, out, e->V.visits, (size_t)e->V.W * e->V.W * sizeof(long long), stream);
+}
+int cph_get_fractions(cph_engine* e, double* out, void* stream) {
+    if (!e || !out) return fail(e, CPH_E_INVALID, "NULL argument");
+    const int W = e->V.W;
+    const size_t rows = (size_t)e->h_w_site_off.back();
+    std::vector<long long> occ(std::max<size_t>(1, rows * CPH_MAX_STATES));
+    long long ns = 0;
+    if (rows) TRY(copy_out(e, occ.data(), e->V.occ, rows * CPH_MAX_STATES * sizeof(long long), stream));
+    TRY(copy_out(e, &ns, e->V.n_obs, sizeof(long long), stream));
+    if (ns <= 0) return fail(e, CPH_E_STATE, "no observable sample taken yet");
+    // rows of slot s follow the sites of the system that starts at slot s
+    for (int s = 0; s < W; ++s) {
+        const int sys = e->h_w_sys[s];
+        for (int g = e->h_sys_site_off[sys], k = 0; g < e->h_sys_site_off[sys + 1]; ++g, ++k) {
+            const int* n = (e->h_site_kind[g] == CPH_SITE_PH ? e->h_site_np.data() : e->h_site_ne.data()) +
+                           e->h_site_noff[g];
+            const int nst = e->h_site_nst[g];
+            int lo = n[0], hi = n[0];
+            for (int t = 1; t < nst; ++t) lo = std::min(lo, n[t]), hi = std::max(hi, n[t]);
+            const size_t row = (size_t)e->h_w_site_off[s] + k;
+            double acc = 0.0;
+            if (hi > lo)
+                for (int t = 0; t < nst; ++t)
+                    acc += (double)occ[row * CPH_MAX_STATES + t] * (double)(n[t] - lo) / (double)(hi - lo);
+            out[row] = acc / (double)ns;
+        }
+    }
+    return CPH_OK;
+}
+int cph_reset_observables(cph_engine* e, void* stream) {
+    if (!e) return fail(e, CPH_E_INVALID, "NULL argument");
+    cph_engine* E = e;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rows = (size_t)e->h_w_site_off.back();
+    if (rows) CK(cudaMemsetAsync(e->V.occ, 0, rows * CPH_MAX_STATES * sizeof(long long), st));
+    CK(cudaMemsetAsync(e->V.visits, 0, (size_t)e->V.W * e->V.W * sizeof(long long), st));
+    CK(cudaMemsetAsync(e->V.n_obs, 0, sizeof(long long), st));
+    return CPH_OK;
 }
 int cph_get_reference_energies(cph_engine* e, double* out) {
     return copy_out(e, out, e ? e->V.site_uref : nullptr, sizeof(double) * (e ? e->n_site_states : 0), nullptr);

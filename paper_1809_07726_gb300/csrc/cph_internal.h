@@ -10,6 +10,8 @@
 //   sigh, sqe, mass  double [system atoms]       sigma/2, sqrt(eps), mass
 //   eacc             int64  [W * 5]              fixed-point (2^32) energy terms per walker
 //   Ffix, dRfix      int64  [3N], [N]            fixed-point (2^32) pair-force and dE/dR sums
+//   occ              int64  [sites * 8]          state counts per (slot, site) row
+//   visits           int64  [W * W]              samples per (walker, slot)
 #pragma once
 #include <cstdint>
 #include "../../include/cphremd.h"
@@ -63,6 +65,8 @@ struct View {
     cph_mc_record* mc_rec;
     cph_exchange_record* ex_rec;
     int* ex_n;
+    // sampling observables: per (slot, site) state counts, per (walker, slot) visits, samples
+    long long *occ, *visits, *n_obs;
     // grid
     const double *gE, *gpH, *gT;
     int nE, npH, nT, n_order;

@@ -265,6 +265,27 @@ def slot_index(iE: int, ipH: int, iT: int, nE: int, npH: int) -> int:
     return iE + nE * (ipH + npH * iT)
 
 
+def titratable_ion(kind: str, ref: float, rho: float = 1.6) -> System:
+    """One atom that is a whole titratable site.  pH: state 0 protonated
+    (q = 0, one proton), state 1 deprotonated (q = -1).  Redox: state 0
+    oxidised (q = 0), state 1 reduced (q = -1, one electron).  A lone atom has
+    no descreening partner, so its Born radius, and with it every state's
+    electrostatic energy, is the same at any position."""
+    z = np.zeros(1)
+    q = np.array([[0.0], [-1.0]])
+    if kind == "ph":
+        site = Site("ph", np.zeros(1, np.int32), q, np.array([1, 0], np.int32),
+                    np.zeros(2, np.int32), float(ref))
+    else:
+        site = Site("redox", np.zeros(1, np.int32), q, np.zeros(2, np.int32),
+                    np.array([0, 1], np.int32), float(ref))
+    return System(x=np.zeros((1, 3)), mass=np.array([16.0]), q=z.copy(), rho=np.array([rho]),
+                  screen=np.array([0.85]), sigma=np.array([3.0]), eps=np.array([0.1]),
+                  bonds=np.zeros((0, 2), np.int32), bond_k=z[:0].copy(), bond_r0=z[:0].copy(),
+                  angles=np.zeros((0, 3), np.int32), angle_k=z[:0].copy(),
+                  angle_t0=z[:0].copy(), sites=[site])
+
+
 # ---------------------------------------------------------------------------
 # The five workloads (systems + condition grids).  Seeds: 1 for the 160-atom
 # system, 2 for 2400 atoms, 3/4/5 for 500/2000/8000 atoms, 6 for the 8000-atom

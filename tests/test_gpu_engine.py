@@ -230,6 +230,15 @@ def test_fp64_whole_schedule_matches_oracle():
         np.testing.assert_allclose(x[eng.walker_slice(w)], W.x[w], rtol=0, atol=1e-9)
     np.testing.assert_array_equal(eng.condition_map(), W.slot_of)
     np.testing.assert_array_equal(eng.site_states(), np.concatenate(W.state))
+    # sampling observables: identical decisions give identical integer counts
+    occ, n_samples = eng.occupancy()
+    assert n_samples == W.n_obs == n
+    for s in range(grid.n_slots):
+        rows = occ[eng.site_offsets[s]:eng.site_offsets[s + 1]]
+        np.testing.assert_array_equal(rows, W.occ[s])
+    np.testing.assert_array_equal(eng.visits(), W.visits)
+    np.testing.assert_allclose(eng.fractions(), np.concatenate(oracle.site_fractions(W)),
+                               rtol=1e-14, atol=0)
 
 
 def test_fp32_langevin_step_matches_oracle():
