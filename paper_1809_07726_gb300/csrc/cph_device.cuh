@@ -119,33 +119,42 @@ constexpr float kHctXmax = 0.35f;
 //   S(y) = sum 2k y^(k-1) = 2/(1-y)^2,
 // with max relative errors 3.5e-9, 1.4e-8 and 1.8e-8 (gen_hct_poly.py derives
 // the coefficients).
-__device__ __forceinline__ float hct_series_h(float y) { // P
-    float p = 1.361160215f;
-    p = fmaf(p, y, 0.8443080909f);
-    p = fmaf(p, y, 0.8931260308f);
-    p = fmaf(p, y, 0.8570198603f);
-    p = fmaf(p, y, 0.8000012903f);
-    p = fmaf(p, y, 0.6666666645f);
+// Packed FP32: one float2 carries the same quantity for two pairs, and
+// fma.rn.f32x2 / add / mul (sm_100 and later) work on both halves in one
+// instruction.  The helpers below take float or float2 alike.
+__device__ __forceinline__ float fma_p(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 fma_p(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class T> __device__ __forceinline__ T splat(float v);
+template <> __device__ __forceinline__ float splat<float>(float v) { return v; }
+template <> __device__ __forceinline__ float2 splat<float2>(float v) { return make_float2(v, v); }
+
+template <class T> __device__ __forceinline__ T hct_series_h(T y) { // P
+    T p = splat<T>(1.361160215f);
+    p = fma_p(p, y, splat<T>(0.8443080909f));
+    p = fma_p(p, y, splat<T>(0.8931260308f));
+    p = fma_p(p, y, splat<T>(0.8570198603f));
+    p = fma_p(p, y, splat<T>(0.8000012903f));
+    p = fma_p(p, y, splat<T>(0.6666666645f));
     return p;
 }
 
-__device__ __forceinline__ float hct_series_dr(float y) { // Q
-    float p = 20.1395503f;
-    p = fmaf(p, y, 9.836372412f);
-    p = fmaf(p, y, 8.959016539f);
-    p = fmaf(p, y, 6.855114687f);
-    p = fmaf(p, y, 4.800021136f);
-    p = fmaf(p, y, 2.666666631f);
+template <class T> __device__ __forceinline__ T hct_series_dr(T y) { // Q
+    T p = splat<T>(20.1395503f);
+    p = fma_p(p, y, splat<T>(9.836372412f));
+    p = fma_p(p, y, splat<T>(8.959016539f));
+    p = fma_p(p, y, splat<T>(6.855114687f));
+    p = fma_p(p, y, splat<T>(4.800021136f));
+    p = fma_p(p, y, splat<T>(2.666666631f));
     return p;
 }
 
-__device__ __forceinline__ float hct_series_ds(float y) { // S
-    float p = 18.77114444f;
-    p = fmaf(p, y, 8.994253274f);
-    p = fmaf(p, y, 8.065659941f);
-    p = fmaf(p, y, 5.998104684f);
-    p = fmaf(p, y, 4.0000197f);
-    p = fmaf(p, y, 1.999999967f);
+template <class T> __device__ __forceinline__ T hct_series_ds(T y) { // S
+    T p = splat<T>(18.77114444f);
+    p = fma_p(p, y, splat<T>(8.994253274f));
+    p = fma_p(p, y, splat<T>(8.065659941f));
+    p = fma_p(p, y, splat<T>(5.998104684f));
+    p = fma_p(p, y, splat<T>(4.0000197f));
+    p = fma_p(p, y, splat<T>(1.999999967f));
     return p;
 }
 

@@ -598,6 +598,17 @@ int launch_sym_pair(cph_engine* E, const SymItem* items, int n, bool energy, int
     return CPH_OK;
 }
 
+// operand staging of the FP32 pair kernels: positions before the Born-radii
+// pass, charge and radius terms before the GB pass (after any MC sweep)
+int launch_stage(cph_engine* E, int pass, int a0, int n, cudaStream_t st) {
+    const int bs = 256, g = (n + bs - 1) / bs;
+    if (n <= 0 || pass == 2) return CPH_OK;
+    if (pass == 0) k_stage_x<<<g, bs, 0, st>>>(E->V, a0, n);
+    else k_stage_gb<<<g, bs, 0, st>>>(E->V, a0, n);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
 int launch_atoms(cph_engine* E, int which, bool energy, int a0, int n, cudaStream_t st) {
     const int bs = 256, g = (n + bs - 1) / bs;
     if (n <= 0) return CPH_OK;
@@ -633,6 +644,7 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
             return pass == 1 ? launch_gb(E, E->d_items, E->n_items, energy, st)
                              : launch_chain(E, E->d_items, E->n_items, energy, st);
         }
+        TRY(launch_stage(E, pass, 0, E->V.total_atoms, st));
         TRY(launch_sym_pair(E, E->d_sym, E->n_sym, energy, pass, st));
         if (pass == 2) TRY(launch_bonded(E, energy, 0, E->V.W, st));
         return launch_atoms(E, fin, energy, 0, E->V.total_atoms, st);
@@ -644,6 +656,7 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
             if (pass == 0) TRY(launch_born(E, it, ni, energy, st));
             else TRY(pass == 1 ? launch_gb(E, it, ni, energy, st) : launch_chain(E, it, ni, energy, st));
         } else {
+            TRY(launch_stage(E, pass, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], st));
             TRY(launch_sym_pair(E, E->d_sym_by_w + E->sym_w_off[w], E->sym_w_off[w + 1] - E->sym_w_off[w],
                                 energy, pass, st));
             if (pass == 2) TRY(launch_bonded(E, energy, w, 1, st));
@@ -1077,6 +1090,18 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(upload(E, sigh, &dd)); V.sigh = dd;
     TRY(upload(E, sqe, &dd)); V.sqe = dd;
     TRY(upload(E, mass, &dd)); V.mass = dd;
+    {
+        std::vector<float4> pb(rt.size());
+        std::vector<float2> pl(rt.size());
+        for (size_t p = 0; p < rt.size(); ++p) {
+            pb[p] = make_float4((float)sc[p], (float)rt[p], (float)(1.0 / rt[p]), 0.f);
+            pl[p] = make_float2((float)sigh[p], (float)sqe[p]);
+        }
+        float4* d4;
+        float2* d2;
+        TRY(upload(E, pb, &d4)); V.pb32 = d4;
+        TRY(upload(E, pl, &d2)); V.plj32 = d2;
+    }
     TRY(upload(E, excl_off, &d)); V.excl_off = d;
     TRY(upload(E, excl_j, &d)); V.excl_j = d;
     TRY(upload(E, bond_off, &d)); V.bond_off = d;
@@ -1132,6 +1157,13 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(alloc0(E, 3 * (size_t)total, &dfx)); V.Ffix = dfx;
     TRY(alloc0(E, (size_t)total, &dfx)); V.dRfix = dfx;
     TRY(alloc0(E, (size_t)total, &dfx)); V.Hfix = dfx;
+    {
+        float4* d4;
+        float* d1;
+        TRY(alloc0(E, (size_t)total, &d4)); V.xs = d4;
+        TRY(alloc0(E, (size_t)total, &d4)); V.gq = d4;
+        TRY(alloc0(E, (size_t)total, &d1)); V.c32 = d1;
+    }
     long long* dl;
     TRY(alloc0(E, (size_t)W * kEAcc, &dl)); V.eacc = dl;
     std::vector<int> ident(W);

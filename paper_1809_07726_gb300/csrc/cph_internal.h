@@ -10,6 +10,9 @@
 //   sigh, sqe, mass  double [system atoms]       sigma/2, sqrt(eps), mass
 //   eacc             int64  [W * 5]              fixed-point (2^32) energy terms per walker
 //   Ffix, dRfix      int64  [3N], [N]            fixed-point (2^32) pair-force and dE/dR sums
+//   xs, gq           float4 [total_atoms]        FP32 positions / GB terms for the pair kernels
+//   c32              float  [total_atoms]        FP32 chain-rule weights
+//   pb32, plj32      float4, float2 [system atoms] static FP32 radii / LJ parameters
 //   occ              int64  [sites * 8]          state counts per (slot, site) row
 //   visits           int64  [W * W]              samples per (walker, slot)
 #pragma once
@@ -74,6 +77,12 @@ struct View {
     // parameters
     double tau, inv_eps_in, sqrt_k, alpha, beta, gamma, offset, dt, gamma_ln;
     float rfar2; // pairs with r^2 >= rfar2 are in the series regime in both directions
+    // FP32 pair-kernel operands, staged once per step by one thread per atom
+    float4* xs;          // (x, y, z, 0) relative to the walker's first atom
+    float4* gq;          // (sqrt(k) q, R, 1/R, log2(e) / (4 R)), after the Born radii and MC
+    float* c32;          // chain-rule weights c
+    const float4* pb32;  // per system atom, static: (s, rt, 1/rt, 0)
+    const float2* plj32; // per system atom, static: (sigma/2, sqrt(eps))
     unsigned long long seed;
 };
 

@@ -87,165 +87,235 @@ __device__ __forceinline__ float hct_dr_series(float rinv2, float rinv, float s)
     return -x * y * hct_series_dr(y) * rinv2;
 }
 
+// ============================================== operand staging (FP32)
+// The pair kernels read FP32 operands only.  Positions are taken relative to
+// the walker's first atom (|x| stays within the molecule's extent, so FP32
+// keeps ~4e-6 A at 40 A) and rounded once per step; the charge and Born-radius
+// terms are rounded once per step after the Born radii and any MC sweep.
+__global__ void k_stage_x(View V, int a0, int n) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int a = a0 + l, o = V.w_off[V.a_walker[a]];
+    V.xs[a] = make_float4((float)(V.x[3 * a] - V.x[3 * o]), (float)(V.x[3 * a + 1] - V.x[3 * o + 1]),
+                          (float)(V.x[3 * a + 2] - V.x[3 * o + 2]), 0.f);
+}
+
+__global__ void k_stage_gb(View V, int a0, int n) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int a = a0 + l;
+    const float R = (float)V.R[a], iR = __frcp_rn(R);
+    V.gq[a] = make_float4((float)(V.q[a] * V.sqrt_k), R, iR, (0.25f * kLog2e) * iR);
+}
+
 // ====================================================== GB + Coulomb + LJ
-struct GbI {
-    float x, y, z;
-    float q;   // sqrt(k) q_i
-    float qc;  // sqrt(k) q_i / eps_in
-    float R;   // Born radius
-    float dk;  // log2(e) / (4 R_i): D log2(e) = r^2 dk_i / R_j
-    float sg;  // sigma_i / 2
-    float se4; // 4 sqrt(eps_i)
+// Packed over partner tiles: j-tiles are taken two at a time (A, B), and at
+// step k lane l pairs each of its two i atoms with partner l + k of both
+// tiles; the halves of every float2 belong to tile A and tile B.  The i atom's
+// values sit in both halves (set once per item), partner data is staged
+// tile-interleaved (SoA, 16-byte rows, no bank conflicts), and the partner
+// sums travel as float2 (one shuffle per half).  Each half sees exactly the
+// arithmetic of one tile, so results do not depend on how tiles are paired.
+struct GbI2 {
+    float2 x, y, z;
+    float2 q;   // sqrt(k) q_i
+    float2 R;   // Born radius
+    float2 dk;  // log2(e) / (4 R_i): D log2(e) = r^2 dk_i / R_j
+    float2 sg;  // sigma_i / 2
+    float2 se4; // 4 sqrt(eps_i)
 };
 
-struct GbAcc {
-    float x, y, z, dr;
+// one staged pair of j-tiles, two copies in a row (partner l + k at l + k)
+struct GbJs {
+    float4 a[2 * kSymJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kSymJ]; // (-zA, -zB, qA, qB), q = sqrt(k) q_j
+    float4 c[2 * kSymJ]; // (RA, RB, 1/RA, 1/RB)
+    float4 d[2 * kSymJ]; // (sigmaA/2, sigmaB/2, sqrt(epsA), sqrt(epsB))
+};
+
+// masks of the two i atoms against the tile pair: bit jj of sk = pair not
+// counted, bit jj of nb = no Coulomb / LJ; [u][0] tile A, [u][1] tile B
+struct GbMask {
+    uint32_t sk[2][2], nb[2][2];
 };
 
 template <bool MASKED, bool ENERGY>
-__device__ __forceinline__ void gb_tile(const float4* sa, const float4* sb, int lane, const GbI (&I)[2],
-                                        GbAcc (&a)[2], GbAcc& jacc, const uint32_t (&skip)[2],
-                                        const uint32_t (&nbm)[2], float tau, float iei,
+__device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I)[2], float2 (&a)[2][4],
+                                        float2 (&ja)[4], const GbMask& m, float tau, float iei,
                                         KSum<float>& egb, KSum<float>& ec, KSum<float>& elj) {
+    const int src = (lane + 1) & 31;
+    const float2 ln2 = splat<float2>(kLn2), one = splat<float2>(1.f), c12 = splat<float2>(12.f),
+                 cm6 = splat<float2>(-6.f), mtau = splat<float2>(-tau), mq = splat<float2>(-0.25f),
+                 ie = splat<float2>(iei);
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
-        const int jj = (lane + k) & (kSymJ - 1);
-        const float4 A = sa[jj];
-        const float4 B = sb[jj];
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k], D = sj.d[lane + k];
+        const float2 qj = make_float2(B.z, B.w), Rj = make_float2(C.x, C.y);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const float dx = I[u].x - A.x, dy = I[u].y - A.y, dz = I[u].z - A.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float g = 1.f, nb = 1.f;
+            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            float2 qq = __fmul2_rn(I[u].q, qj);
+            float2 ep4 = __fmul2_rn(I[u].se4, make_float2(D.z, D.w));
             if (MASKED) {
-                const bool sk = (skip[u] >> jj) & 1u;
-                g = sk ? 0.f : 1.f;
-                nb = ((nbm[u] >> jj) & 1u) ? 0.f : 1.f;
-                r2 = sk ? 1.f : r2;
+                const int jj = (lane + k) & (kSymJ - 1);
+                const bool s0 = (m.sk[u][0] >> jj) & 1u, s1 = (m.sk[u][1] >> jj) & 1u;
+                const bool b0 = (m.nb[u][0] >> jj) & 1u, b1 = (m.nb[u][1] >> jj) & 1u;
+                r2.x = s0 ? 1.f : r2.x;
+                r2.y = s1 ? 1.f : r2.y;
+                qq.x = s0 ? 0.f : qq.x;
+                qq.y = s1 ? 0.f : qq.y;
+                ep4.x = b0 ? 0.f : ep4.x;
+                ep4.y = b1 ? 0.f : ep4.y;
             }
-            const float rinv = rsqrt_ftz(r2);
-            const float rinv2 = rinv * rinv;
-            const float qq = I[u].q * A.w;
-            const float D2 = r2 * (I[u].dk * B.y); // D log2(e), D = r^2 / (4 R_i R_j)
-            const float e = exp2_ftz(-D2);
-            const float fi = rsqrt_ftz(fmaf(I[u].R * B.x, e, r2));
-            const float qf3 = (MASKED ? g * qq : qq) * fi * fi * fi;
-            const float t = qf3 * e * fmaf(D2, kLn2, 1.f);
-            a[u].dr = fmaf(t, B.x, a[u].dr);
-            jacc.dr = fmaf(t, I[u].R, jacc.dr);
-            const float sig = I[u].sg + B.z;
-            const float sr2 = sig * sig * rinv2;
-            const float sr6 = sr2 * sr2 * sr2;
-            const float ep4 = (MASKED ? nb * I[u].se4 : I[u].se4) * B.w;
-            const float cq = (MASKED ? nb * I[u].qc : I[u].qc) * A.w;
-            const float fs = fmaf(cq, rinv, ep4 * sr6 * fmaf(12.f, sr6, -6.f)) * rinv2
-                           - tau * qf3 * fmaf(-0.25f, e, 1.f);
-            a[u].x = fmaf(fs, dx, a[u].x);
-            a[u].y = fmaf(fs, dy, a[u].y);
-            a[u].z = fmaf(fs, dz, a[u].z);
-            jacc.x = fmaf(-fs, dx, jacc.x);
-            jacc.y = fmaf(-fs, dy, jacc.y);
-            jacc.z = fmaf(-fs, dz, jacc.z);
+            float2 cq = __fmul2_rn(qq, ie); // sqrt(k) q_i sqrt(k) q_j / eps_in
+            if (MASKED) {
+                const int jj = (lane + k) & (kSymJ - 1);
+                cq.x = ((m.nb[u][0] >> jj) & 1u) ? 0.f : cq.x;
+                cq.y = ((m.nb[u][1] >> jj) & 1u) ? 0.f : cq.y;
+            }
+            const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+            const float2 D2 = __fmul2_rn(r2, __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
+            const float2 e = make_float2(exp2_ftz(-D2.x), exp2_ftz(-D2.y));
+            const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2);
+            const float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
+            const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
+            const float2 t = __fmul2_rn(__fmul2_rn(qf3, e), __ffma2_rn(D2, ln2, one));
+            a[u][3] = __ffma2_rn(t, Rj, a[u][3]);
+            ja[3] = __ffma2_rn(t, I[u].R, ja[3]);
+            const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
+            const float2 sr2 = __fmul2_rn(__fmul2_rn(sig, sig), rinv2);
+            const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+            const float2 l6 = __fmul2_rn(ep4, sr6);
+            const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
+            const float2 w = __fmul2_rn(__fmul2_rn(mtau, qf3), __ffma2_rn(mq, e, one));
+            const float2 fs = __ffma2_rn(__ffma2_rn(cq, rinv, lj), rinv2, w);
+            const float2 mfs = make_float2(-fs.x, -fs.y);
+            a[u][0] = __ffma2_rn(fs, dx, a[u][0]);
+            a[u][1] = __ffma2_rn(fs, dy, a[u][1]);
+            a[u][2] = __ffma2_rn(fs, dz, a[u][2]);
+            ja[0] = __ffma2_rn(mfs, dx, ja[0]);
+            ja[1] = __ffma2_rn(mfs, dy, ja[1]);
+            ja[2] = __ffma2_rn(mfs, dz, ja[2]);
             if (ENERGY) {
-                egb.add((MASKED ? g * qq : qq) * fi);
-                ec.add(cq * rinv);
-                elj.add(ep4 * sr6 * (sr6 - 1.f));
+                const float2 eg = __fmul2_rn(qq, fi), eco = __fmul2_rn(cq, rinv);
+                const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
+                egb.add(eg.x);
+                egb.add(eg.y);
+                ec.add(eco.x);
+                ec.add(eco.y);
+                elj.add(el.x);
+                elj.add(el.y);
             }
         }
-        const int src = (lane + 1) & 31;
-        jacc.x = __shfl_sync(0xffffffffu, jacc.x, src);
-        jacc.y = __shfl_sync(0xffffffffu, jacc.y, src);
-        jacc.z = __shfl_sync(0xffffffffu, jacc.z, src);
-        jacc.dr = __shfl_sync(0xffffffffu, jacc.dr, src);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            ja[c].x = __shfl_sync(0xffffffffu, ja[c].x, src);
+            ja[c].y = __shfl_sync(0xffffffffu, ja[c].y, src);
+        }
     }
 }
 
 template <bool ENERGY>
-__global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymG * kSymJ], sb[kSymG * kSymJ];
-    __shared__ float red[kSymG][4][kSymJ][4];
-    __shared__ long long sfx[kSymI][4]; // i-side fixed-point sums (each thread owns two rows)
+__global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __restrict__ items, View V) {
+    __shared__ GbJs sj[kSymG / 2];
+    __shared__ __align__(16) float red[kSymG][4][kSymJ][4];
+    __shared__ long long sfx[4][kSymI]; // i-side fixed-point sums, component-major (conflict-free)
     __shared__ double ered[kSymThreads / 32][3];
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1], cz = V.x[3 * (A + it.i0) + 2];
-    const float sqk = (float)V.sqrt_k, tau = (float)V.tau, iei = (float)V.inv_eps_in;
+    const float tau = (float)V.tau, iei = (float)V.inv_eps_in;
     int ii[2];
     bool vi[2];
-    GbI I[2];
+    GbI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < N;
         const int i = vi[u] ? ii[u] : it.i0;
-        I[u].x = vi[u] ? (float)(V.x[3 * (A + i)] - cx) : -kFarF;
-        I[u].y = vi[u] ? (float)(V.x[3 * (A + i) + 1] - cy) : -kFarF;
-        I[u].z = vi[u] ? (float)(V.x[3 * (A + i) + 2] - cz) : -kFarF;
-        I[u].q = vi[u] ? (float)(V.q[A + i] * V.sqrt_k) : 0.f;
-        I[u].qc = vi[u] ? (float)(V.q[A + i] * V.sqrt_k * V.inv_eps_in) : 0.f;
-        I[u].R = vi[u] ? (float)V.R[A + i] : 1.f;
-        I[u].dk = vi[u] ? (float)(0.25 * 1.4426950408889634 / V.R[A + i]) : 1.f;
-        I[u].sg = vi[u] ? (float)V.sigh[P + i] : 0.f;
-        I[u].se4 = vi[u] ? (float)(4.0 * V.sqe[P + i]) : 0.f;
+        const float4 xi = V.xs[A + i], gi = V.gq[A + i];
+        const float2 li = V.plj32[P + i];
+        I[u].x = splat<float2>(vi[u] ? xi.x : -kFarF);
+        I[u].y = splat<float2>(vi[u] ? xi.y : -kFarF);
+        I[u].z = splat<float2>(vi[u] ? xi.z : -kFarF);
+        I[u].q = splat<float2>(vi[u] ? gi.x : 0.f);
+        I[u].R = splat<float2>(vi[u] ? gi.y : 1.f);
+        I[u].dk = splat<float2>(vi[u] ? gi.w : 1.f);
+        I[u].sg = splat<float2>(vi[u] ? li.x : 0.f);
+        I[u].se4 = splat<float2>(vi[u] ? 4.f * li.y : 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
+        for (int c = 0; c < 4; ++c) sfx[c][warp * 64 + u * 32 + lane] = 0;
     KSum<float> egb, ec, elj;
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
-        const int ng = min(kSymG, it.jt1 - g0);
+        const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
-            const int j = g0 * kSymJ + tid;
-            float4 a, b;
-            if (j < N) {
-                a = make_float4((float)(V.x[3 * (A + j)] - cx), (float)(V.x[3 * (A + j) + 1] - cy),
-                                (float)(V.x[3 * (A + j) + 2] - cz), (float)V.q[A + j] * sqk);
-                b = make_float4((float)V.R[A + j], (float)(1.0 / V.R[A + j]), (float)V.sigh[P + j],
-                                (float)V.sqe[P + j]);
-            } else {
-                a = make_float4(kFarF, kFarF, kFarF, 0.f);
-                b = make_float4(1.f, 1.f, 0.f, 0.f);
+        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
+            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
+            if (pr < npair) {
+                float v[2][8];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = 2 * pr + h, j = (g0 + g) * kSymJ + e;
+                    if (g < ng && j < N) {
+                        const float4 xj = V.xs[A + j], gj = V.gq[A + j];
+                        const float2 lj = V.plj32[P + j];
+                        v[h][0] = -xj.x; v[h][1] = -xj.y; v[h][2] = -xj.z; v[h][3] = gj.x;
+                        v[h][4] = gj.y; v[h][5] = gj.z; v[h][6] = lj.x; v[h][7] = lj.y;
+                    } else { // padding: far away, no charge, no LJ
+                        v[h][0] = -kFarF; v[h][1] = -kFarF; v[h][2] = -kFarF; v[h][3] = 0.f;
+                        v[h][4] = 1.f; v[h][5] = 1.f; v[h][6] = 0.f; v[h][7] = 0.f;
+                    }
+                }
+                GbJs& S = sj[pr];
+                const int r = e + cpy * kSymJ;
+                S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+                S.b[r] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+                S.c[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
+                S.d[r] = make_float4(v[0][6], v[1][6], v[0][7], v[1][7]);
             }
-            sa[tid] = a;
-            sb[tid] = b;
         }
         __syncthreads();
-        for (int g = 0; g < ng; ++g) {
-            const int jt = g0 + g, j0 = jt * kSymJ;
-            GbAcc jacc = {0.f, 0.f, 0.f, 0.f};
-            GbAcc acc[2] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-            uint32_t skip[2] = {0u, 0u}, nbm[2] = {0u, 0u};
-            if (jt == next) {
-                ++mp;
-                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+        for (int pr = 0; pr < npair; ++pr) {
+            const int jtA = g0 + 2 * pr; // tile B (jtA + 1) may lie past the item: padding
+            float2 ja[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            float2 acc[2][4] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}},
+                                {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
+            GbMask m = {};
+            bool masked = false;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm[u]);
-                gb_tile<true, ENERGY>(sa + g * kSymJ, sb + g * kSymJ, lane, I, acc, jacc, skip, nbm, tau,
-                                      iei, egb, ec, elj);
-            } else {
-                gb_tile<false, ENERGY>(sa + g * kSymJ, sb + g * kSymJ, lane, I, acc, jacc, skip, nbm, tau,
-                                       iei, egb, ec, elj);
-            }
+            for (int h = 0; h < 2; ++h) {
+                const int jt = jtA + h;
+                if (jt < it.jt1 && jt == next) {
+                    ++mp;
+                    next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+                    masked = true;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) { // per-tile conversion: independent of the item's chunking
-                long long* row = sfx[warp * 64 + u * 32 + lane];
-                row[0] += to_fixed(acc[u].x, (float)kScaleE);
-                row[1] += to_fixed(acc[u].y, (float)kScaleE);
-                row[2] += to_fixed(acc[u].z, (float)kScaleE);
-                row[3] += to_fixed(acc[u].dr, (float)kScaleE);
+                    for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, m.sk[u][h], m.nb[u][h]);
+                }
             }
-            // lane l now holds the partials of partner l of this tile
-            red[g][warp][lane][0] = jacc.x;
-            red[g][warp][lane][1] = jacc.y;
-            red[g][warp][lane][2] = jacc.z;
-            red[g][warp][lane][3] = jacc.dr;
+            if (masked) gb_tile<true, ENERGY>(sj[pr], lane, I, acc, ja, m, tau, iei, egb, ec, elj);
+            else gb_tile<false, ENERGY>(sj[pr], lane, I, acc, ja, m, tau, iei, egb, ec, elj);
+            // per-tile conversion (each half is one tile): independent of the item's chunking
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    sfx[c][warp * 64 + u * 32 + lane] +=
+                        to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
+            // lane l now holds the partials of partner l of both tiles
+            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(ja[0].x, ja[1].x, ja[2].x, ja[3].x);
+            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(ja[0].y, ja[1].y, ja[2].y, ja[3].y);
         }
         __syncthreads();
         // add the four warps' partials of every staged partner and send them
@@ -262,11 +332,11 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_gb_sym(const SymItem* __rest
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (vi[u]) {
-            const long long* row = sfx[warp * 64 + u * 32 + lane];
-            fix_add(&V.Ffix[3 * (A + ii[u])], row[0]);
-            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], row[1]);
-            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], row[2]);
-            fix_add(&V.dRfix[A + ii[u]], row[3]);
+            const int r = warp * 64 + u * 32 + lane;
+            fix_add(&V.Ffix[3 * (A + ii[u])], sfx[0][r]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], sfx[1][r]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], sfx[2][r]);
+            fix_add(&V.dRfix[A + ii[u]], sfx[3][r]);
         }
     }
     if (ENERGY) {
@@ -306,149 +376,194 @@ __global__ void k_fin_c(View V, int a0, int n) {
     const int P = V.sys_poff[V.w_sys[w]] + (a - V.w_off[w]);
     const double q = V.q[a] * V.sqrt_k, R = V.R[a];
     const double dEdR = 0.5 * V.tau * ((double)V.dRfix[a] / kScaleE + q * q / (R * R));
-    V.c[a] = dEdR * V.dRdpsi[a] * 0.5 * V.rt[P];
+    const double c = dEdR * V.dRdpsi[a] * 0.5 * V.rt[P];
+    V.c[a] = c;
+    V.c32[a] = (float)c;
     if (ENERGY)
         atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 0],
                   (unsigned long long)__double2ll_rn(-0.5 * V.tau * q * q / R * kScaleE));
 }
 
 // ========================================================= chain rule
-struct ChI {
-    float x, y, z, c, s, rt;
+// F_i -= sum_k c_k dI_k/dx_i with c = dE/dR dR/dpsi rt/2: for a pair, the force
+// along the separation is t = -(c_i dH(r, rt_i, s_j)/dr + c_j dH(r, rt_j, s_i)/dr) / r.
+// In the far regime dH/dr = -s^3 Q(s^2/r^2) / r^5, so
+// t = (c_i s_j^3 Q(s_j^2/r^2) + c_j s_i^3 Q(s_i^2/r^2)) / r^6.
+// Packed over partner tiles like the GB pass.
+struct ChI2 {
+    float2 x, y, z, c, s2, s3; // the i atom's value in both halves
+    float s, rt;               // closed-form operands
+};
+
+struct ChJs {
+    float4 a[2 * kSymJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kSymJ]; // (-zA, -zB, cA, cB)
+    float4 c[2 * kSymJ]; // (s2A, s2B, s3A, s3B)
+    float4 n[2 * kSymJ]; // (sA, sB, rtA, rtB): closed forms
 };
 
 template <bool MASKED>
-__device__ __forceinline__ void chain_tile(const float4* sa, const float2* sb, int lane, const ChI (&I)[2],
-                                           float (&ax)[2], float (&ay)[2], float (&az)[2], float& jx,
-                                           float& jy, float& jz, const uint32_t (&skip)[2], float rfar2) {
+__device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 (&I)[2], float2 (&a)[2][3],
+                                           float2 (&ja)[3], const uint32_t (&sk)[2][2], float rfar2) {
+    const int src = (lane + 1) & 31;
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
-        const int jj = (lane + k) & (kSymJ - 1);
-        const float4 A = sa[jj];
-        const float2 B = sb[jj];
-        float dx[2], dy[2], dz[2], r2[2], rinv[2], g[2];
-        bool sk[2] = {false, false}, nr[2];
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 cj = make_float2(B.z, B.w), s2j = make_float2(C.x, C.y), s3j = make_float2(C.z, C.w);
+        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            dx[u] = I[u].x - A.x;
-            dy[u] = I[u].y - A.y;
-            dz[u] = I[u].z - A.z;
-            r2[u] = fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u]));
+            dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            dy[u] = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            dz[u] = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx[u], dx[u], __ffma2_rn(dy[u], dy[u], __fmul2_rn(dz[u], dz[u])));
             if (MASKED) {
-                sk[u] = (skip[u] >> jj) & 1u;
-                r2[u] = sk[u] ? 1.f : r2[u];
+                const int jj = (lane + k) & (kSymJ - 1);
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? 1.f : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? 1.f : r2[u].y;
             }
-            rinv[u] = rsqrt_ftz(r2[u]);
-            const float rinv2 = rinv[u] * rinv[u];
-            g[u] = I[u].c * hct_dr_series(rinv2, rinv[u], B.x) + A.w * hct_dr_series(rinv2, rinv[u], I[u].s);
-            nr[u] = r2[u] < rfar2;
+            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 qj = hct_series_dr(__fmul2_rn(s2j, rinv2));
+            const float2 qi = hct_series_dr(__fmul2_rn(I[u].s2, rinv2));
+            const float2 term = __ffma2_rn(__fmul2_rn(I[u].c, s3j), qj, __fmul2_rn(__fmul2_rn(cj, I[u].s3), qi));
+            const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
+            t[u] = __fmul2_rn(term, __fmul2_rn(rinv4, rinv2));
         }
         // closed forms only where some lane has a pair inside r_far (rare)
-        if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
+        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        if (__any_sync(0xffffffffu, nr)) {
+            const float4 Nj = sj.n[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (nr[u]) {
-                    const float r = r2[u] * rinv[u];
-                    g[u] = I[u].c * hct_dr(r, rinv[u], I[u].rt, B.x) + A.w * hct_dr(r, rinv[u], B.y, I[u].s);
+                if (r2[u].x < rfar2) {
+                    const float r = r2[u].x * rinv[u].x;
+                    const float g = I[u].c.x * hct_dr(r, rinv[u].x, I[u].rt, Nj.x) + B.z * hct_dr(r, rinv[u].x, Nj.z, I[u].s);
+                    t[u].x = -g * rinv[u].x;
+                }
+                if (r2[u].y < rfar2) {
+                    const float r = r2[u].y * rinv[u].y;
+                    const float g = I[u].c.x * hct_dr(r, rinv[u].y, I[u].rt, Nj.y) + B.w * hct_dr(r, rinv[u].y, Nj.w, I[u].s);
+                    t[u].y = -g * rinv[u].y;
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            float gg = g[u];
-            if (MASKED) gg = sk[u] ? 0.f : gg;
-            const float t = -gg * rinv[u];
-            ax[u] = fmaf(t, dx[u], ax[u]);
-            ay[u] = fmaf(t, dy[u], ay[u]);
-            az[u] = fmaf(t, dz[u], az[u]);
-            jx = fmaf(-t, dx[u], jx);
-            jy = fmaf(-t, dy[u], jy);
-            jz = fmaf(-t, dz[u], jz);
+            if (MASKED) {
+                const int jj = (lane + k) & (kSymJ - 1);
+                t[u].x = ((sk[u][0] >> jj) & 1u) ? 0.f : t[u].x;
+                t[u].y = ((sk[u][1] >> jj) & 1u) ? 0.f : t[u].y;
+            }
+            const float2 mt = make_float2(-t[u].x, -t[u].y);
+            a[u][0] = __ffma2_rn(t[u], dx[u], a[u][0]);
+            a[u][1] = __ffma2_rn(t[u], dy[u], a[u][1]);
+            a[u][2] = __ffma2_rn(t[u], dz[u], a[u][2]);
+            ja[0] = __ffma2_rn(mt, dx[u], ja[0]);
+            ja[1] = __ffma2_rn(mt, dy[u], ja[1]);
+            ja[2] = __ffma2_rn(mt, dz[u], ja[2]);
         }
-        const int src = (lane + 1) & 31;
-        jx = __shfl_sync(0xffffffffu, jx, src);
-        jy = __shfl_sync(0xffffffffu, jy, src);
-        jz = __shfl_sync(0xffffffffu, jz, src);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ja[c].x = __shfl_sync(0xffffffffu, ja[c].x, src);
+            ja[c].y = __shfl_sync(0xffffffffu, ja[c].y, src);
+        }
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymG * kSymJ];
-    __shared__ float2 sb[kSymG * kSymJ];
-    __shared__ float red[kSymG][4][kSymJ][3];
-    __shared__ long long sfx[kSymI][3]; // i-side fixed-point sums (each thread owns two rows)
+__global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __restrict__ items, View V) {
+    __shared__ ChJs sj[kSymG / 2];
+    __shared__ __align__(16) float red[kSymG][4][kSymJ][4]; // component 3 unused (vector stores)
+    __shared__ long long sfx[3][kSymI]; // i-side fixed-point sums, component-major (conflict-free)
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1], cz = V.x[3 * (A + it.i0) + 2];
     const float rfar2 = V.rfar2;
     int ii[2];
     bool vi[2];
-    ChI I[2];
+    ChI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < N;
         const int i = vi[u] ? ii[u] : it.i0;
-        I[u].x = vi[u] ? (float)(V.x[3 * (A + i)] - cx) : -kFarF;
-        I[u].y = vi[u] ? (float)(V.x[3 * (A + i) + 1] - cy) : -kFarF;
-        I[u].z = vi[u] ? (float)(V.x[3 * (A + i) + 2] - cz) : -kFarF;
-        I[u].c = vi[u] ? (float)V.c[A + i] : 0.f;
-        I[u].s = vi[u] ? (float)V.sc[P + i] : 0.f;
-        I[u].rt = vi[u] ? (float)V.rt[P + i] : 1.f;
+        const float4 xi = V.xs[A + i], pi = V.pb32[P + i];
+        const float si = vi[u] ? pi.x : 0.f;
+        I[u].x = splat<float2>(vi[u] ? xi.x : -kFarF);
+        I[u].y = splat<float2>(vi[u] ? xi.y : -kFarF);
+        I[u].z = splat<float2>(vi[u] ? xi.z : -kFarF);
+        I[u].c = splat<float2>(vi[u] ? V.c32[A + i] : 0.f);
+        I[u].s2 = splat<float2>(si * si);
+        I[u].s3 = splat<float2>(si * si * si);
+        I[u].s = si;
+        I[u].rt = vi[u] ? pi.y : 1.f;
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
+        for (int c = 0; c < 3; ++c) sfx[c][warp * 64 + u * 32 + lane] = 0;
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
-        const int ng = min(kSymG, it.jt1 - g0);
+        const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
-            const int j = g0 * kSymJ + tid;
-            float4 a;
-            float2 b;
-            if (j < N) {
-                a = make_float4((float)(V.x[3 * (A + j)] - cx), (float)(V.x[3 * (A + j) + 1] - cy),
-                                (float)(V.x[3 * (A + j) + 2] - cz), (float)V.c[A + j]);
-                b = make_float2((float)V.sc[P + j], (float)V.rt[P + j]);
-            } else {
-                a = make_float4(kFarF, kFarF, kFarF, 0.f);
-                b = make_float2(0.f, 1.f);
+        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
+            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
+            if (pr < npair) {
+                float v[2][6];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = 2 * pr + h, j = (g0 + g) * kSymJ + e;
+                    if (g < ng && j < N) {
+                        const float4 xj = V.xs[A + j], pj = V.pb32[P + j];
+                        v[h][0] = -xj.x; v[h][1] = -xj.y; v[h][2] = -xj.z; v[h][3] = V.c32[A + j];
+                        v[h][4] = pj.x; v[h][5] = pj.y;
+                    } else { // padding: far away, no weight, no sphere
+                        v[h][0] = -kFarF; v[h][1] = -kFarF; v[h][2] = -kFarF; v[h][3] = 0.f;
+                        v[h][4] = 0.f; v[h][5] = 1.f;
+                    }
+                }
+                ChJs& S = sj[pr];
+                const int r = e + cpy * kSymJ;
+                const float s2a = v[0][4] * v[0][4], s2b = v[1][4] * v[1][4];
+                S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+                S.b[r] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+                S.c[r] = make_float4(s2a, s2b, s2a * v[0][4], s2b * v[1][4]);
+                S.n[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
             }
-            sa[tid] = a;
-            sb[tid] = b;
         }
         __syncthreads();
-        for (int g = 0; g < ng; ++g) {
-            const int jt = g0 + g, j0 = jt * kSymJ;
-            float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f};
-            float jx = 0.f, jy = 0.f, jz = 0.f;
-            uint32_t skip[2] = {0u, 0u};
-            if (jt == next) {
-                ++mp;
-                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-                uint32_t nbm;
+        for (int pr = 0; pr < npair; ++pr) {
+            const int jtA = g0 + 2 * pr;
+            float2 ja[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            float2 acc[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
+            uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
+            bool masked = false;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
-                chain_tile<true>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
-            } else {
-                chain_tile<false>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ax, ay, az, jx, jy, jz, skip, rfar2);
-            }
+            for (int h = 0; h < 2; ++h) {
+                const int jt = jtA + h;
+                if (jt < it.jt1 && jt == next) {
+                    ++mp;
+                    next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+                    masked = true;
+                    uint32_t nbm;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                long long* row = sfx[warp * 64 + u * 32 + lane];
-                row[0] += to_fixed(ax[u], (float)kScaleE);
-                row[1] += to_fixed(ay[u], (float)kScaleE);
-                row[2] += to_fixed(az[u], (float)kScaleE);
+                    for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, sk[u][h], nbm);
+                }
             }
-            red[g][warp][lane][0] = jx;
-            red[g][warp][lane][1] = jy;
-            red[g][warp][lane][2] = jz;
+            if (masked) chain_tile<true>(sj[pr], lane, I, acc, ja, sk, rfar2);
+            else chain_tile<false>(sj[pr], lane, I, acc, ja, sk, rfar2);
+            // per-tile conversion (each half is one tile)
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    sfx[c][warp * 64 + u * 32 + lane] +=
+                        to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
+            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(ja[0].x, ja[1].x, ja[2].x, 0.f);
+            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(ja[0].y, ja[1].y, ja[2].y, 0.f);
         }
         __syncthreads();
         for (int v = tid; v < ng * kSymJ * 3; v += kSymThreads) {
@@ -461,10 +576,10 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_chain_sym(const SymItem* __r
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (vi[u]) {
-            const long long* row = sfx[warp * 64 + u * 32 + lane];
-            fix_add(&V.Ffix[3 * (A + ii[u])], row[0]);
-            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], row[1]);
-            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], row[2]);
+            const int r = warp * 64 + u * 32 + lane;
+            fix_add(&V.Ffix[3 * (A + ii[u])], sfx[0][r]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 1], sfx[1][r]);
+            fix_add(&V.Ffix[3 * (A + ii[u]) + 2], sfx[2][r]);
         }
     }
 }
@@ -580,80 +695,108 @@ __global__ void k_final_forces(View V, int a0, int n) {
 // Each unordered pair yields both descreening integrals, H(r, rt_i, s_j) for
 // psi_i and H(r, rt_j, s_i) for psi_j (one shared distance).  Sums go to the
 // int64 accumulator Hfix (scale 2^40); k_fin_born turns them into R.
-struct BoI {
-    float x, y, z, s, rt, irt;
+// In the far regime H = P(y) s^3 / r^4 with y = s^2 / r^2 (P the fitted
+// series), so s^2 and s^3 are staged and 1/r^4 serves both directions.
+// Packed over partner tiles like the GB pass.
+struct BoI2 {
+    float2 x, y, z, s2, s3; // the i atom's value in both halves
+    float s, rt, irt;       // closed-form operands
+};
+
+struct BoJs {
+    float4 a[2 * kSymJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kSymJ]; // (-zA, -zB, s2A, s2B)
+    float4 c[2 * kSymJ]; // (s3A, s3B, sA, sB)
+    float4 n[2 * kSymJ]; // (rtA, rtB, 1/rtA, 1/rtB): closed forms
 };
 
 template <bool MASKED>
-__device__ __forceinline__ void born_tile(const float4* sa, const float2* sb, int lane, const BoI (&I)[2],
-                                          float (&ah)[2], float& jh, const uint32_t (&skip)[2], float rfar2) {
+__device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (&I)[2], float2 (&ah)[2],
+                                          float2& jh, const uint32_t (&sk)[2][2], float rfar2) {
+    const int src = (lane + 1) & 31;
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
-        const int jj = (lane + k) & (kSymJ - 1);
-        const float4 A = sa[jj];
-        const float2 B = sb[jj];
-        float r2[2], rinv[2], hi[2], hj[2];
-        bool sk[2] = {false, false}, nr[2];
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 s2j = make_float2(B.z, B.w), s3j = make_float2(C.x, C.y);
+        float2 r2[2], rinv[2], hi[2], hj[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const float dx = I[u].x - A.x, dy = I[u].y - A.y, dz = I[u].z - A.z;
-            r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
             if (MASKED) {
-                sk[u] = (skip[u] >> jj) & 1u;
-                r2[u] = sk[u] ? 1.f : r2[u];
+                const int jj = (lane + k) & (kSymJ - 1);
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? 1.f : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? 1.f : r2[u].y;
             }
-            rinv[u] = rsqrt_ftz(r2[u]);
-            hi[u] = hct_series(rinv[u], B.x);
-            hj[u] = hct_series(rinv[u], I[u].s);
-            nr[u] = r2[u] < rfar2;
+            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
+            hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), __fmul2_rn(s3j, rinv4));
+            hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), __fmul2_rn(I[u].s3, rinv4));
         }
         // closed forms only where some lane has a pair inside r_far (rare)
-        if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
+        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        if (__any_sync(0xffffffffu, nr)) {
+            const float4 Nj = sj.n[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (nr[u]) {
-                    const float r = r2[u] * rinv[u];
-                    hi[u] = hct(r, rinv[u], I[u].rt, I[u].irt, B.x);
-                    hj[u] = hct(r, rinv[u], A.w, B.y, I[u].s);
+                if (r2[u].x < rfar2) {
+                    const float r = r2[u].x * rinv[u].x;
+                    hi[u].x = hct(r, rinv[u].x, I[u].rt, I[u].irt, C.z);
+                    hj[u].x = hct(r, rinv[u].x, Nj.x, Nj.z, I[u].s);
+                }
+                if (r2[u].y < rfar2) {
+                    const float r = r2[u].y * rinv[u].y;
+                    hi[u].y = hct(r, rinv[u].y, I[u].rt, I[u].irt, C.w);
+                    hj[u].y = hct(r, rinv[u].y, Nj.y, Nj.w, I[u].s);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (MASKED) {
-                hi[u] = sk[u] ? 0.f : hi[u];
-                hj[u] = sk[u] ? 0.f : hj[u];
+                const int jj = (lane + k) & (kSymJ - 1);
+                const bool s0 = (sk[u][0] >> jj) & 1u, s1 = (sk[u][1] >> jj) & 1u;
+                hi[u].x = s0 ? 0.f : hi[u].x;
+                hj[u].x = s0 ? 0.f : hj[u].x;
+                hi[u].y = s1 ? 0.f : hi[u].y;
+                hj[u].y = s1 ? 0.f : hj[u].y;
             }
-            ah[u] += hi[u];
-            jh += hj[u];
+            ah[u] = __fadd2_rn(ah[u], hi[u]);
+            jh = __fadd2_rn(jh, hj[u]);
         }
-        jh = __shfl_sync(0xffffffffu, jh, (lane + 1) & 31);
+        jh.x = __shfl_sync(0xffffffffu, jh.x, src);
+        jh.y = __shfl_sync(0xffffffffu, jh.y, src);
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __restrict__ items, View V) {
-    __shared__ float4 sa[kSymG * kSymJ];
-    __shared__ float2 sb[kSymG * kSymJ];
+__global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __restrict__ items, View V) {
+    __shared__ BoJs sj[kSymG / 2];
     __shared__ float red[kSymG][4][kSymJ];
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1], cz = V.x[3 * (A + it.i0) + 2];
     const float rfar2 = V.rfar2;
     int ii[2];
     bool vi[2];
-    BoI I[2];
+    BoI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < N;
         const int i = vi[u] ? ii[u] : it.i0;
-        I[u].x = vi[u] ? (float)(V.x[3 * (A + i)] - cx) : -kFarF;
-        I[u].y = vi[u] ? (float)(V.x[3 * (A + i) + 1] - cy) : -kFarF;
-        I[u].z = vi[u] ? (float)(V.x[3 * (A + i) + 2] - cz) : -kFarF;
-        I[u].s = vi[u] ? (float)V.sc[P + i] : 0.f;
-        I[u].rt = vi[u] ? (float)V.rt[P + i] : 1.f;
-        I[u].irt = vi[u] ? (float)(1.0 / V.rt[P + i]) : 1.f;
+        const float4 xi = V.xs[A + i], pi = V.pb32[P + i];
+        const float si = vi[u] ? pi.x : 0.f;
+        I[u].x = splat<float2>(vi[u] ? xi.x : -kFarF);
+        I[u].y = splat<float2>(vi[u] ? xi.y : -kFarF);
+        I[u].z = splat<float2>(vi[u] ? xi.z : -kFarF);
+        I[u].s2 = splat<float2>(si * si);
+        I[u].s3 = splat<float2>(si * si * si);
+        I[u].s = si;
+        I[u].rt = vi[u] ? pi.y : 1.f;
+        I[u].irt = vi[u] ? pi.z : 1.f;
     }
     long long hx[2] = {0, 0}; // i-side fixed-point sums
     int mp = V.smt_off[it.st];
@@ -661,42 +804,60 @@ __global__ void __launch_bounds__(kSymThreads, 8) k_born_sym(const SymItem* __re
     while (mp < me && V.smt_list[mp] < it.jt0) ++mp;
     int next = mp < me ? V.smt_list[mp] : 0x7fffffff;
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
-        const int ng = min(kSymG, it.jt1 - g0);
+        const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kSymJ) { // stage up to four j-tiles, one atom per thread
-            const int j = g0 * kSymJ + tid;
-            float4 a;
-            float2 b;
-            if (j < N) {
-                a = make_float4((float)(V.x[3 * (A + j)] - cx), (float)(V.x[3 * (A + j) + 1] - cy),
-                                (float)(V.x[3 * (A + j) + 2] - cz), (float)V.rt[P + j]);
-                b = make_float2((float)V.sc[P + j], (float)(1.0 / V.rt[P + j]));
-            } else {
-                a = make_float4(kFarF, kFarF, kFarF, 1.f);
-                b = make_float2(0.f, 1.f);
+        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
+            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
+            if (pr < npair) {
+                float v[2][6];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = 2 * pr + h, j = (g0 + g) * kSymJ + e;
+                    if (g < ng && j < N) {
+                        const float4 xj = V.xs[A + j], pj = V.pb32[P + j];
+                        v[h][0] = -xj.x; v[h][1] = -xj.y; v[h][2] = -xj.z;
+                        v[h][3] = pj.x; v[h][4] = pj.y; v[h][5] = pj.z;
+                    } else { // padding: far away, no sphere
+                        v[h][0] = -kFarF; v[h][1] = -kFarF; v[h][2] = -kFarF;
+                        v[h][3] = 0.f; v[h][4] = 1.f; v[h][5] = 1.f;
+                    }
+                }
+                BoJs& S = sj[pr];
+                const int r = e + cpy * kSymJ;
+                const float s2a = v[0][3] * v[0][3], s2b = v[1][3] * v[1][3];
+                S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+                S.b[r] = make_float4(v[0][2], v[1][2], s2a, s2b);
+                S.c[r] = make_float4(s2a * v[0][3], s2b * v[1][3], v[0][3], v[1][3]);
+                S.n[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
             }
-            sa[tid] = a;
-            sb[tid] = b;
         }
         __syncthreads();
-        for (int g = 0; g < ng; ++g) {
-            const int jt = g0 + g, j0 = jt * kSymJ;
-            float jh = 0.f;
-            float ah[2] = {0.f, 0.f};
-            uint32_t skip[2] = {0u, 0u};
-            if (jt == next) {
-                ++mp;
-                next = mp < me ? V.smt_list[mp] : 0x7fffffff;
-                uint32_t nbm;
+        for (int pr = 0; pr < npair; ++pr) {
+            const int jtA = g0 + 2 * pr;
+            float2 jh = make_float2(0.f, 0.f);
+            float2 ah[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
+            bool masked = false;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], j0, N, skip[u], nbm);
-                born_tile<true>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ah, jh, skip, rfar2);
-            } else {
-                born_tile<false>(sa + g * kSymJ, sb + g * kSymJ, lane, I, ah, jh, skip, rfar2);
+            for (int h = 0; h < 2; ++h) {
+                const int jt = jtA + h;
+                if (jt < it.jt1 && jt == next) {
+                    ++mp;
+                    next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+                    masked = true;
+                    uint32_t nbm;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, sk[u][h], nbm);
+                }
             }
-            hx[0] += to_fixed(ah[0], (float)kScaleH);
-            hx[1] += to_fixed(ah[1], (float)kScaleH);
-            red[g][warp][lane] = jh;
+            if (masked) born_tile<true>(sj[pr], lane, I, ah, jh, sk, rfar2);
+            else born_tile<false>(sj[pr], lane, I, ah, jh, sk, rfar2);
+            // per-tile conversion (each half is one tile)
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                hx[u] += to_fixed(ah[u].x, (float)kScaleH) + to_fixed(ah[u].y, (float)kScaleH);
+            red[2 * pr][warp][lane] = jh.x;
+            red[2 * pr + 1][warp][lane] = jh.y;
         }
         __syncthreads();
         if (tid < ng * kSymJ) {

@@ -15,7 +15,7 @@ Y = 0.35 ** 2
 
 def coeffs(name):
     src = open(SRC).read()
-    body = re.search(r"float %s\(float y\) \{.*?\n\}" % name, src, re.S).group(0)
+    body = re.search(r"T %s\(T y\) \{.*?\n\}" % name, src, re.S).group(0)
     vals = [float(v) for v in re.findall(r"([0-9]+\.[0-9]+)f", body)]
     return vals[::-1]  # Horner lists the highest power first
 
