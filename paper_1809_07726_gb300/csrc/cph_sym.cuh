@@ -34,7 +34,7 @@ constexpr int kSymThreads = 128;
 constexpr int kSymI = 256;    // atoms per i-tile (two per thread)
 constexpr int kSymJ = 32;     // atoms per j-tile
 constexpr int kSymChunk = 48; // j-tiles per work item at most (default; autotuned)
-constexpr int kSymG = 4;      // j-tiles staged per barrier (one atom per thread)
+constexpr int kSymG = 8;      // j-tiles staged per barrier (four tile pairs)
 
 struct SymItem {
     int w, i0, jt0, jt1, st, pad;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
                                         KSum<float>& egb, KSum<float>& ec, KSum<float>& elj) {
     const int src = (lane + 1) & 31;
     const float2 ln2 = splat<float2>(kLn2), one = splat<float2>(1.f), c12 = splat<float2>(12.f),
-                 cm6 = splat<float2>(-6.f), mtau = splat<float2>(-tau), mq = splat<float2>(-0.25f),
+                 cm6 = splat<float2>(-6.f), mtau = splat<float2>(-tau), qtau4 = splat<float2>(0.25f * tau),
                  ie = splat<float2>(iei);
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
@@ -183,7 +183,8 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
             const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2);
             const float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
             const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
-            const float2 t = __fmul2_rn(__fmul2_rn(qf3, e), __ffma2_rn(D2, ln2, one));
+            const float2 qfe = __fmul2_rn(qf3, e);
+            const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
             a[u][3] = __ffma2_rn(t, Rj, a[u][3]);
             ja[3] = __ffma2_rn(t, I[u].R, ja[3]);
             const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
@@ -191,15 +192,15 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
             const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
             const float2 l6 = __fmul2_rn(ep4, sr6);
             const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
-            const float2 w = __fmul2_rn(__fmul2_rn(mtau, qf3), __ffma2_rn(mq, e, one));
+            // -tau qf3 (1 - e/4)
+            const float2 w = __ffma2_rn(qtau4, qfe, __fmul2_rn(mtau, qf3));
             const float2 fs = __ffma2_rn(__ffma2_rn(cq, rinv, lj), rinv2, w);
-            const float2 mfs = make_float2(-fs.x, -fs.y);
             a[u][0] = __ffma2_rn(fs, dx, a[u][0]);
             a[u][1] = __ffma2_rn(fs, dy, a[u][1]);
             a[u][2] = __ffma2_rn(fs, dz, a[u][2]);
-            ja[0] = __ffma2_rn(mfs, dx, ja[0]);
-            ja[1] = __ffma2_rn(mfs, dy, ja[1]);
-            ja[2] = __ffma2_rn(mfs, dz, ja[2]);
+            ja[0] = __ffma2_rn(fs, dx, ja[0]); // the partner's force is minus this sum
+            ja[1] = __ffma2_rn(fs, dy, ja[1]);
+            ja[2] = __ffma2_rn(fs, dz, ja[2]);
             if (ENERGY) {
                 const float2 eg = __fmul2_rn(qq, fi), eco = __fmul2_rn(cq, rinv);
                 const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
@@ -260,9 +261,10 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
         const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
-            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
-            if (pr < npair) {
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kSymJ; q += kSymThreads) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            {
                 float v[2][8];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -314,8 +316,8 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
                     sfx[c][warp * 64 + u * 32 + lane] +=
                         to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
             // lane l now holds the partials of partner l of both tiles
-            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(ja[0].x, ja[1].x, ja[2].x, ja[3].x);
-            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(ja[0].y, ja[1].y, ja[2].y, ja[3].y);
+            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(-ja[0].x, -ja[1].x, -ja[2].x, ja[3].x);
+            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(-ja[0].y, -ja[1].y, -ja[2].y, ja[3].y);
         }
         __syncthreads();
         // add the four warps' partials of every staged partner and send them
@@ -402,10 +404,20 @@ struct ChJs {
     float4 n[2 * kSymJ]; // (sA, sB, rtA, rtB): closed forms
 };
 
+// Closed-form force weight t of one pair inside r_far, out of line for the
+// same reason as born_near.
+__device__ __noinline__ float chain_near(float r2, float rinv, float c_i, float rt_i, float s_i, float c_j,
+                                         float s_j, float rt_j) {
+    const float r = r2 * rinv;
+    const float g = c_i * hct_dr(r, rinv, rt_i, s_j) + c_j * hct_dr(r, rinv, rt_j, s_i);
+    return -g * rinv;
+}
+
 template <bool MASKED>
 __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 (&I)[2], float2 (&a)[2][3],
                                            float2 (&ja)[3], const uint32_t (&sk)[2][2], float rfar2) {
     const int src = (lane + 1) & 31;
+    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
@@ -417,10 +429,10 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
             dy[u] = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
             dz[u] = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
             r2[u] = __ffma2_rn(dx[u], dx[u], __ffma2_rn(dy[u], dy[u], __fmul2_rn(dz[u], dz[u])));
-            if (MASKED) {
+            if (MASKED) { // skipped pairs stay off the closed-form branch
                 const int jj = (lane + k) & (kSymJ - 1);
-                r2[u].x = ((sk[u][0] >> jj) & 1u) ? 1.f : r2[u].x;
-                r2[u].y = ((sk[u][1] >> jj) & 1u) ? 1.f : r2[u].y;
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
             rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
             const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
@@ -436,16 +448,10 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
             const float4 Nj = sj.n[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (r2[u].x < rfar2) {
-                    const float r = r2[u].x * rinv[u].x;
-                    const float g = I[u].c.x * hct_dr(r, rinv[u].x, I[u].rt, Nj.x) + B.z * hct_dr(r, rinv[u].x, Nj.z, I[u].s);
-                    t[u].x = -g * rinv[u].x;
-                }
-                if (r2[u].y < rfar2) {
-                    const float r = r2[u].y * rinv[u].y;
-                    const float g = I[u].c.x * hct_dr(r, rinv[u].y, I[u].rt, Nj.y) + B.w * hct_dr(r, rinv[u].y, Nj.w, I[u].s);
-                    t[u].y = -g * rinv[u].y;
-                }
+                if (r2[u].x < rfar2)
+                    t[u].x = chain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].s, B.z, Nj.x, Nj.z);
+                if (r2[u].y < rfar2)
+                    t[u].y = chain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].s, B.w, Nj.y, Nj.w);
             }
         }
 #pragma unroll
@@ -455,13 +461,12 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
                 t[u].x = ((sk[u][0] >> jj) & 1u) ? 0.f : t[u].x;
                 t[u].y = ((sk[u][1] >> jj) & 1u) ? 0.f : t[u].y;
             }
-            const float2 mt = make_float2(-t[u].x, -t[u].y);
             a[u][0] = __ffma2_rn(t[u], dx[u], a[u][0]);
             a[u][1] = __ffma2_rn(t[u], dy[u], a[u][1]);
             a[u][2] = __ffma2_rn(t[u], dz[u], a[u][2]);
-            ja[0] = __ffma2_rn(mt, dx[u], ja[0]);
-            ja[1] = __ffma2_rn(mt, dy[u], ja[1]);
-            ja[2] = __ffma2_rn(mt, dz[u], ja[2]);
+            ja[0] = __ffma2_rn(t[u], dx[u], ja[0]); // the partner's force is minus this sum
+            ja[1] = __ffma2_rn(t[u], dy[u], ja[1]);
+            ja[2] = __ffma2_rn(t[u], dz[u], ja[2]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -509,9 +514,10 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
         const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
-            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
-            if (pr < npair) {
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kSymJ; q += kSymThreads) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            {
                 float v[2][6];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -562,8 +568,8 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
                 for (int c = 0; c < 3; ++c)
                     sfx[c][warp * 64 + u * 32 + lane] +=
                         to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
-            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(ja[0].x, ja[1].x, ja[2].x, 0.f);
-            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(ja[0].y, ja[1].y, ja[2].y, 0.f);
+            *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(-ja[0].x, -ja[1].x, -ja[2].x, 0.f);
+            *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(-ja[0].y, -ja[1].y, -ja[2].y, 0.f);
         }
         __syncthreads();
         for (int v = tid; v < ng * kSymJ * 3; v += kSymThreads) {
@@ -710,10 +716,21 @@ struct BoJs {
     float4 n[2 * kSymJ]; // (rtA, rtB, 1/rtA, 1/rtB): closed forms
 };
 
+// Closed-form integrals of one pair inside r_far, kept out of line: a warp
+// only gets here when one of its lanes has such a pair, and a single copy of
+// this code keeps the unrolled tile loops small enough for the instruction
+// cache.  Returns (H(r, rt_i, s_j), H(r, rt_j, s_i)).
+__device__ __noinline__ float2 born_near(float r2, float rinv, float rt_i, float irt_i, float s_i, float s_j,
+                                         float rt_j, float irt_j) {
+    const float r = r2 * rinv;
+    return make_float2(hct(r, rinv, rt_i, irt_i, s_j), hct(r, rinv, rt_j, irt_j, s_i));
+}
+
 template <bool MASKED>
 __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (&I)[2], float2 (&ah)[2],
                                           float2& jh, const uint32_t (&sk)[2][2], float rfar2) {
     const int src = (lane + 1) & 31;
+    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
@@ -725,10 +742,10 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
             const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
             const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
             r2[u] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            if (MASKED) {
+            if (MASKED) { // skipped pairs stay off the closed-form branch
                 const int jj = (lane + k) & (kSymJ - 1);
-                r2[u].x = ((sk[u][0] >> jj) & 1u) ? 1.f : r2[u].x;
-                r2[u].y = ((sk[u][1] >> jj) & 1u) ? 1.f : r2[u].y;
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
             rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
             const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
@@ -743,14 +760,14 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (r2[u].x < rfar2) {
-                    const float r = r2[u].x * rinv[u].x;
-                    hi[u].x = hct(r, rinv[u].x, I[u].rt, I[u].irt, C.z);
-                    hj[u].x = hct(r, rinv[u].x, Nj.x, Nj.z, I[u].s);
+                    const float2 h = born_near(r2[u].x, rinv[u].x, I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z);
+                    hi[u].x = h.x;
+                    hj[u].x = h.y;
                 }
                 if (r2[u].y < rfar2) {
-                    const float r = r2[u].y * rinv[u].y;
-                    hi[u].y = hct(r, rinv[u].y, I[u].rt, I[u].irt, C.w);
-                    hj[u].y = hct(r, rinv[u].y, Nj.y, Nj.w, I[u].s);
+                    const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w);
+                    hi[u].y = h.x;
+                    hj[u].y = h.y;
                 }
             }
         }
@@ -806,9 +823,10 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kSymG) {
         const int ng = min(kSymG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        { // stage up to two tile pairs: thread (pair, copy, entry) writes whole rows
-            const int pr = tid >> 6, cpy = (tid >> 5) & 1, e = tid & 31;
-            if (pr < npair) {
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kSymJ; q += kSymThreads) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            {
                 float v[2][6];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -860,10 +878,10 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
             red[2 * pr + 1][warp][lane] = jh.y;
         }
         __syncthreads();
-        if (tid < ng * kSymJ) {
-            const int g = tid / kSymJ, j = tid % kSymJ;
+        for (int q = tid; q < ng * kSymJ; q += kSymThreads) {
+            const int g = q / kSymJ, j = q % kSymJ;
             const float v = red[g][0][j] + red[g][1][j] + red[g][2][j] + red[g][3][j];
-            const int jg = g0 * kSymJ + tid;
+            const int jg = g0 * kSymJ + q;
             if (jg < N) red_add_h(&V.Hfix[A + jg], v, V.status);
         }
     }
