@@ -35,19 +35,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "aggregate replica-steps/s & GB pair evals/s, batched vs per-replica launches"
 WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-atom systems"
-# Algorithmic cost of one unordered pair in each pass, counted from the closed
-# forms (FP32-pipe instructions incl. FMA as 1, MUFU transcendental ops).
-PASS_COST = {"born": (45, 7), "gb": (41, 3), "chain": (47, 7)}
-# GB-energy backward (Born radii recomputed): born 45/7 + GB adjoint 32/2 +
-# chain adjoint (dH/dr, dH/drt, dH/ds in both directions) 66/7 per unordered pair
-BACKWARD_COST = (143, 16)
+# Algorithmic cost of one unordered pair in each pass, counted from the forms
+# the method evaluates for a far pair (r >= r_far: the HCT series; over 99 % of
+# the pairs here): FP32 lane operations (an FMA counts once) and MUFU
+# operations (rsqrt, ex2).  born: distance 6, powers of 1/r 2, two series
+# terms 16, sums 2; gb: distance 6, GB kernel and dE/dR 18, LJ 9, Coulomb 2,
+# force and partner force 6 (minus fused products), 3 MUFU; chain: distance 6,
+# powers 3, two dH/dr series 12, weights 5, forces 6.
+PASS_COST = {"born": (26, 1), "gb": (40, 3), "chain": (32, 1)}
+# GB-energy backward (Born radii recomputed): born 26/1 + GB adjoint (energy,
+# dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
+# dH/drt = 0 far) 48/1
+BACKWARD_COST = (106, 4)
 N_SM = 152
+FP32_LANES = 128   # FP32 lane operations per clock per SM
+MUFU_LANES = 16    # MUFU operations per clock per SM
+
+
+def clk_per_pair_per_sm(fp32, mufu):
+    """The FP32 (FMA) pipe and the MUFU pipe work in parallel; packed f32x2
+    instructions keep issue slots off the critical path, so a pass needs
+    max(fp32 / 128, mufu / 16) SM clocks per pair."""
+    return max(fp32 / FP32_LANES, mufu / MUFU_LANES)
 
 
 def pairs_per_clk_per_sm(fp32, mufu):
-    """Issue-slot and MUFU bound: 128 instructions / clk / SM over all
-    instructions, 16 MUFU ops / clk / SM."""
-    return min(128.0 / (fp32 + mufu), 16.0 / mufu)
+    return 1.0 / clk_per_pair_per_sm(fp32, mufu)
 
 
 class ClockSampler:
@@ -298,8 +311,7 @@ def run_gpu(args):
     fp, mu = PASS_COST[names[dom]]
     peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(fp, mu) / 1e9
     achieved = total_pairs / (pass_ms[dom] / 1e3) / 1e9
-    step_peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(
-        sum(v[0] for v in PASS_COST.values()), sum(v[1] for v in PASS_COST.values())) / 1e9
+    step_peak = N_SM * f_mhz * 1e6 / sum(clk_per_pair_per_sm(*v) for v in PASS_COST.values()) / 1e9
 
     if args.quick:
         if rank == 0:
@@ -383,7 +395,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
                      "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
                      "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) x "
-                                   f"min(128/({fp}+{mu}), 16/{mu}) pairs/clk/SM",
+                                   f"1/max({fp}/128, {mu}/16) pairs/clk/SM (FP32 lanes, MUFU)",
                      "step_frac": (total_pairs / (sum(pass_ms) / 1e3) / 1e9) / step_peak},
         "e2e": {"value": e2e_value, "unit": "replica-steps/s",
                 "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e},
