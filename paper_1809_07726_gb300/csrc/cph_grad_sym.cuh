@@ -2,9 +2,11 @@
 // every unordered pair of a replica is evaluated once and contributes to both
 // atoms, with the decomposition of the engine's FP32 passes -- a CTA of 128
 // threads owns a 256-atom i-tile (two atoms per lane) and sweeps 32-atom
-// j-tiles of the upper triangle in groups of four staged by all threads;
+// j-tiles of the upper triangle two at a time (tile pairs, packed f32x2
+// arithmetic, see cph_pair_tiles.cuh), eight tiles staged per barrier;
 // partner-side partials rotate across lanes by warp shuffle and land, like the
 // i-side ones, in int64 fixed-point accumulators (exact, order independent).
+// Coordinates are used as given (x_i - x_j is one FP32 rounding).
 // Work items are decoded from the block index (replica, i-tile, chunk of
 // j-tiles); chunks past the end of a row exit at once.  Nothing is allocated:
 // accumulators live in the caller's workspace.
@@ -15,14 +17,15 @@
 // disjoint-sphere series regime (dH/drt = 0 there).
 #pragma once
 #include "cph_device.cuh"
+#include "cph_pair_tiles.cuh"
 
 namespace cph {
 namespace grad {
 
 constexpr int kGT = 128;     // threads per CTA
 constexpr int kGI = 256;     // atoms per i-tile
-constexpr int kGJ = 32;      // atoms per j-tile
-constexpr int kGG = 4;       // j-tiles staged per barrier
+constexpr int kGJ = kTileJ;   // atoms per j-tile
+constexpr int kGG = 8;       // j-tiles staged per barrier (four tile pairs)
 constexpr int kGChunk = 16;  // j-tiles per work item
 constexpr float kFar = 1.0e4f; // padding / invalid atoms sit this far away
 
@@ -94,9 +97,8 @@ __device__ __forceinline__ bool gmasked(int jt, int i0, int n) {
 }
 
 // ------------------------------------------------------------ Born radii
-__global__ void __launch_bounds__(kGT, 8) k_gborn_sym(SView g) {
-    __shared__ float4 sa[kGG * kGJ];
-    __shared__ float2 sb[kGG * kGJ];
+__global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
+    __shared__ BoJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ];
     const GItem it = gitem(g);
     if (!it.ok) return;
@@ -105,93 +107,80 @@ __global__ void __launch_bounds__(kGT, 8) k_gborn_sym(SView g) {
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
     const float off = (float)g.offset, rfar2 = gfar2(g);
-    const float cx = X[3 * it.i0], cy = X[3 * it.i0 + 1], cz = X[3 * it.i0 + 2];
     int ii[2];
     bool vi[2];
-    float xi[2], yi[2], zi[2], si[2], rti[2], irti[2];
+    BoI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < n;
         const int i = vi[u] ? ii[u] : it.i0;
-        xi[u] = vi[u] ? X[3 * i] - cx : -kFar;
-        yi[u] = vi[u] ? X[3 * i + 1] - cy : -kFar;
-        zi[u] = vi[u] ? X[3 * i + 2] - cz : -kFar;
-        rti[u] = vi[u] ? RH[i] - off : 1.f;
-        si[u] = vi[u] ? g.screen[i] * rti[u] : 0.f;
-        irti[u] = 1.f / rti[u];
+        const float rt = vi[u] ? RH[i] - off : 1.f, si = vi[u] ? g.screen[i] * rt : 0.f;
+        I[u].x = splat<float2>(vi[u] ? X[3 * i] : -kFar);
+        I[u].y = splat<float2>(vi[u] ? X[3 * i + 1] : -kFar);
+        I[u].z = splat<float2>(vi[u] ? X[3 * i + 2] : -kFar);
+        I[u].s2 = splat<float2>(si * si);
+        I[u].s3 = splat<float2>(si * si * si);
+        I[u].s = si;
+        I[u].rt = rt;
+        I[u].irt = 1.f / rt;
     }
     long long hx[2] = {0, 0};
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kGG) {
-        const int ng = min(kGG, it.jt1 - g0);
+        const int ng = min(kGG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kGJ) {
-            const int j = g0 * kGJ + tid;
-            if (j < n) {
-                const float rtj = RH[j] - off;
-                sa[tid] = make_float4(X[3 * j] - cx, X[3 * j + 1] - cy, X[3 * j + 2] - cz, rtj);
-                sb[tid] = make_float2(g.screen[j] * rtj, 1.f / rtj);
-            } else {
-                sa[tid] = make_float4(kFar, kFar, kFar, 1.f);
-                sb[tid] = make_float2(0.f, 1.f);
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kGJ; q += kGT) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            float v[2][6];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gt = 2 * pr + h, j = (g0 + gt) * kGJ + e;
+                if (gt < ng && j < n) {
+                    const float rt = RH[j] - off;
+                    v[h][0] = -X[3 * j]; v[h][1] = -X[3 * j + 1]; v[h][2] = -X[3 * j + 2];
+                    v[h][3] = g.screen[j] * rt; v[h][4] = rt; v[h][5] = 1.f / rt;
+                } else { // padding: far away, no sphere
+                    v[h][0] = kFar; v[h][1] = kFar; v[h][2] = kFar;
+                    v[h][3] = 0.f; v[h][4] = 1.f; v[h][5] = 1.f;
+                }
             }
+            BoJs& S = sj[pr];
+            const int r = e + cpy * kGJ;
+            const float s2a = v[0][3] * v[0][3], s2b = v[1][3] * v[1][3];
+            S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+            S.b[r] = make_float4(v[0][2], v[1][2], s2a, s2b);
+            S.c[r] = make_float4(s2a * v[0][3], s2b * v[1][3], v[0][3], v[1][3]);
+            S.n[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
         }
         __syncthreads();
-        for (int gt = 0; gt < ng; ++gt) {
-            const int jt = g0 + gt, j0 = jt * kGJ;
-            const bool msk = gmasked(jt, it.i0, n);
-            uint32_t skip[2] = {0u, 0u};
-            if (msk) {
-                skip[0] = gskip(ii[0], vi[0], j0, n);
-                skip[1] = gskip(ii[1], vi[1], j0, n);
+        for (int pr = 0; pr < npair; ++pr) {
+            float2 jh = make_float2(0.f, 0.f);
+            float2 ah[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
+            bool masked = false;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jt = g0 + 2 * pr + h;
+                if (jt < it.jt1 && gmasked(jt, it.i0, n)) {
+                    masked = true;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
+                }
             }
-            const float4* A4 = sa + gt * kGJ;
-            const float2* B2 = sb + gt * kGJ;
-            float ah[2] = {0.f, 0.f}, jh = 0.f;
-#pragma unroll 2
-            for (int k = 0; k < kGJ; ++k) {
-                const int jj = (lane + k) & (kGJ - 1);
-                const float4 A = A4[jj];
-                const float2 B = B2[jj];
-                float r2[2], rinv[2], hi[2], hj[2];
-                bool sk[2], nr[2];
+            if (masked) born_tile<true>(sj[pr], lane, I, ah, jh, sk, rfar2);
+            else born_tile<false>(sj[pr], lane, I, ah, jh, sk, rfar2);
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const float dx = xi[u] - A.x, dy = yi[u] - A.y, dz = zi[u] - A.z;
-                    r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    sk[u] = msk && ((skip[u] >> jj) & 1u);
-                    r2[u] = sk[u] ? 1.f : r2[u];
-                    rinv[u] = rsqrt_ftz(r2[u]);
-                    const float x1 = B.x * rinv[u], x2 = si[u] * rinv[u];
-                    hi[u] = x1 * x1 * x1 * hct_series_h(x1 * x1) * rinv[u];
-                    hj[u] = x2 * x2 * x2 * hct_series_h(x2 * x2) * rinv[u];
-                    nr[u] = r2[u] < rfar2;
-                }
-                if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-                        if (nr[u]) {
-                            const float r = r2[u] * rinv[u];
-                            hi[u] = hct(r, rinv[u], rti[u], irti[u], B.x);
-                            hj[u] = hct(r, rinv[u], A.w, B.y, si[u]);
-                        }
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    ah[u] += sk[u] ? 0.f : hi[u];
-                    jh += sk[u] ? 0.f : hj[u];
-                }
-                jh = __shfl_sync(0xffffffffu, jh, (lane + 1) & 31);
-            }
-            hx[0] += to_fixed(ah[0], (float)kScaleH);
-            hx[1] += to_fixed(ah[1], (float)kScaleH);
-            red[gt][warp][lane] = jh;
+            for (int u = 0; u < 2; ++u)
+                hx[u] += to_fixed(ah[u].x, (float)kScaleH) + to_fixed(ah[u].y, (float)kScaleH);
+            red[2 * pr][warp][lane] = jh.x;
+            red[2 * pr + 1][warp][lane] = jh.y;
         }
         __syncthreads();
-        if (tid < ng * kGJ) {
-            const int gt = tid / kGJ, j = tid % kGJ;
+        for (int q = tid; q < ng * kGJ; q += kGT) {
+            const int gt = q / kGJ, j = q % kGJ;
             const float v = red[gt][0][j] + red[gt][1][j] + red[gt][2][j] + red[gt][3][j];
-            const int jg = g0 * kGJ + tid;
+            const int jg = g0 * kGJ + q;
             if (jg < n) atomicAdd((unsigned long long*)&g.Hfix[base + jg], (unsigned long long)to_fixed(v, (float)kScaleH));
         }
     }
@@ -224,11 +213,85 @@ __global__ void k_gfin_born(SView g) {
 // Per unordered pair (qs = sqrt(k) q): E += qs_i qs_j / f (times -tau at the
 // end); dE/dR both ways; sum_j qs_j / f for dE/dq both ways; the direct
 // gradient tau qq (1 - e/4) / f^3 (x_i - x_j) to i and its negative to j.
+// Packed over partner tiles (A, B) like the engine's passes.
+struct GpI2 {
+    float2 x, y, z, q, R, dk; // the i atom's value in both halves
+};
+
+struct GpJs {
+    float4 a[2 * kGJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kGJ]; // (-zA, -zB, qA, qB)
+    float4 c[2 * kGJ]; // (RA, RB, 1/RA, 1/RB)
+};
+
+template <bool MASKED, bool BACKWARD>
+__device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 (&I)[2], float2 (&ai)[2][5],
+                                           float2 (&aj)[5], float2 (&ei)[2], const uint32_t (&sk)[2][2],
+                                           float tau) {
+    const int src = (lane + 1) & 31;
+    const float2 ln2 = splat<float2>(kLn2), one = splat<float2>(1.f), tau2 = splat<float2>(tau),
+                 mtau4 = splat<float2>(-0.25f * tau);
+#pragma unroll 2
+    for (int k = 0; k < kGJ; ++k) {
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 qj = make_float2(B.z, B.w), Rj = make_float2(C.x, C.y);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            bool s0 = false, s1 = false;
+            if (MASKED) {
+                const int jj = (lane + k) & (kGJ - 1);
+                s0 = (sk[u][0] >> jj) & 1u;
+                s1 = (sk[u][1] >> jj) & 1u;
+                r2.x = s0 ? 1.f : r2.x;
+                r2.y = s1 ? 1.f : r2.y;
+            }
+            const float2 D2 = __fmul2_rn(r2, __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
+            const float2 e = make_float2(exp2_ftz(-D2.x), exp2_ftz(-D2.y));
+            const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2);
+            float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
+            if (MASKED) {
+                fi.x = s0 ? 0.f : fi.x;
+                fi.y = s1 ? 0.f : fi.y;
+            }
+            const float2 qq = __fmul2_rn(I[u].q, qj);
+            ei[u] = __ffma2_rn(qq, fi, ei[u]);
+            if (BACKWARD) {
+                const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
+                const float2 qfe = __fmul2_rn(qf3, e);
+                const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
+                ai[u][0] = __ffma2_rn(t, Rj, ai[u][0]);
+                aj[0] = __ffma2_rn(t, I[u].R, aj[0]);
+                ai[u][1] = __ffma2_rn(qj, fi, ai[u][1]);
+                aj[1] = __ffma2_rn(I[u].q, fi, aj[1]);
+                // tau qf3 (1 - e/4)
+                const float2 g2 = __ffma2_rn(mtau4, qfe, __fmul2_rn(tau2, qf3));
+                ai[u][2] = __ffma2_rn(g2, dx, ai[u][2]);
+                ai[u][3] = __ffma2_rn(g2, dy, ai[u][3]);
+                ai[u][4] = __ffma2_rn(g2, dz, ai[u][4]);
+                aj[2] = __ffma2_rn(g2, dx, aj[2]); // the partner's gradient is minus this sum
+                aj[3] = __ffma2_rn(g2, dy, aj[3]);
+                aj[4] = __ffma2_rn(g2, dz, aj[4]);
+            }
+        }
+        if (BACKWARD) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                aj[c].x = __shfl_sync(0xffffffffu, aj[c].x, src);
+                aj[c].y = __shfl_sync(0xffffffffu, aj[c].y, src);
+            }
+        }
+    }
+}
+
 template <bool BACKWARD>
-__global__ void __launch_bounds__(kGT, 6) k_gpair_sym(SView g) {
-    __shared__ float4 sa[kGG * kGJ], sb[kGG * kGJ];
+__global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
+    __shared__ GpJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ][5];
-    __shared__ long long sfx[kGI][5];
+    __shared__ long long sfx[5][kGI]; // i-side sums, component-major (conflict-free)
     __shared__ double ered[kGT / 32];
     const GItem it = gitem(g);
     if (!it.ok) return;
@@ -237,99 +300,90 @@ __global__ void __launch_bounds__(kGT, 6) k_gpair_sym(SView g) {
     const float* Q = g.q + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
     const float sqk = (float)g.sqrt_k, tau = (float)g.tau;
-    const float cx = X[3 * it.i0], cy = X[3 * it.i0 + 1], cz = X[3 * it.i0 + 2];
     int ii[2];
     bool vi[2];
-    float xi[2], yi[2], zi[2], qi[2], Ri[2], dki[2];
+    GpI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < n;
         const int i = vi[u] ? ii[u] : it.i0;
-        xi[u] = vi[u] ? X[3 * i] - cx : -kFar;
-        yi[u] = vi[u] ? X[3 * i + 1] - cy : -kFar;
-        zi[u] = vi[u] ? X[3 * i + 2] - cz : -kFar;
-        qi[u] = vi[u] ? Q[i] * sqk : 0.f;
-        Ri[u] = vi[u] ? (float)g.R[base + i] : 1.f;
-        dki[u] = vi[u] ? (float)(0.25 * 1.4426950408889634 / g.R[base + i]) : 1.f;
+        const float R = vi[u] ? (float)g.R[base + i] : 1.f;
+        I[u].x = splat<float2>(vi[u] ? X[3 * i] : -kFar);
+        I[u].y = splat<float2>(vi[u] ? X[3 * i + 1] : -kFar);
+        I[u].z = splat<float2>(vi[u] ? X[3 * i + 2] : -kFar);
+        I[u].q = splat<float2>(vi[u] ? Q[i] * sqk : 0.f);
+        I[u].R = splat<float2>(R);
+        I[u].dk = splat<float2>((0.25f * kLog2e) * __frcp_rn(R));
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
+        for (int c = 0; c < 5; ++c) sfx[c][warp * 64 + u * 32 + lane] = 0;
     }
     KSum<float> egb;
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kGG) {
-        const int ng = min(kGG, it.jt1 - g0);
+        const int ng = min(kGG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kGJ) {
-            const int j = g0 * kGJ + tid;
-            if (j < n) {
-                sa[tid] = make_float4(X[3 * j] - cx, X[3 * j + 1] - cy, X[3 * j + 2] - cz, Q[j] * sqk);
-                sb[tid] = make_float4((float)g.R[base + j], (float)(1.0 / g.R[base + j]), 0.f, 0.f);
-            } else {
-                sa[tid] = make_float4(kFar, kFar, kFar, 0.f);
-                sb[tid] = make_float4(1.f, 1.f, 0.f, 0.f);
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kGJ; q += kGT) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            float v[2][6];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gt = 2 * pr + h, j = (g0 + gt) * kGJ + e;
+                if (gt < ng && j < n) {
+                    const float R = (float)g.R[base + j];
+                    v[h][0] = -X[3 * j]; v[h][1] = -X[3 * j + 1]; v[h][2] = -X[3 * j + 2];
+                    v[h][3] = Q[j] * sqk; v[h][4] = R; v[h][5] = __frcp_rn(R);
+                } else { // padding: far away, no charge
+                    v[h][0] = kFar; v[h][1] = kFar; v[h][2] = kFar;
+                    v[h][3] = 0.f; v[h][4] = 1.f; v[h][5] = 1.f;
+                }
             }
+            GpJs& S = sj[pr];
+            const int r = e + cpy * kGJ;
+            S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+            S.b[r] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+            S.c[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
         }
         __syncthreads();
-        for (int gt = 0; gt < ng; ++gt) {
-            const int jt = g0 + gt, j0 = jt * kGJ;
-            const bool msk = gmasked(jt, it.i0, n);
-            uint32_t skip[2] = {0u, 0u};
-            if (msk) {
-                skip[0] = gskip(ii[0], vi[0], j0, n);
-                skip[1] = gskip(ii[1], vi[1], j0, n);
+        for (int pr = 0; pr < npair; ++pr) {
+            float2 ai[2][5], aj[5], ei[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                ai[0][c] = ai[1][c] = aj[c] = make_float2(0.f, 0.f);
             }
-            const float4* A4 = sa + gt * kGJ;
-            const float4* B4 = sb + gt * kGJ;
-            float ai[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
-            float aj[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-            for (int k = 0; k < kGJ; ++k) {
-                const int jj = (lane + k) & (kGJ - 1);
-                const float4 A = A4[jj];
-                const float4 B = B4[jj];
+            uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
+            bool masked = false;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const float dx = xi[u] - A.x, dy = yi[u] - A.y, dz = zi[u] - A.z;
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool sk = msk && ((skip[u] >> jj) & 1u);
-                    r2 = sk ? 1.f : r2;
-                    const float m = sk ? 0.f : 1.f;
-                    const float D2 = r2 * (dki[u] * B.y);
-                    const float e = exp2_ftz(-D2);
-                    const float fi = m * rsqrt_ftz(fmaf(Ri[u] * B.x, e, r2));
-                    const float qq = qi[u] * A.w;
-                    egb.add(qq * fi);
-                    if (BACKWARD) {
-                        const float qf3 = qq * fi * fi * fi;
-                        const float t = qf3 * e * fmaf(D2, kLn2, 1.f);
-                        ai[u][0] = fmaf(t, B.x, ai[u][0]);
-                        aj[0] = fmaf(t, Ri[u], aj[0]);
-                        ai[u][1] = fmaf(A.w, fi, ai[u][1]);
-                        aj[1] = fmaf(qi[u], fi, aj[1]);
-                        const float gt2 = tau * qf3 * fmaf(-0.25f, e, 1.f);
-                        ai[u][2] = fmaf(gt2, dx, ai[u][2]);
-                        ai[u][3] = fmaf(gt2, dy, ai[u][3]);
-                        ai[u][4] = fmaf(gt2, dz, ai[u][4]);
-                        aj[2] = fmaf(-gt2, dx, aj[2]);
-                        aj[3] = fmaf(-gt2, dy, aj[3]);
-                        aj[4] = fmaf(-gt2, dz, aj[4]);
-                    }
-                }
-                if (BACKWARD) {
-                    const int src = (lane + 1) & 31;
+            for (int h = 0; h < 2; ++h) {
+                const int jt = g0 + 2 * pr + h;
+                if (jt < it.jt1 && gmasked(jt, it.i0, n)) {
+                    masked = true;
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) aj[c] = __shfl_sync(0xffffffffu, aj[c], src);
+                    for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
                 }
+            }
+            if (masked) gpair_tile<true, BACKWARD>(sj[pr], lane, I, ai, aj, ei, sk, tau);
+            else gpair_tile<false, BACKWARD>(sj[pr], lane, I, ai, aj, ei, sk, tau);
+            // energy: plain per-tile sums, compensated across tiles
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                egb.add(ei[u].x);
+                egb.add(ei[u].y);
             }
             if (BACKWARD) {
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    long long* row = sfx[warp * 64 + u * 32 + lane];
+                    const int row = warp * 64 + u * 32 + lane;
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) row[c] += to_fixed(ai[u][c], (float)kScaleE);
+                    for (int c = 0; c < 5; ++c)
+                        sfx[c][row] += to_fixed(ai[u][c].x, (float)kScaleE) + to_fixed(ai[u][c].y, (float)kScaleE);
                 }
 #pragma unroll
-                for (int c = 0; c < 5; ++c) red[gt][warp][lane][c] = aj[c];
+                for (int c = 0; c < 5; ++c) {
+                    const float sgn = c >= 2 ? -1.f : 1.f;
+                    red[2 * pr][warp][lane][c] = sgn * aj[c].x;
+                    red[2 * pr + 1][warp][lane][c] = sgn * aj[c].y;
+                }
             }
         }
         if (BACKWARD) {
@@ -350,13 +404,13 @@ __global__ void __launch_bounds__(kGT, 6) k_gpair_sym(SView g) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (!vi[u]) continue;
-            const long long* row = sfx[warp * 64 + u * 32 + lane];
+            const int row = warp * 64 + u * 32 + lane;
             const size_t a = base + ii[u];
-            atomicAdd((unsigned long long*)&g.dRfix[a], (unsigned long long)row[0]);
-            atomicAdd((unsigned long long*)&g.dqfix[a], (unsigned long long)row[1]);
-            atomicAdd((unsigned long long*)&g.gfix[3 * a], (unsigned long long)row[2]);
-            atomicAdd((unsigned long long*)&g.gfix[3 * a + 1], (unsigned long long)row[3]);
-            atomicAdd((unsigned long long*)&g.gfix[3 * a + 2], (unsigned long long)row[4]);
+            atomicAdd((unsigned long long*)&g.dRfix[a], (unsigned long long)sfx[0][row]);
+            atomicAdd((unsigned long long*)&g.dqfix[a], (unsigned long long)sfx[1][row]);
+            atomicAdd((unsigned long long*)&g.gfix[3 * a], (unsigned long long)sfx[2][row]);
+            atomicAdd((unsigned long long*)&g.gfix[3 * a + 1], (unsigned long long)sfx[3][row]);
+            atomicAdd((unsigned long long*)&g.gfix[3 * a + 2], (unsigned long long)sfx[4][row]);
         }
     }
     // pair energy of this item: compensated lane sums, FP64 block reduction
@@ -400,21 +454,137 @@ __global__ void k_genergy_out(SView g) {
 // Per unordered pair, with c = dE/dpsi rt/2 of each atom:
 //   gradient  (c_i dH(r; rt_i, s_j)/dr + c_j dH(r; rt_j, s_i)/dr) (x_i - x_j)/r to i, minus to j;
 //   art_i += dH(r; rt_i, s_j)/drt,   as_i += c_j dH(r; rt_j, s_i)/ds   (and i <-> j),
-// which k_gfin_out turns into dE/drho.
-__device__ __forceinline__ float hct_dr_series(float rinv2, float rinv, float s) {
-    const float x = s * rinv, y = x * x;
-    return -x * y * hct_series_dr(y) * rinv2;
+// which k_gfin_out turns into dE/drho.  In the far regime dH/dr =
+// -s^3 Q(y)/r^5, dH/ds = s^2 S(y)/r^4 with y = s^2/r^2, and dH/drt = 0.
+// Packed over partner tiles (A, B) like the engine's passes.
+struct GcI2 {
+    float2 x, y, z, c, s2, s3; // the i atom's value in both halves
+    float s, rt, irt;          // closed-form operands
+};
+
+struct GcJs {
+    float4 a[2 * kGJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kGJ]; // (-zA, -zB, cA, cB)
+    float4 c[2 * kGJ]; // (s2A, s2B, s3A, s3B)
+    float4 n[2 * kGJ]; // (sA, sB, rtA, rtB): closed forms
+    float2 m[2 * kGJ]; // (1/rtA, 1/rtB): closed forms
+};
+
+struct GcNear {
+    float t, hti, htj, asi, asj;
+};
+
+// Closed forms of one pair inside r_far, out of line (a warp only gets here
+// when one of its lanes has such a pair): the gradient factor t, dH/drt both
+// ways, and the c-weighted dH/ds both ways.
+static __device__ __noinline__ GcNear gchain_near(float r2, float rinv, float ci, float rti, float irti, float si,
+                                                  float cj, float sj, float rtj, float irtj) {
+    const float r = r2 * rinv;
+    GcNear o;
+    o.t = (ci * hct_dr(r, rinv, rti, sj) + cj * hct_dr(r, rinv, rtj, si)) * rinv;
+    o.hti = hct_drt(r, rti, irti, sj);
+    o.htj = hct_drt(r, rtj, irtj, si);
+    o.asi = cj * hct_ds(r, rinv, rtj, si);
+    o.asj = ci * hct_ds(r, rinv, rti, sj);
+    return o;
 }
 
-__device__ __forceinline__ float ds_series(float rinv2, float rinv, float s) {
-    const float x = s * rinv, y = x * x;
-    return y * hct_series_ds(y) * rinv2;
+template <bool MASKED>
+__device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2 (&I)[2], float2 (&ai)[2][5],
+                                            float2 (&aj)[5], const uint32_t (&sk)[2][2], float rfar2) {
+    const int src = (lane + 1) & 31;
+    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
+    const float2 mone = splat<float2>(-1.f);
+#pragma unroll 2
+    for (int k = 0; k < kGJ; ++k) {
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 cj = make_float2(B.z, B.w), s2j = make_float2(C.x, C.y), s3j = make_float2(C.z, C.w);
+        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2], asi[2], asj[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            dy[u] = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            dz[u] = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx[u], dx[u], __ffma2_rn(dy[u], dy[u], __fmul2_rn(dz[u], dz[u])));
+            if (MASKED) {
+                const int jj = (lane + k) & (kGJ - 1);
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
+            }
+            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
+            const float2 yj = __fmul2_rn(s2j, rinv2), yi = __fmul2_rn(I[u].s2, rinv2);
+            const float2 qj = hct_series_dr(yj), qi = hct_series_dr(yi);
+            // t = (c_i dH_i/dr + c_j dH_j/dr) / r = -(c_i s_j^3 Q_j + c_j s_i^3 Q_i) / r^6
+            const float2 term = __ffma2_rn(__fmul2_rn(I[u].c, s3j), qj, __fmul2_rn(__fmul2_rn(cj, I[u].s3), qi));
+            t[u] = __fmul2_rn(term, __fmul2_rn(__fmul2_rn(rinv4, rinv2), mone));
+            // c_j dH(r; rt_j, s_i)/ds = c_j s_i^2 S_i / r^4, and i <-> j
+            asi[u] = __fmul2_rn(__fmul2_rn(cj, I[u].s2), __fmul2_rn(hct_series_ds(yi), rinv4));
+            asj[u] = __fmul2_rn(__fmul2_rn(I[u].c, s2j), __fmul2_rn(hct_series_ds(yj), rinv4));
+        }
+        // closed forms only where some lane has a pair inside r_far (rare; skipped
+        // pairs never get here, and dH/drt is zero in the far regime, so only
+        // this branch adds to the rt sums)
+        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        if (__any_sync(0xffffffffu, nr)) {
+            const float4 Nj = sj.n[lane + k];
+            const float2 Mj = sj.m[lane + k];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (r2[u].x < rfar2) {
+                    const GcNear o = gchain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.z, Nj.x,
+                                                 Nj.z, Mj.x);
+                    t[u].x = o.t;
+                    ai[u][3].x += o.hti;
+                    aj[3].x += o.htj;
+                    asi[u].x = o.asi;
+                    asj[u].x = o.asj;
+                }
+                if (r2[u].y < rfar2) {
+                    const GcNear o = gchain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.w, Nj.y,
+                                                 Nj.w, Mj.y);
+                    t[u].y = o.t;
+                    ai[u][3].y += o.hti;
+                    aj[3].y += o.htj;
+                    asi[u].y = o.asi;
+                    asj[u].y = o.asj;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (MASKED) {
+                const int jj = (lane + k) & (kGJ - 1);
+                const bool s0 = (sk[u][0] >> jj) & 1u, s1 = (sk[u][1] >> jj) & 1u;
+                t[u].x = s0 ? 0.f : t[u].x;
+                t[u].y = s1 ? 0.f : t[u].y;
+                asi[u].x = s0 ? 0.f : asi[u].x;
+                asi[u].y = s1 ? 0.f : asi[u].y;
+                asj[u].x = s0 ? 0.f : asj[u].x;
+                asj[u].y = s1 ? 0.f : asj[u].y;
+            }
+            ai[u][0] = __ffma2_rn(t[u], dx[u], ai[u][0]);
+            ai[u][1] = __ffma2_rn(t[u], dy[u], ai[u][1]);
+            ai[u][2] = __ffma2_rn(t[u], dz[u], ai[u][2]);
+            aj[0] = __ffma2_rn(t[u], dx[u], aj[0]); // the partner's gradient is minus this sum
+            aj[1] = __ffma2_rn(t[u], dy[u], aj[1]);
+            aj[2] = __ffma2_rn(t[u], dz[u], aj[2]);
+            ai[u][4] = __fadd2_rn(ai[u][4], asi[u]);
+            aj[4] = __fadd2_rn(aj[4], asj[u]);
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            aj[c].x = __shfl_sync(0xffffffffu, aj[c].x, src);
+            aj[c].y = __shfl_sync(0xffffffffu, aj[c].y, src);
+        }
+    }
 }
 
-__global__ void __launch_bounds__(kGT, 6) k_gchain_sym(SView g) {
-    __shared__ float4 sa[kGG * kGJ], sb[kGG * kGJ];
+__global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
+    __shared__ GcJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ][5];
-    __shared__ long long sfx[kGI][5];
+    __shared__ long long sfx[5][kGI]; // i-side sums, component-major (conflict-free)
     const GItem it = gitem(g);
     if (!it.ok) return;
     const int n = g.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -422,117 +592,86 @@ __global__ void __launch_bounds__(kGT, 6) k_gchain_sym(SView g) {
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
     const float off = (float)g.offset, rfar2 = gfar2(g);
-    const float cx = X[3 * it.i0], cy = X[3 * it.i0 + 1], cz = X[3 * it.i0 + 2];
     int ii[2];
     bool vi[2];
-    float xi[2], yi[2], zi[2], ci[2], si[2], rti[2], irti[2];
+    GcI2 I[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         ii[u] = it.i0 + warp * 64 + u * 32 + lane;
         vi[u] = ii[u] < n;
         const int i = vi[u] ? ii[u] : it.i0;
-        xi[u] = vi[u] ? X[3 * i] - cx : -kFar;
-        yi[u] = vi[u] ? X[3 * i + 1] - cy : -kFar;
-        zi[u] = vi[u] ? X[3 * i + 2] - cz : -kFar;
-        ci[u] = vi[u] ? (float)g.c[base + i] : 0.f;
-        rti[u] = vi[u] ? RH[i] - off : 1.f;
-        si[u] = vi[u] ? g.screen[i] * rti[u] : 0.f;
-        irti[u] = 1.f / rti[u];
+        const float rt = vi[u] ? RH[i] - off : 1.f, si = vi[u] ? g.screen[i] * rt : 0.f;
+        I[u].x = splat<float2>(vi[u] ? X[3 * i] : -kFar);
+        I[u].y = splat<float2>(vi[u] ? X[3 * i + 1] : -kFar);
+        I[u].z = splat<float2>(vi[u] ? X[3 * i + 2] : -kFar);
+        I[u].c = splat<float2>(vi[u] ? (float)g.c[base + i] : 0.f);
+        I[u].s2 = splat<float2>(si * si);
+        I[u].s3 = splat<float2>(si * si * si);
+        I[u].s = si;
+        I[u].rt = rt;
+        I[u].irt = 1.f / rt;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sfx[warp * 64 + u * 32 + lane][c] = 0;
+        for (int c = 0; c < 5; ++c) sfx[c][warp * 64 + u * 32 + lane] = 0;
     }
     for (int g0 = it.jt0; g0 < it.jt1; g0 += kGG) {
-        const int ng = min(kGG, it.jt1 - g0);
+        const int ng = min(kGG, it.jt1 - g0), npair = (ng + 1) >> 1;
         __syncthreads();
-        if (tid < ng * kGJ) {
-            const int j = g0 * kGJ + tid;
-            if (j < n) {
-                const float rtj = RH[j] - off;
-                sa[tid] = make_float4(X[3 * j] - cx, X[3 * j + 1] - cy, X[3 * j + 2] - cz, (float)g.c[base + j]);
-                sb[tid] = make_float4(g.screen[j] * rtj, rtj, 1.f / rtj, 0.f);
-            } else {
-                sa[tid] = make_float4(kFar, kFar, kFar, 0.f);
-                sb[tid] = make_float4(0.f, 1.f, 1.f, 0.f);
+        // stage the tile pairs: thread (pair, copy, entry) writes whole rows
+        for (int q = tid; q < npair * 2 * kGJ; q += kGT) {
+            const int pr = q >> 6, cpy = (q >> 5) & 1, e = q & 31;
+            float v[2][7];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gt = 2 * pr + h, j = (g0 + gt) * kGJ + e;
+                if (gt < ng && j < n) {
+                    const float rt = RH[j] - off;
+                    v[h][0] = -X[3 * j]; v[h][1] = -X[3 * j + 1]; v[h][2] = -X[3 * j + 2];
+                    v[h][3] = (float)g.c[base + j]; v[h][4] = g.screen[j] * rt; v[h][5] = rt; v[h][6] = 1.f / rt;
+                } else { // padding: far away, no weight, no sphere
+                    v[h][0] = kFar; v[h][1] = kFar; v[h][2] = kFar;
+                    v[h][3] = 0.f; v[h][4] = 0.f; v[h][5] = 1.f; v[h][6] = 1.f;
+                }
             }
+            GcJs& S = sj[pr];
+            const int r = e + cpy * kGJ;
+            const float s2a = v[0][4] * v[0][4], s2b = v[1][4] * v[1][4];
+            S.a[r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+            S.b[r] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+            S.c[r] = make_float4(s2a, s2b, s2a * v[0][4], s2b * v[1][4]);
+            S.n[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
+            S.m[r] = make_float2(v[0][6], v[1][6]);
         }
         __syncthreads();
-        for (int gt = 0; gt < ng; ++gt) {
-            const int jt = g0 + gt, j0 = jt * kGJ;
-            const bool msk = gmasked(jt, it.i0, n);
-            uint32_t skip[2] = {0u, 0u};
-            if (msk) {
-                skip[0] = gskip(ii[0], vi[0], j0, n);
-                skip[1] = gskip(ii[1], vi[1], j0, n);
+        for (int pr = 0; pr < npair; ++pr) {
+            float2 ai[2][5], aj[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) ai[0][c] = ai[1][c] = aj[c] = make_float2(0.f, 0.f);
+            uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
+            bool masked = false;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jt = g0 + 2 * pr + h;
+                if (jt < it.jt1 && gmasked(jt, it.i0, n)) {
+                    masked = true;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
+                }
             }
-            const float4* A4 = sa + gt * kGJ;
-            const float4* B4 = sb + gt * kGJ;
-            float ai[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
-            float aj[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-            for (int k = 0; k < kGJ; ++k) {
-                const int jj = (lane + k) & (kGJ - 1);
-                const float4 A = A4[jj];
-                const float4 B = B4[jj];
-                float dx[2], dy[2], dz[2], r2[2], rinv[2], hri[2], hrj[2], hti[2], htj[2], hsi[2], hsj[2];
-                bool sk[2], nr[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    dx[u] = xi[u] - A.x;
-                    dy[u] = yi[u] - A.y;
-                    dz[u] = zi[u] - A.z;
-                    r2[u] = fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u]));
-                    sk[u] = msk && ((skip[u] >> jj) & 1u);
-                    r2[u] = sk[u] ? 1.f : r2[u];
-                    rinv[u] = rsqrt_ftz(r2[u]);
-                    const float rinv2 = rinv[u] * rinv[u];
-                    hri[u] = hct_dr_series(rinv2, rinv[u], B.x);
-                    hrj[u] = hct_dr_series(rinv2, rinv[u], si[u]);
-                    hsi[u] = ds_series(rinv2, rinv[u], si[u]); // dH(r; rt_j, s_i)/ds
-                    hsj[u] = ds_series(rinv2, rinv[u], B.x);   // dH(r; rt_i, s_j)/ds
-                    hti[u] = 0.f;
-                    htj[u] = 0.f;
-                    nr[u] = r2[u] < rfar2;
-                }
-                if (__any_sync(0xffffffffu, nr[0] || nr[1])) {
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-                        if (nr[u]) {
-                            const float r = r2[u] * rinv[u];
-                            hri[u] = hct_dr(r, rinv[u], rti[u], B.x);
-                            hrj[u] = hct_dr(r, rinv[u], B.y, si[u]);
-                            hsi[u] = hct_ds(r, rinv[u], B.y, si[u]);
-                            hsj[u] = hct_ds(r, rinv[u], rti[u], B.x);
-                            hti[u] = hct_drt(r, rti[u], irti[u], B.x);
-                            htj[u] = hct_drt(r, B.y, B.z, si[u]);
-                        }
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const float m = sk[u] ? 0.f : 1.f;
-                    const float t = m * (ci[u] * hri[u] + A.w * hrj[u]) * rinv[u];
-                    ai[u][0] = fmaf(t, dx[u], ai[u][0]);
-                    ai[u][1] = fmaf(t, dy[u], ai[u][1]);
-                    ai[u][2] = fmaf(t, dz[u], ai[u][2]);
-                    aj[0] = fmaf(-t, dx[u], aj[0]);
-                    aj[1] = fmaf(-t, dy[u], aj[1]);
-                    aj[2] = fmaf(-t, dz[u], aj[2]);
-                    ai[u][3] = fmaf(m, hti[u], ai[u][3]);
-                    aj[3] = fmaf(m, htj[u], aj[3]);
-                    ai[u][4] = fmaf(m * A.w, hsi[u], ai[u][4]);
-                    aj[4] = fmaf(m * ci[u], hsj[u], aj[4]);
-                }
-                const int src = (lane + 1) & 31;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) aj[c] = __shfl_sync(0xffffffffu, aj[c], src);
-            }
+            if (masked) gchain_tile<true>(sj[pr], lane, I, ai, aj, sk, rfar2);
+            else gchain_tile<false>(sj[pr], lane, I, ai, aj, sk, rfar2);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                long long* row = sfx[warp * 64 + u * 32 + lane];
+                const int row = warp * 64 + u * 32 + lane;
 #pragma unroll
-                for (int c = 0; c < 5; ++c) row[c] += to_fixed(ai[u][c], (float)kScaleE);
+                for (int c = 0; c < 5; ++c)
+                    sfx[c][row] += to_fixed(ai[u][c].x, (float)kScaleE) + to_fixed(ai[u][c].y, (float)kScaleE);
             }
 #pragma unroll
-            for (int c = 0; c < 5; ++c) red[gt][warp][lane][c] = aj[c];
+            for (int c = 0; c < 5; ++c) {
+                const float sgn = c < 3 ? -1.f : 1.f;
+                red[2 * pr][warp][lane][c] = sgn * aj[c].x;
+                red[2 * pr + 1][warp][lane][c] = sgn * aj[c].y;
+            }
         }
         __syncthreads();
         for (int v = tid; v < ng * kGJ * 5; v += kGT) {
@@ -548,13 +687,13 @@ __global__ void __launch_bounds__(kGT, 6) k_gchain_sym(SView g) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (!vi[u]) continue;
-        const long long* row = sfx[warp * 64 + u * 32 + lane];
+        const int row = warp * 64 + u * 32 + lane;
         const size_t a = base + ii[u];
-        atomicAdd((unsigned long long*)&g.gfix[3 * a], (unsigned long long)row[0]);
-        atomicAdd((unsigned long long*)&g.gfix[3 * a + 1], (unsigned long long)row[1]);
-        atomicAdd((unsigned long long*)&g.gfix[3 * a + 2], (unsigned long long)row[2]);
-        atomicAdd((unsigned long long*)&g.artfix[a], (unsigned long long)row[3]);
-        atomicAdd((unsigned long long*)&g.asfix[a], (unsigned long long)row[4]);
+        atomicAdd((unsigned long long*)&g.gfix[3 * a], (unsigned long long)sfx[0][row]);
+        atomicAdd((unsigned long long*)&g.gfix[3 * a + 1], (unsigned long long)sfx[1][row]);
+        atomicAdd((unsigned long long*)&g.gfix[3 * a + 2], (unsigned long long)sfx[2][row]);
+        atomicAdd((unsigned long long*)&g.artfix[a], (unsigned long long)sfx[3][row]);
+        atomicAdd((unsigned long long*)&g.asfix[a], (unsigned long long)sfx[4][row]);
     }
 }
 

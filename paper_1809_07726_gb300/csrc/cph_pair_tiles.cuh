@@ -1,0 +1,104 @@
+// Pair-tile arithmetic shared by the engine's FP32 passes and the
+// differentiable GB energy: a lane's two i atoms against partner l + k of two
+// staged j-tiles (A, B) at step k, every quantity a float2 whose halves belong
+// to tile A and tile B, so that fma/add/mul.rn.f32x2 cover both tiles.
+#pragma once
+#include "cph_device.cuh"
+
+namespace cph {
+
+constexpr int kTileJ = 32; // atoms per j-tile
+
+// ========================================================= Born radii
+// Each unordered pair yields both descreening integrals, H(r, rt_i, s_j) for
+// psi_i (i-side sum ah) and H(r, rt_j, s_i) for psi_j (partner sum jh, which
+// moves one lane per step).  In the far regime H = P(y) s^3 / r^4 with
+// y = s^2 / r^2 (P the fitted series), so s^2 and s^3 are staged and 1/r^4
+// serves both directions.  Bit jj of sk[u][h] marks a pair of i atom u and
+// partner jj of tile h that is not counted.
+struct BoI2 {
+    float2 x, y, z, s2, s3; // the i atom's value in both halves
+    float s, rt, irt;       // closed-form operands
+};
+
+struct BoJs {
+    float4 a[2 * kTileJ]; // (-xA, -xB, -yA, -yB)
+    float4 b[2 * kTileJ]; // (-zA, -zB, s2A, s2B)
+    float4 c[2 * kTileJ]; // (s3A, s3B, sA, sB)
+    float4 n[2 * kTileJ]; // (rtA, rtB, 1/rtA, 1/rtB): closed forms
+};
+
+// Closed-form integrals of one pair inside r_far, kept out of line: a warp
+// only gets here when one of its lanes has such a pair, and a single copy of
+// this code keeps the unrolled tile loops small enough for the instruction
+// cache.  Returns (H(r, rt_i, s_j), H(r, rt_j, s_i)).
+static __device__ __noinline__ float2 born_near(float r2, float rinv, float rt_i, float irt_i, float s_i, float s_j,
+                                         float rt_j, float irt_j) {
+    const float r = r2 * rinv;
+    return make_float2(hct(r, rinv, rt_i, irt_i, s_j), hct(r, rinv, rt_j, irt_j, s_i));
+}
+
+template <bool MASKED>
+__device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (&I)[2], float2 (&ah)[2],
+                                          float2& jh, const uint32_t (&sk)[2][2], float rfar2) {
+    const int src = (lane + 1) & 31;
+    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
+#pragma unroll 2
+    for (int k = 0; k < kTileJ; ++k) {
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 s2j = make_float2(B.z, B.w), s3j = make_float2(C.x, C.y);
+        float2 r2[2], rinv[2], hi[2], hj[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            if (MASKED) { // skipped pairs stay off the closed-form branch
+                const int jj = (lane + k) & (kTileJ - 1);
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
+            }
+            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
+            hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), __fmul2_rn(s3j, rinv4));
+            hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), __fmul2_rn(I[u].s3, rinv4));
+        }
+        // closed forms only where some lane has a pair inside r_far (rare)
+        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        if (__any_sync(0xffffffffu, nr)) {
+            const float4 Nj = sj.n[lane + k];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (r2[u].x < rfar2) {
+                    const float2 h = born_near(r2[u].x, rinv[u].x, I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z);
+                    hi[u].x = h.x;
+                    hj[u].x = h.y;
+                }
+                if (r2[u].y < rfar2) {
+                    const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w);
+                    hi[u].y = h.x;
+                    hj[u].y = h.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (MASKED) {
+                const int jj = (lane + k) & (kTileJ - 1);
+                const bool s0 = (sk[u][0] >> jj) & 1u, s1 = (sk[u][1] >> jj) & 1u;
+                hi[u].x = s0 ? 0.f : hi[u].x;
+                hj[u].x = s0 ? 0.f : hj[u].x;
+                hi[u].y = s1 ? 0.f : hi[u].y;
+                hj[u].y = s1 ? 0.f : hj[u].y;
+            }
+            ah[u] = __fadd2_rn(ah[u], hi[u]);
+            jh = __fadd2_rn(jh, hj[u]);
+        }
+        jh.x = __shfl_sync(0xffffffffu, jh.x, src);
+        jh.y = __shfl_sync(0xffffffffu, jh.y, src);
+    }
+}
+
+} // namespace cph
