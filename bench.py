@@ -48,6 +48,9 @@ PASS_COST = {"born": (26, 1), "gb": (40, 3), "chain": (32, 1)}
 # dH/drt = 0 far) 48/1
 BACKWARD_COST = (106, 4)
 N_SM = 152
+# DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
+# capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
+PASS_DRAM_BYTES = {"chain": 60.49e6}
 FP32_LANES = 128   # FP32 lane operations per clock per SM
 MUFU_LANES = 16    # MUFU operations per clock per SM
 
@@ -156,12 +159,14 @@ def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
 
 # ----------------------------------------------------------------- oracle arm
 
-def oracle_sample(systems, grid, walkers, n_steps, seed):
+def oracle_sample(systems, grid, walkers, n_steps, seed, threads=1):
     """Time the FP64 oracle (as it stands) on ``walkers`` for n_steps of the
-    schedule, single-threaded; returns (seconds, pairs processed)."""
+    schedule, its walkers spread over ``threads`` host threads (the oracle's C
+    routines release the interpreter lock); returns (seconds, pairs processed)."""
     import oracle
     W = oracle.Walkers(systems, grid, seed=seed)
     W.t = 1
+    W.threads = threads
     t0 = time.perf_counter()
     oracle.run_schedule(W, n_steps, walkers=walkers)
     dt = time.perf_counter() - t0
@@ -305,6 +310,8 @@ def run_gpu(args):
 
     # dominant pair pass: CUDA events around each pass on the launching stream
     pass_ms = eng.time_passes(reps=3)
+    # per-SM pipe rates behind the roofline, measured on this GPU at its current clock
+    fp32_rate, mufu_rate = cphremd.probe_pipe_rates()
     names = ["born", "gb", "chain"]
     dom = int(np.argmax(pass_ms))
     f_mhz = clocks["sm_mhz"] or 2070.0
@@ -368,11 +375,19 @@ def run_gpu(args):
         oracle.build()
         sample = [0, 128, 320]  # one walker per system size (500, 2000, 8000 atoms)
         secs, pairs = oracle_sample(systems, grid, sample, 1, seed=seed)
-        cpu_value = 384.0 / (total_pairs / (pairs / secs))
-        cpu = {"value": cpu_value, "unit": "replica-steps/s", "cores": 1, "kind": "oracle",
-               "sample": "one full-schedule step of 3 walkers (500, 2000, 8000 atoms), "
-                         f"{secs:.1f} s single-threaded, scaled to the 384-walker mix by "
-                         "unordered pair count"}
+        one_core = 384.0 / (total_pairs / (pairs / secs))
+        # all host cores: one walker of the 8000-atom system per core
+        ncores = os.cpu_count() or 1
+        big = [w for w in range(grid.n_slots) if grid.system_of_slot[w] == 2][:ncores]
+        secs_all, pairs_all = oracle_sample(systems, grid, big, 1, seed=seed, threads=ncores)
+        all_cores = 384.0 / (total_pairs / (pairs_all / secs_all))
+        cpu = {"value": all_cores, "unit": "replica-steps/s", "cores": ncores, "kind": "oracle",
+               "sample": f"one full-schedule step of {len(big)} 8000-atom walkers on {ncores} "
+                         f"threads ({secs_all:.1f} s), scaled to the 384-walker mix by "
+                         "unordered pair count",
+               "one_core": {"value": one_core, "cores": 1,
+                            "sample": "one full-schedule step of 3 walkers (500, 2000, "
+                                      f"8000 atoms), {secs:.1f} s single-threaded"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "replica-steps/s", "n_gpus": world,
@@ -393,13 +408,18 @@ def run_gpu(args):
                          "ms_per_step": graph_ms, "steps": period},
         "pass_ms": {n: float(x) for n, x in zip(names, pass_ms)},
         "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
-                     "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": PASS_DRAM_BYTES.get(names[dom]),
+                     "traffic_basis": "DRAM read + write bytes per launch of the pass's pair kernel (ncu)",
                      "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) x "
                                    f"1/max({fp}/128, {mu}/16) pairs/clk/SM (FP32 lanes, MUFU)",
                      "step_frac": (total_pairs / (sum(pass_ms) / 1e3) / 1e9) / step_peak},
         "e2e": {"value": e2e_value, "unit": "replica-steps/s",
                 "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e},
         "backward": backward,
+        "pipe_rates": {"fp32_lane_ops_per_clk_per_sm": fp32_rate / (N_SM * f_mhz * 1e6),
+                       "mufu_ops_per_clk_per_sm": mufu_rate / (N_SM * f_mhz * 1e6),
+                       "assumed": [FP32_LANES, MUFU_LANES],
+                       "probe": "packed f32x2 FMA loop and rsqrt.approx loop, best of 3"},
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s": wall,

@@ -233,6 +233,15 @@ int cph_run(cph_engine* e, int64_t n_steps, void* stream);
  * charges and site states are unchanged.  Synchronises `stream`. */
 int cph_time_passes(cph_engine* e, int reps, double* ms /* host [3] */, void* stream);
 
+/* Diagnostic for the roofline of the pair passes: throughput of the FP32 (FMA)
+ * pipe, driven by packed f32x2 FMAs, and of the MUFU pipe, driven by
+ * rsqrt.approx, on the current device, timed with CUDA events on `stream`
+ * (best of three runs of about a millisecond each, after one warm-up run).
+ * Outputs are operations per second over the whole GPU (an FMA counts once);
+ * divided by the SM count and the SM clock they give the per-SM rates the
+ * roofline uses.  Allocates nothing; synchronises `stream`. */
+int cph_probe_pipe_rates(double* fp32_ops_per_s, double* mufu_ops_per_s, void* stream);
+
 /* Tile-shape autotuner: times the three pair passes at the current state for
  * each candidate work-item size (j-tiles of 32 atoms per CTA: 8..128) and
  * keeps the fastest; *chosen (may be NULL) receives it.  Derived per-atom
@@ -266,6 +275,23 @@ int cph_get_exchange_records(cph_engine* e, cph_exchange_record* out, int max, i
                              void* stream);
 int64_t cph_get_step(const cph_engine* e);
 int cph_set_step(cph_engine* e, int64_t step);
+
+/* Checkpoint and restart.  cph_get_state writes into one host buffer of
+ * cph_state_bytes(e) bytes everything that, with the engine's systems, grid
+ * and run parameters, fixes the rest of the trajectory: positions,
+ * velocities, site states, the condition map, the step counter, the Philox
+ * seed, the exchange counters (which dimension and which neighbour parity
+ * come next), pending velocity scales, the acceptance statistics and the
+ * sampling observables.  cph_set_state restores it into an engine built from
+ * the same systems, grid and run parameters (any seed: the checkpoint's seed
+ * is adopted); the continued run is then bitwise the run that wrote it.  A
+ * checkpoint of another layout or version is refused with CPH_E_INVALID and
+ * leaves the engine unchanged.  Forces, energies, Born radii and the records
+ * of the last MC / exchange event are derived and are not stored.  The
+ * buffer's format is private to the library (same version, same build). */
+size_t cph_state_bytes(const cph_engine* e);
+int cph_get_state(cph_engine* e, void* buf, size_t bytes, void* stream);
+int cph_set_state(cph_engine* e, const void* buf, size_t bytes, void* stream);
 /* Synchronise `stream` and report device-side status: CPH_OK, CPH_E_NONFINITE
  * (a walker produced a non-finite energy or position) or a CUDA error. */
 int cph_status(cph_engine* e, void* stream);

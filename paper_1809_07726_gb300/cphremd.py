@@ -135,9 +135,13 @@ def lib():
             "cph_get_exchange_records": ([vp, vp, i, vp, vp], i),
             "cph_get_step": ([vp], i64),
             "cph_set_step": ([vp, i64], i),
+            "cph_state_bytes": ([vp], C.c_size_t),
+            "cph_get_state": ([vp, vp, C.c_size_t, vp], i),
+            "cph_set_state": ([vp, vp, C.c_size_t, vp], i),
             "cph_status": ([vp, vp], i),
             "cph_time_passes": ([vp, i, vp, vp], i),
             "cph_autotune": ([vp, vp, C.POINTER(C.c_int)], i),
+            "cph_probe_pipe_rates": ([C.POINTER(C.c_double), C.POINTER(C.c_double), vp], i),
             "cph_gb_workspace_bytes": ([i, i], C.c_size_t),
             "cph_gb_energy": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, C.c_size_t,
                                vp], i),
@@ -360,6 +364,16 @@ class Engine:
                                                C.byref(got), _stream(stream)))
         return [buf[i] for i in range(got.value)]
 
+    def get_state(self, stream=None):
+        """Checkpoint as a uint8 array (see cph_get_state)."""
+        buf = np.zeros(lib().cph_state_bytes(self.ptr), np.uint8)
+        self._c(lib().cph_get_state(self.ptr, _p(buf), buf.size, _stream(stream)))
+        return buf
+
+    def set_state(self, buf, stream=None):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._c(lib().cph_set_state(self.ptr, _p(buf), buf.size, _stream(stream)))
+
     def get_step(self):
         return int(lib().cph_get_step(self.ptr))
 
@@ -383,6 +397,13 @@ class Engine:
 
     def walker_slice(self, w):
         return slice(int(self.offsets[w]), int(self.offsets[w + 1]))
+
+
+def probe_pipe_rates(stream=None):
+    """(FP32 lane ops/s, MUFU ops/s) measured on the current device."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().cph_probe_pipe_rates(C.byref(a), C.byref(b), _stream(stream)))
+    return a.value, b.value
 
 
 def fit_hill(kind, x, f, T=300.0, v=1.0):

@@ -1585,6 +1585,119 @@ int cph_set_step(cph_engine* e, int64_t step) {
     e->h_step = step;
     return CPH_OK;
 }
+// ---- checkpoint: one host byte buffer, header then fixed-order sections
+namespace {
+struct CkHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t W, total_atoms, site_rows;
+    uint64_t seed;
+    int64_t step;
+};
+constexpr uint32_t kCkVersion = 1;
+
+struct CkLayout {
+    size_t x, v, st, slot, wat, vs, ex, stats, occ, vis, nobs, total;
+};
+
+CkLayout ck_layout(const cph_engine* e) {
+    const size_t W = e->V.W, N = e->V.total_atoms, S = e->h_w_site_off.back();
+    CkLayout L;
+    size_t o = sizeof(CkHeader);
+    auto take = [&o](size_t bytes) { const size_t at = o; o += (bytes + 7) & ~size_t(7); return at; };
+    L.x = take(3 * N * sizeof(double));
+    L.v = take(3 * N * sizeof(double));
+    L.st = take(S * sizeof(int));
+    L.slot = take(W * sizeof(int));
+    L.wat = take(W * sizeof(int));
+    L.vs = take(W * sizeof(double));
+    L.ex = take(4 * sizeof(int));
+    L.stats = take(10 * sizeof(long long));
+    L.occ = take(S * CPH_MAX_STATES * sizeof(long long));
+    L.vis = take(W * W * sizeof(long long));
+    L.nobs = take(sizeof(long long));
+    L.total = o;
+    return L;
+}
+} // namespace
+
+size_t cph_state_bytes(const cph_engine* e) { return e ? ck_layout(e).total : 0; }
+
+int cph_get_state(cph_engine* e, void* buf, size_t bytes, void* stream) {
+    if (!e || !buf) return fail(e, CPH_E_INVALID, "NULL argument");
+    const CkLayout L = ck_layout(e);
+    if (bytes < L.total) return fail(e, CPH_E_INVALID, "state buffer holds %zu bytes, %zu needed", bytes, L.total);
+    char* b = (char*)buf;
+    const size_t W = e->V.W, N = e->V.total_atoms, S = e->h_w_site_off.back();
+    CkHeader h{};
+    memcpy(h.magic, "CPHCKPT", 8);
+    h.version = kCkVersion;
+    h.W = (int32_t)W;
+    h.total_atoms = (int32_t)N;
+    h.site_rows = (int32_t)S;
+    h.seed = e->V.seed;
+    h.step = e->h_step;
+    memcpy(b, &h, sizeof h);
+    TRY(copy_out(e, b + L.x, e->V.x, 3 * N * sizeof(double), stream));
+    TRY(copy_out(e, b + L.v, e->V.v, 3 * N * sizeof(double), stream));
+    if (S) TRY(copy_out(e, b + L.st, e->V.site_state, S * sizeof(int), stream));
+    TRY(copy_out(e, b + L.slot, e->V.slot_of, W * sizeof(int), stream));
+    TRY(copy_out(e, b + L.wat, e->V.walker_at, W * sizeof(int), stream));
+    TRY(copy_out(e, b + L.vs, e->V.vscale, W * sizeof(double), stream));
+    TRY(copy_out(e, b + L.ex, e->V.ex_state, 4 * sizeof(int), stream));
+    TRY(copy_out(e, b + L.stats, e->V.stats, 10 * sizeof(long long), stream));
+    if (S) TRY(copy_out(e, b + L.occ, e->V.occ, S * CPH_MAX_STATES * sizeof(long long), stream));
+    TRY(copy_out(e, b + L.vis, e->V.visits, W * W * sizeof(long long), stream));
+    TRY(copy_out(e, b + L.nobs, e->V.n_obs, sizeof(long long), stream));
+    return CPH_OK;
+}
+
+int cph_set_state(cph_engine* e, const void* buf, size_t bytes, void* stream) {
+    if (!e || !buf) return fail(e, CPH_E_INVALID, "NULL argument");
+    const CkLayout L = ck_layout(e);
+    const char* b = (const char*)buf;
+    const size_t W = e->V.W, N = e->V.total_atoms, S = e->h_w_site_off.back();
+    CkHeader h;
+    if (bytes < sizeof h) return fail(e, CPH_E_INVALID, "state buffer too short");
+    memcpy(&h, b, sizeof h);
+    if (memcmp(h.magic, "CPHCKPT", 8) != 0 || h.version != kCkVersion)
+        return fail(e, CPH_E_INVALID, "not an engine checkpoint (or another version)");
+    if ((size_t)h.W != W || (size_t)h.total_atoms != N || (size_t)h.site_rows != S || bytes < L.total)
+        return fail(e, CPH_E_INVALID, "checkpoint of another layout: %d walkers, %d atoms, %d site rows",
+                    h.W, h.total_atoms, h.site_rows);
+    if (h.step < 0) return fail(e, CPH_E_INVALID, "negative step in checkpoint");
+    const double* x = (const double*)(b + L.x);
+    const double* v = (const double*)(b + L.v);
+    for (size_t k = 0; k < 3 * N; ++k)
+        if (!std::isfinite(x[k]) || !std::isfinite(v[k])) return fail(e, CPH_E_INVALID, "non-finite coordinate in checkpoint");
+    std::vector<int> slot((const int*)(b + L.slot), (const int*)(b + L.slot) + W);
+    int ex[4];
+    memcpy(ex, b + L.ex, sizeof ex);
+    for (int k = 0; k < 4; ++k)
+        if (ex[k] < 0) return fail(e, CPH_E_INVALID, "bad exchange counters in checkpoint");
+    // validated setters: site states (also rebuild the charges) and condition map
+    if (S) TRY(cph_set_site_states(e, (const int*)(b + L.st), stream));
+    TRY(cph_set_condition_map(e, slot.data(), stream));
+    TRY(copy_in(e, e->V.x, x, 3 * N * sizeof(double), stream));
+    TRY(copy_in(e, e->V.v, v, 3 * N * sizeof(double), stream));
+    TRY(copy_in(e, e->V.vscale, b + L.vs, W * sizeof(double), stream));
+    TRY(copy_in(e, e->V.ex_state, ex, sizeof ex, stream));
+    TRY(copy_in(e, e->V.stats, b + L.stats, 10 * sizeof(long long), stream));
+    if (S) TRY(copy_in(e, e->V.occ, b + L.occ, S * CPH_MAX_STATES * sizeof(long long), stream));
+    TRY(copy_in(e, e->V.visits, b + L.vis, W * W * sizeof(long long), stream));
+    TRY(copy_in(e, e->V.n_obs, b + L.nobs, sizeof(long long), stream));
+    TRY(cph_set_step(e, h.step));
+    if (h.seed != e->V.seed) { // captured graphs hold the old key in their kernel parameters
+        e->V.seed = h.seed;
+        for (auto& g : e->graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    return CPH_OK;
+}
+
 int cph_status(cph_engine* e, void* stream) {
     if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
     int st = 0;

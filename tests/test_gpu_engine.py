@@ -291,3 +291,29 @@ def test_autotuned_tile_shape_changes_nothing_but_speed(ragged_systems):
     b.run(20)
     np.testing.assert_array_equal(a.positions(), b.positions())
     np.testing.assert_array_equal(a.forces(), b.forces())
+
+
+def test_checkpoint_restart_continues_bitwise(ragged_systems):
+    """A run restored from a checkpoint continues exactly as the run that
+    wrote it, whatever seed the restoring engine was built with; a checkpoint
+    of another layout is refused."""
+    grid = _grid_for(ragged_systems)
+    kw = dict(mc_ph_every=3, mc_redox_every=4, exchange_every=5)
+    a = cphremd.init_system(ragged_systems, grid, seed=13, **kw)
+    a.run(23)
+    ck = a.get_state()
+    a.run(37)
+    b = cphremd.init_system(ragged_systems, grid, seed=99, **kw)
+    b.set_state(ck)
+    assert b.get_step() == 23
+    b.run(37)
+    for get in ("positions", "velocities", "site_states", "condition_map", "accept_stats",
+                "visits", "charges"):
+        np.testing.assert_array_equal(getattr(a, get)(), getattr(b, get)())
+    np.testing.assert_array_equal(a.occupancy()[0], b.occupancy()[0])
+    assert a.get_step() == b.get_step() == 60
+    small = ragged_systems[:2]
+    c = cphremd.init_system(small, _grid_for(small), seed=13, **kw)
+    with pytest.raises(cphremd.CphError) as err:
+        c.set_state(ck)
+    assert err.value.code == cphremd.E_INVALID
