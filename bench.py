@@ -341,6 +341,16 @@ def run_gpu(args):
     barrier()
     pr_ms = p0.elapsed_time(p1) / n_pr
     pr_pass_ms = pr.time_passes(reps=1)
+    # the same per-replica launches spread over 8 streams (as 8 processes per GPU would)
+    pr.set_replica_streams(8)
+    pr.run(2)
+    barrier()
+    p0.record(stream)
+    for _ in range(n_pr):
+        pr.run(1)
+    p1.record(stream)
+    barrier()
+    pr8_ms = p0.elapsed_time(p1) / n_pr
     del pr
 
     # end to end through the public API from host buffers: init (H2D of the
@@ -403,7 +413,9 @@ def run_gpu(args):
         "pair_evals_per_s": world * total_pairs * args.steps / t_max,
         "per_replica": {"value": W / (pr_ms / 1e3), "unit": "replica-steps/s", "ms_per_step": pr_ms,
                         "pass_ms": [float(x) for x in pr_pass_ms],
-                        "speedup_batched": pr_ms / (1e3 * t_max / args.steps)},
+                        "speedup_batched": pr_ms / (1e3 * t_max / args.steps),
+                        "streams_8": {"value": W / (pr8_ms / 1e3), "ms_per_step": pr8_ms,
+                                      "speedup_batched": pr8_ms / (1e3 * t_max / args.steps)}},
         "graph_replay": {"value": W / (graph_ms / 1e3), "unit": "replica-steps/s",
                          "ms_per_step": graph_ms, "steps": period},
         "pass_ms": {n: float(x) for n, x in zip(names, pass_ms)},

@@ -197,6 +197,12 @@ int cph_site_offsets(const cph_engine* e, int* offsets /* host [W+1] into site-s
 #define CPH_LAUNCH_BATCHED 0
 #define CPH_LAUNCH_PER_REPLICA 1
 int cph_set_launch_mode(cph_engine* e, int mode);
+/* Streams of the per-replica launch mode: walker w's launches go to internal
+ * stream w mod n (n = 1..32; 1, the default, keeps them on the caller's
+ * stream).  Each per-walker launch sequence is forked from the caller's
+ * stream and joined back to it, as one process per replica sharing a GPU
+ * would overlap.  Results are bitwise identical for any n. */
+int cph_set_replica_streams(cph_engine* e, int n);
 
 /* Forces and energies of every walker at the current state (Born radii,
  * GB + Coulomb + LJ pair pass, chain rule through the radii, bonded terms,

@@ -105,6 +105,7 @@ def lib():
             "cph_walker_offsets": ([vp, vp], i),
             "cph_site_offsets": ([vp, vp], i),
             "cph_set_launch_mode": ([vp, i], i),
+            "cph_set_replica_streams": ([vp, i], i),
             "cph_evaluate": ([vp, vp], i),
             "cph_step_replicas": ([vp, i64, vp], i),
             "cph_mc_titrate": ([vp, i, vp], i),
@@ -257,6 +258,9 @@ class Engine:
     # ---- hot path
     def set_launch_mode(self, mode):
         self._c(lib().cph_set_launch_mode(self.ptr, mode))
+
+    def set_replica_streams(self, n):
+        self._c(lib().cph_set_replica_streams(self.ptr, int(n)))
 
     def evaluate(self, stream=None):
         self._c(lib().cph_evaluate(self.ptr, _stream(stream)))

@@ -446,6 +446,10 @@ struct cph_engine {
     int ex_cap = 0;
     int mc_kinds_last = 0;
     cudaStream_t cap_stream = nullptr;
+    // per-replica launches on several streams: walker w on rs[w % n_rs]
+    int n_rs = 1;
+    cudaStream_t rs[32] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[32] = {};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_period = 0;
     ~cph_engine() {
@@ -454,6 +458,11 @@ struct cph_engine {
         if (d_sym) cudaFree(d_sym);
         if (d_sym_by_w) cudaFree(d_sym_by_w);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (int k = 0; k < 32; ++k) {
+            if (rs[k]) cudaStreamDestroy(rs[k]);
+            if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
     }
 };
 
@@ -559,6 +568,29 @@ int launch_chain(cph_engine* E, const Item* items, int n, bool energy, cudaStrea
 int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, int s_off,
                   int mc_kinds);
 
+// Per-replica mode on n_rs > 1 streams: every per-walker launch sequence is
+// forked from the caller's stream and joined back to it, so ordering against
+// everything else on that stream (and stream capture) is kept.
+int fan_out(cph_engine* E, cudaStream_t st) {
+    if (E->launch_mode == 0 || E->n_rs <= 1) return CPH_OK;
+    CK(cudaEventRecord(E->ev_fork, st));
+    for (int k = 0; k < E->n_rs; ++k) CK(cudaStreamWaitEvent(E->rs[k], E->ev_fork, 0));
+    return CPH_OK;
+}
+
+int fan_in(cph_engine* E, cudaStream_t st) {
+    if (E->launch_mode == 0 || E->n_rs <= 1) return CPH_OK;
+    for (int k = 0; k < E->n_rs; ++k) {
+        CK(cudaEventRecord(E->ev_join[k], E->rs[k]));
+        CK(cudaStreamWaitEvent(st, E->ev_join[k], 0));
+    }
+    return CPH_OK;
+}
+
+cudaStream_t lane_stream(const cph_engine* E, int w, cudaStream_t st) {
+    return E->n_rs > 1 ? E->rs[w % E->n_rs] : st;
+}
+
 int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
     const int W = E->V.W;
     int first = 1;
@@ -571,12 +603,15 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
             else
                 k_mc<double><<<W, kMcThreads, 0, st>>>(E->V, kind, s_off, first, 0);
         } else {
+            TRY(fan_out(E, st));
             for (int w = 0; w < W; ++w) {
+                cudaStream_t s = lane_stream(E, w, st);
                 if (E->precision == CPH_PREC_FP32)
-                    k_mc<float><<<1, kMcThreads, 0, st>>>(E->V, kind, s_off, first, w);
+                    k_mc<float><<<1, kMcThreads, 0, s>>>(E->V, kind, s_off, first, w);
                 else
-                    k_mc<double><<<1, kMcThreads, 0, st>>>(E->V, kind, s_off, first, w);
+                    k_mc<double><<<1, kMcThreads, 0, s>>>(E->V, kind, s_off, first, w);
             }
+            TRY(fan_in(E, st));
         }
         first = 0;
         CK(cudaGetLastError());
@@ -649,21 +684,23 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
         if (pass == 2) TRY(launch_bonded(E, energy, 0, E->V.W, st));
         return launch_atoms(E, fin, energy, 0, E->V.total_atoms, st);
     }
+    TRY(fan_out(E, st));
     for (int w = 0; w < W; ++w) {
         const Item* it = E->d_items_by_w + E->item_w_off[w];
         const int ni = E->item_w_off[w + 1] - E->item_w_off[w];
+        cudaStream_t s = lane_stream(E, w, st);
         if (!fp32) {
-            if (pass == 0) TRY(launch_born(E, it, ni, energy, st));
-            else TRY(pass == 1 ? launch_gb(E, it, ni, energy, st) : launch_chain(E, it, ni, energy, st));
+            if (pass == 0) TRY(launch_born(E, it, ni, energy, s));
+            else TRY(pass == 1 ? launch_gb(E, it, ni, energy, s) : launch_chain(E, it, ni, energy, s));
         } else {
-            TRY(launch_stage(E, pass, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], st));
+            TRY(launch_stage(E, pass, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], s));
             TRY(launch_sym_pair(E, E->d_sym_by_w + E->sym_w_off[w], E->sym_w_off[w + 1] - E->sym_w_off[w],
-                                energy, pass, st));
-            if (pass == 2) TRY(launch_bonded(E, energy, w, 1, st));
-            TRY(launch_atoms(E, fin, energy, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], st));
+                                energy, pass, s));
+            if (pass == 2) TRY(launch_bonded(E, energy, w, 1, s));
+            TRY(launch_atoms(E, fin, energy, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], s));
         }
     }
-    return CPH_OK;
+    return fan_in(E, st);
 }
 
 int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, int s_off,
@@ -677,16 +714,19 @@ int launch_forces(cph_engine* E, bool energy, cudaStream_t st, bool mc_between, 
 
 int launch_langevin(cph_engine* E, int s_off, cudaStream_t st) {
     const int bs = 256;
-    auto one = [&](int a0, int n) {
+    auto one = [&](int a0, int n, cudaStream_t s) {
         if (E->precision == CPH_PREC_FP32)
-            k_langevin<float><<<(n + bs - 1) / bs, bs, 0, st>>>(E->V, s_off, a0, n);
+            k_langevin<float><<<(n + bs - 1) / bs, bs, 0, s>>>(E->V, s_off, a0, n);
         else
-            k_langevin<double><<<(n + bs - 1) / bs, bs, 0, st>>>(E->V, s_off, a0, n);
+            k_langevin<double><<<(n + bs - 1) / bs, bs, 0, s>>>(E->V, s_off, a0, n);
     };
     if (E->launch_mode == 0) {
-        one(0, E->V.total_atoms);
+        one(0, E->V.total_atoms, st);
     } else {
-        for (int w = 0; w < E->V.W; ++w) one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w]);
+        TRY(fan_out(E, st));
+        for (int w = 0; w < E->V.W; ++w)
+            one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], lane_stream(E, w, st));
+        TRY(fan_in(E, st));
     }
     CK(cudaGetLastError());
     return CPH_OK;
@@ -1273,6 +1313,22 @@ int cph_set_launch_mode(cph_engine* e, int mode) {
     if (!e || (mode != CPH_LAUNCH_BATCHED && mode != CPH_LAUNCH_PER_REPLICA))
         return fail(e, CPH_E_INVALID, "bad launch mode");
     e->launch_mode = mode;
+    return CPH_OK;
+}
+
+int cph_set_replica_streams(cph_engine* e, int n) {
+    if (!e || n < 1 || n > 32) return fail(e, CPH_E_INVALID, "replica streams must be 1..32");
+    cph_engine* E = e;
+    if (!e->ev_fork) CK(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming));
+    for (int k = 0; k < n; ++k) {
+        if (!e->rs[k]) CK(cudaStreamCreateWithFlags(&e->rs[k], cudaStreamNonBlocking));
+        if (!e->ev_join[k]) CK(cudaEventCreateWithFlags(&e->ev_join[k], cudaEventDisableTiming));
+    }
+    if (n != e->n_rs && e->graph[1]) { // the per-replica graph was captured on the old streams
+        cudaGraphExecDestroy(e->graph[1]);
+        e->graph[1] = nullptr;
+    }
+    e->n_rs = n;
     return CPH_OK;
 }
 

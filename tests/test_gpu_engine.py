@@ -33,9 +33,9 @@ def _grid_for(systems, per_system=2):
                       order=("E",))
 
 
-def _compare_walker(eng, w, sysd, x, q, tol_f, tol_e, tol_r):
+def _compare_walker(eng, w, sysd, x, q, tol_f, tol_e, tol_r, gb=None):
     o = oracle.OSystem(sysd)
-    terms, Fo, Ro, _ = oracle.energy(o, x, q, oracle.GBParams())
+    terms, Fo, Ro, _ = oracle.energy(o, x, q, gb or oracle.GBParams())
     sl = eng.walker_slice(w)
     F = eng.forces()[sl]
     R = eng.born_radii()[sl]
@@ -71,11 +71,16 @@ def test_batched_equals_per_replica_bitwise(ragged_systems):
     a = cphremd.init_system(ragged_systems, grid, seed=3)
     b = cphremd.init_system(ragged_systems, grid, seed=3)
     b.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
+    c = cphremd.init_system(ragged_systems, grid, seed=3)
+    c.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
+    c.set_replica_streams(4)  # walkers on four streams, forked and joined per sequence
     a.run(25)
     b.run(25)
+    c.run(25)
     for get in ("positions", "velocities", "forces", "born_radii", "site_states",
                 "condition_map"):
         np.testing.assert_array_equal(getattr(a, get)(), getattr(b, get)())
+        np.testing.assert_array_equal(getattr(a, get)(), getattr(c, get)())
 
 
 def test_runs_are_deterministic(ragged_systems):
@@ -317,3 +322,23 @@ def test_checkpoint_restart_continues_bitwise(ragged_systems):
     with pytest.raises(cphremd.CphError) as err:
         c.set_state(ck)
     assert err.value.code == cphremd.E_INVALID
+
+
+# OBC model II ("igb=5"), and model I with other dielectric constants: the
+# GB variants are parameter sets of the same kernels
+GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85),
+               dict(eps_in=2.0, eps_out=80.0, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125)]
+
+
+@pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
+                                           (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11)])
+@pytest.mark.parametrize("v", GB_VARIANTS)
+def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr):
+    grid = _grid_for(ragged_systems)
+    gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"])
+    eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec, gb=gb)
+    eng.evaluate()
+    og = oracle.GBParams(**v)
+    for w in range(grid.n_slots):
+        s = ragged_systems[grid.system_of_slot[w]]
+        _compare_walker(eng, w, s, s.x, s.q, tf, te, tr, gb=og)

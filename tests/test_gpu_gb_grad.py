@@ -81,3 +81,24 @@ def test_full_size_batch_sampled_replica():
     assert _rel_rms(dr[r], gr) <= 1e-5
     # every replica finite and distinct (each saw its own coordinates)
     assert np.isfinite(E).all() and len(np.unique(E)) == 128
+
+
+def test_obc2_energy_and_gradient_match_oracle():
+    """OBC model II ("igb=5": alpha 1.0, beta 0.8, gamma 4.85) through the same kernels."""
+    import torch
+    v = dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85)
+    gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"])
+    s, x, q, rho = _batch(2, 300, 71)
+    xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
+    st = _torch(s.screen, torch.float32)
+    E = cphremd.gb_energy(xt, qt, rt, st, gb=gb).cpu().numpy()
+    dx, dq, dr = (t.cpu().numpy().astype(np.float64) for t in cphremd.gb_energy_backward(
+        xt, qt, rt, st, torch.ones(2, dtype=torch.float64, device="cuda:0"), gb=gb))
+    for r in range(2):
+        xr, qr, rr = (a[r].astype(np.float32).astype(np.float64) for a in (x, q, rho))
+        Eo, gx, gq, gr = oracle.gb_grad(xr, qr, rr, s.screen.astype(np.float32).astype(np.float64),
+                                        oracle.GBParams(**v))
+        assert abs(E[r] - Eo) <= 1e-6 * abs(Eo), (E[r], Eo)
+        assert _rel_rms(dx[r], gx) <= 1e-5
+        assert _rel_rms(dq[r], gq) <= 1e-5
+        assert _rel_rms(dr[r], gr) <= 1e-5
