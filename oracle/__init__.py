@@ -64,7 +64,8 @@ def build(force: bool = False) -> str:
 
 class OGB(C.Structure):
     _fields_ = [("eps_in", C.c_double), ("eps_out", C.c_double), ("offset", C.c_double),
-                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double)]
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("kappa", C.c_double)]
 
 
 class OSYS(C.Structure):
@@ -108,16 +109,20 @@ def _p(a: np.ndarray):
 @dataclass
 class GBParams:
     """OBC model I ("igb=2") values: offset 0.09 A, (alpha, beta, gamma) =
-    (0.8, 0.0, 2.909125); eps_in = 1, eps_out = 78.5."""
+    (0.8, 0.0, 2.909125); eps_in = 1, eps_out = 78.5; no salt (kappa = 0).
+    With kappa > 0 every GB term -k q_i q_j tau / f takes tau(f) = 1/eps_in -
+    exp(-kappa f)/eps_out (Debye-Hueckel screening of the reaction field)."""
     eps_in: float = 1.0
     eps_out: float = 78.5
     offset: float = 0.09
     alpha: float = 0.8
     beta: float = 0.0
     gamma: float = 2.909125
+    kappa: float = 0.0   # salt screening (Debye-Hueckel), 1/A; 0 = no salt
 
     def c(self) -> OGB:
-        return OGB(self.eps_in, self.eps_out, self.offset, self.alpha, self.beta, self.gamma)
+        return OGB(self.eps_in, self.eps_out, self.offset, self.alpha, self.beta, self.gamma,
+                   self.kappa)
 
 
 def exclusion_matrix(n: int, bonds: np.ndarray, extra=None) -> np.ndarray:

@@ -33,6 +33,7 @@
 
 typedef struct {
     double eps_in, eps_out, offset, alpha, beta, gamma;
+    double kappa; /* Debye-Hueckel screening length inverse, 1/A (0: no salt) */
 } ogb;
 
 typedef struct {
@@ -152,23 +153,30 @@ void o_born(int n, const double *x, const double *rho, const double *screen,
     }
 }
 
-static double gb_tau(const ogb *g) { return 1.0 / g->eps_in - 1.0 / g->eps_out; }
+/* A GB pair at effective distance f (a self term: f = R) contributes
+ * -k q_i q_j tau(f) / f, with tau(f) = 1/eps_in - exp(-kappa f)/eps_out: the
+ * solvent's reaction field screened by salt in the Debye-Hueckel form
+ * (kappa = 0: the salt-free constant 1/eps_in - 1/eps_out).  Its derivative is
+ * d(tau(f)/f)/df = -taud(f)/f^2 with taud(f) = tau(f) - kappa f exp(-kappa f)/eps_out. */
+static double gb_tauf(const ogb *g, double f) { return 1.0 / g->eps_in - exp(-g->kappa * f) / g->eps_out; }
+static double gb_taud(const ogb *g, double f) {
+    return gb_tauf(g, f) - g->kappa * f * exp(-g->kappa * f) / g->eps_out;
+}
 
 /* ------------------------------------------------- electrostatics only */
 
 /* U_el = E_coul + E_GB for charges q at positions x with Born radii R. */
 double o_uel(const osys *S, const ogb *g, const double *x, const double *q, const double *R) {
     int n = S->n;
-    double tau = gb_tau(g);
     double e = 0.0;
-    for (int i = 0; i < n; i++) e += -0.5 * O_KCOUL * tau * q[i] * q[i] / R[i];
+    for (int i = 0; i < n; i++) e += -0.5 * O_KCOUL * gb_tauf(g, R[i]) * q[i] * q[i] / R[i];
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {
             double d[3];
             double r = dist(x, i, j, d);
             double RR = R[i] * R[j];
             double f = sqrt(r * r + RR * exp(-r * r / (4.0 * RR)));
-            e += -O_KCOUL * tau * q[i] * q[j] / f;
+            e += -O_KCOUL * gb_tauf(g, f) * q[i] * q[j] / f;
             if (!S->excl[(size_t)i * n + j]) e += O_KCOUL * q[i] * q[j] / (g->eps_in * r);
         }
     }
@@ -183,7 +191,6 @@ double o_uel(const osys *S, const ogb *g, const double *x, const double *q, cons
 void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
               double *terms, double *F, double *Rout, double *psiout) {
     int n = S->n;
-    double tau = gb_tau(g);
     double *psi = (double *)malloc(sizeof(double) * n);
     double *R = (double *)malloc(sizeof(double) * n);
     double *dEdR = (double *)calloc(n, sizeof(double));
@@ -192,8 +199,8 @@ void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
 
     double egb = 0.0, ecoul = 0.0, elj = 0.0, ebond = 0.0, eang = 0.0;
     for (int i = 0; i < n; i++) {
-        egb += -0.5 * O_KCOUL * tau * q[i] * q[i] / R[i];
-        dEdR[i] += 0.5 * O_KCOUL * tau * q[i] * q[i] / (R[i] * R[i]);
+        egb += -0.5 * O_KCOUL * gb_tauf(g, R[i]) * q[i] * q[i] / R[i];
+        dEdR[i] += 0.5 * O_KCOUL * gb_taud(g, R[i]) * q[i] * q[i] / (R[i] * R[i]);
     }
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {
@@ -204,8 +211,8 @@ void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
             double ex = exp(-D);
             double f = sqrt(r * r + RR * ex);
             double qq = q[i] * q[j];
-            egb += -O_KCOUL * tau * qq / f;
-            double dEdf = O_KCOUL * tau * qq / (f * f);
+            egb += -O_KCOUL * gb_tauf(g, f) * qq / f;
+            double dEdf = O_KCOUL * gb_taud(g, f) * qq / (f * f);
             double dfdr = r / f * (1.0 - 0.25 * ex);
             dEdR[i] += dEdf * R[j] * ex * (1.0 + D) / (2.0 * f);
             dEdR[j] += dEdf * R[i] * ex * (1.0 + D) / (2.0 * f);
@@ -303,7 +310,6 @@ void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
 void o_gb_grad(int n, const double *x, const double *q, const double *rho,
                const double *screen, const ogb *g, double *E,
                double *dx, double *dq, double *drho) {
-    double tau = gb_tau(g);
     double *psi = (double *)malloc(sizeof(double) * n);
     double *R = (double *)malloc(sizeof(double) * n);
     double *dEdR = (double *)calloc(n, sizeof(double));
@@ -313,9 +319,10 @@ void o_gb_grad(int n, const double *x, const double *q, const double *rho,
     o_born(n, x, rho, screen, g, psi, R);
     double e = 0.0;
     for (int i = 0; i < n; i++) {
-        e += -0.5 * O_KCOUL * tau * q[i] * q[i] / R[i];
-        gq[i] += -O_KCOUL * tau * q[i] / R[i];
-        dEdR[i] += 0.5 * O_KCOUL * tau * q[i] * q[i] / (R[i] * R[i]);
+        const double ts = gb_tauf(g, R[i]);
+        e += -0.5 * O_KCOUL * ts * q[i] * q[i] / R[i];
+        gq[i] += -O_KCOUL * ts * q[i] / R[i];
+        dEdR[i] += 0.5 * O_KCOUL * gb_taud(g, R[i]) * q[i] * q[i] / (R[i] * R[i]);
     }
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {
@@ -326,10 +333,11 @@ void o_gb_grad(int n, const double *x, const double *q, const double *rho,
             double ex = exp(-D);
             double f = sqrt(r * r + RR * ex);
             double qq = q[i] * q[j];
-            e += -O_KCOUL * tau * qq / f;
-            gq[i] += -O_KCOUL * tau * q[j] / f;
-            gq[j] += -O_KCOUL * tau * q[i] / f;
-            double dEdf = O_KCOUL * tau * qq / (f * f);
+            const double tf = gb_tauf(g, f);
+            e += -O_KCOUL * tf * qq / f;
+            gq[i] += -O_KCOUL * tf * q[j] / f;
+            gq[j] += -O_KCOUL * tf * q[i] / f;
+            double dEdf = O_KCOUL * gb_taud(g, f) * qq / (f * f);
             dEdR[i] += dEdf * R[j] * ex * (1.0 + D) / (2.0 * f);
             dEdR[j] += dEdf * R[i] * ex * (1.0 + D) / (2.0 * f);
             double dEdr = dEdf * r / f * (1.0 - 0.25 * ex);

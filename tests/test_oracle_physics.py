@@ -265,3 +265,64 @@ def test_gb_gradient_matches_finite_differences(small_chain):
         fd = (oracle.gb_grad(x, qp, s.rho, s.screen, gb)[0]
               - oracle.gb_grad(x, qm, s.rho, s.screen, gb)[0]) / (2 * h)
         assert dq[i] == pytest.approx(fd, rel=1e-7, abs=1e-8 * np.abs(dq).max())
+
+
+# ---------------------------------------------------------------- salt screening
+
+def test_salt_born_isolated_ion():
+    """With salt the lone ion's Born energy is -1/2 k (1/eps_in - exp(-kappa R)/eps_out) q^2/R."""
+    for kappa in (0.05, 0.3):
+        gb = GBParams(kappa=kappa)
+        q, rho = -0.8, 1.7
+        s, o = _one_system(1, [[0.1, 0.2, -0.3]], [q], [rho])
+        terms = oracle.energy(o, s.x, s.q, gb)[0]
+        Rb = rho - gb.offset
+        want = -0.5 * KCOUL * (1 / gb.eps_in - math.exp(-kappa * Rb) / gb.eps_out) * q * q / Rb
+        assert terms[0] == pytest.approx(want, rel=1e-14)
+
+
+def test_salt_far_pair_is_debye_huckel():
+    """Far apart (f = r), Coulomb + the GB cross term leave the screened
+    Debye-Hueckel interaction k q1 q2 exp(-kappa r) / (eps_out r)."""
+    q1, q2 = 0.7, -0.9
+    for kappa, r in ((0.1, 30.0), (0.1, 60.0), (0.02, 150.0)):
+        gb = GBParams(kappa=kappa)
+        s, o = _one_system(2, [[0, 0, 0], [r, 0, 0]], [q1, q2], [1.5, 1.7])
+        terms, _, R, _ = oracle.energy(o, s.x, s.q, gb)
+        self_e = sum(-0.5 * KCOUL * (1 / gb.eps_in - math.exp(-kappa * R[k]) / gb.eps_out) * qk * qk / R[k]
+                     for k, qk in enumerate((q1, q2)))
+        pair = terms[0] + terms[1] - self_e
+        target = KCOUL * q1 * q2 * math.exp(-kappa * r) / (gb.eps_out * r)
+        assert pair == pytest.approx(target, rel=1e-9)
+
+
+def test_salt_vanishing_kappa_is_salt_free(small_chain):
+    s, o, x = small_chain
+    t0 = oracle.energy(o, x, s.q, GBParams(), forces=False)[0]
+    t1 = oracle.energy(o, x, s.q, GBParams(kappa=1e-12), forces=False)[0]
+    np.testing.assert_allclose(t1, t0, rtol=1e-10)
+
+
+def test_salt_forces_and_gradient_match_central_differences(small_chain):
+    s, o, x = small_chain
+    gb = GBParams(kappa=0.15)
+    terms, F, _, _ = oracle.energy(o, x, s.q, gb)
+    E, dx, dq, dr = oracle.gb_grad(x, s.q, s.rho, s.screen, gb)
+    assert E == pytest.approx(terms[0], rel=1e-13)
+    assert float(np.dot(s.q, dq)) == pytest.approx(2 * E, rel=1e-12)  # still quadratic in q
+    h = 1e-5
+    rng = np.random.default_rng(5)
+    for i in rng.choice(s.n, 6, replace=False):
+        c = int(rng.integers(3))
+        xp, xm = x.copy(), x.copy()
+        xp[i, c] += h
+        xm[i, c] -= h
+        fd = -(oracle.energy(o, xp, s.q, gb, forces=False)[0][5]
+               - oracle.energy(o, xm, s.q, gb, forces=False)[0][5]) / (2 * h)
+        assert F[i, c] == pytest.approx(fd, rel=2e-6, abs=2e-6 * np.abs(F).max())
+        rp, rm = s.rho.copy(), s.rho.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (oracle.gb_grad(x, s.q, rp, s.screen, gb)[0]
+              - oracle.gb_grad(x, s.q, rm, s.screen, gb)[0]) / (2 * h)
+        assert dr[i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dr).max())
