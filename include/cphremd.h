@@ -135,11 +135,18 @@ typedef struct cph_grid_desc {
 } cph_grid_desc;
 
 /* OBC generalized-Born parameters ("igb=2": offset 0.09 A, alpha 0.8,
- * beta 0.0, gamma 2.909125; eps_in 1, eps_out 78.5). */
+ * beta 0.0, gamma 2.909125; eps_in 1, eps_out 78.5; "igb=5" is alpha 1.0,
+ * beta 0.8, gamma 4.85).  kappa >= 0 (1/A) screens the solvent reaction field
+ * by salt in the Debye-Hueckel form: every GB term -k q_i q_j tau / f takes
+ * tau(f) = 1/eps_in - exp(-kappa f)/eps_out (f = R for the self terms); the
+ * paper states no salt, and 0 (the default) gives the constant
+ * 1/eps_in - 1/eps_out.  The differentiable energy (cph_gb_energy*) takes
+ * kappa = 0 only. */
 typedef struct cph_gb_params {
     double eps_in, eps_out;
     double offset;                  /* rho_tilde = rho - offset */
     double alpha, beta, gamma;      /* tanh(alpha psi - beta psi^2 + gamma psi^3) */
+    double kappa;                   /* salt screening, 1/A (0 = none) */
 } cph_gb_params;
 
 typedef struct cph_run_params {

@@ -84,6 +84,19 @@ __host__ __device__ inline double unit_open(uint32_t u) {
     return (double)u * 2.3283064365386963e-10 + 1.1641532182693481e-10;
 }
 
+// ------------------------------------------------------- salt screening
+// A GB term of effective distance f (f = R for a self term) carries
+// tau(f) = 1/eps_in - exp(-kappa f)/eps_out; d(tau(f)/f)/df = -taud(f)/f^2 with
+// taud(f) = tau(f) - kappa f exp(-kappa f)/eps_out.  kappa = 0: both are the
+// constant 1/eps_in - 1/eps_out.
+__host__ __device__ inline double salt_tau(double f, double iei, double ieo, double kappa) {
+    return iei - exp(-kappa * f) * ieo;
+}
+__host__ __device__ inline double salt_taud(double f, double iei, double ieo, double kappa) {
+    const double es = exp(-kappa * f) * ieo;
+    return iei - es - kappa * f * es;
+}
+
 // --------------------------------------------------------- fixed point
 __device__ inline long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
 __device__ inline long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }

@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
     __shared__ double redd[kMcThreads / 32];
     const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
     const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
+    const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
+    const bool salt = V.kappa > 0;
     for (int k = 0; k < ns; ++k) {
         const int g = g0 + k;
         if (V.site_kind[g] != kind) {
@@ -92,14 +94,16 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
             Real part = 0;
             for (int m = 0; m < nat; ++m) {
                 if (mat[m] == j) {
-                    part += mdq[m] * qj * (-tau / mR[m]);
+                    const Real ts = salt ? iei - ieo * Pr::expm(kap * mR[m]) : tau;
+                    part += mdq[m] * qj * (-ts / mR[m]);
                 } else {
                     const Real dx = mx[m] - xj, dy = my[m] - yj, dz = mz[m] - zj;
                     const Real r2 = dx * dx + dy * dy + dz * dz;
                     const Real rinv = Pr::rsqrt(r2);
                     const Real D = Real(0.25) * r2 / (mR[m] * Rj);
                     const Real fi = Pr::rsqrt(r2 + mR[m] * Rj * Pr::expm(D));
-                    part += mdq[m] * qj * (iei * rinv - tau * fi);
+                    const Real tf = salt ? iei - ieo * Pr::expm(kap / fi) : tau;
+                    part += mdq[m] * qj * (iei * rinv - tf * fi);
                 }
             }
             Pr::add(lin, part, Real(kScaleE));
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
                 const int an = V.site_atoms[ao + n];
                 const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
                 if (n == m) {
-                    corr += 0.5 * dqm * dqn * (-V.tau * kCoulomb / Rm);
+                    corr += 0.5 * dqm * dqn * (-salt_tau(Rm, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / Rm);
                     continue;
                 }
                 const double d0 = xm0 - V.x[3 * (A + an)], d1 = xm1 - V.x[3 * (A + an) + 1],
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
                 const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 const double RR = Rm * V.R[A + an];
                 const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
-                double amn = -V.tau * kCoulomb / f;
+                double amn = -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / f;
                 bool ex = false;
                 for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e)
                     if (V.excl_j[e] == an) ex = true;
@@ -363,7 +367,7 @@ __global__ void k_site_ref(View V, const double* __restrict__ x0, const int* __r
     double U = 0.0;
     for (int m = 0; m < nat; ++m) {
         const double qm = V.site_q[qo + st * nat + m];
-        U += -0.5 * V.tau * kCoulomb * qm * qm / R[m];
+        U += -0.5 * salt_tau(R[m], V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb * qm * qm / R[m];
         const int am = V.site_atoms[ao + m];
         for (int n = m + 1; n < nat; ++n) {
             const int an = V.site_atoms[ao + n];
@@ -372,7 +376,8 @@ __global__ void k_site_ref(View V, const double* __restrict__ x0, const int* __r
                    d2 = x0[3 * (P + am) + 2] - x0[3 * (P + an) + 2];
             const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
             const double RR = R[m] * R[n];
-            U += -V.tau * kCoulomb * qm * qn / sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+            const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+            U += -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb * qm * qn / f;
             bool ex = false;
             for (int e = V.excl_off[P + am]; e < V.excl_off[P + am + 1]; ++e)
                 if (V.excl_j[e] == an) ex = true;
@@ -627,8 +632,11 @@ int launch_sym_pair(cph_engine* E, const SymItem* items, int n, bool energy, int
     if (n <= 0) return CPH_OK;
     if (pass == 0) k_born_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
     else if (pass == 2) k_chain_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
-    else if (energy) k_gb_sym<true><<<n, kSymThreads, 0, st>>>(items, E->V);
-    else k_gb_sym<false><<<n, kSymThreads, 0, st>>>(items, E->V);
+    else if (E->V.kappa > 0) {
+        if (energy) k_gb_sym<true, true><<<n, kSymThreads, 0, st>>>(items, E->V);
+        else k_gb_sym<false, true><<<n, kSymThreads, 0, st>>>(items, E->V);
+    } else if (energy) k_gb_sym<true, false><<<n, kSymThreads, 0, st>>>(items, E->V);
+    else k_gb_sym<false, false><<<n, kSymThreads, 0, st>>>(items, E->V);
     CK(cudaGetLastError());
     return CPH_OK;
 }
@@ -865,6 +873,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     if (!sys || n_sys < 1 || !grid || !p) return fail(nullptr, CPH_E_INVALID, "missing descriptor");
     if (p->precision != CPH_PREC_FP32 && p->precision != CPH_PREC_FP64)
         return fail(nullptr, CPH_E_INVALID, "unknown precision %d", p->precision);
+    if (!(p->gb.kappa >= 0) || !std::isfinite(p->gb.kappa))
+        return fail(nullptr, CPH_E_INVALID, "salt screening kappa must be finite and >= 0");
     if (!(p->dt > 0) || !(p->gamma_ln >= 0) || !(p->gb.eps_in > 0) || !(p->gb.eps_out > 0))
         return fail(nullptr, CPH_E_INVALID, "dt, gamma_ln, eps_in, eps_out must be positive");
     if (p->mc_ph_every < 0 || p->mc_redox_every < 0 || p->exchange_every < 0)
@@ -1248,6 +1258,9 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.n_order = grid->n_order;
     for (int k = 0; k < 3; ++k) V.order[k] = k < grid->n_order ? grid->order[k] : 0;
     V.tau = 1.0 / p->gb.eps_in - 1.0 / p->gb.eps_out;
+    V.kappa = p->gb.kappa;
+    V.inv_eps_out = 1.0 / p->gb.eps_out;
+    V.tau_pair = p->gb.kappa > 0 ? 1.0 : V.tau;
     V.inv_eps_in = 1.0 / p->gb.eps_in;
     V.sqrt_k = std::sqrt(kCoulomb);
     V.alpha = p->gb.alpha;

@@ -76,6 +76,10 @@ struct View {
     int order[3];
     // parameters
     double tau, inv_eps_in, sqrt_k, alpha, beta, gamma, offset, dt, gamma_ln;
+    // salt screening: kappa (1/A), 1/eps_out, and the factor the finishing
+    // kernels apply to pair sums (tau without salt; 1 with salt, whose pair
+    // kernels carry tau(f) per pair)
+    double kappa, inv_eps_out, tau_pair;
     float rfar2; // pairs with r^2 >= rfar2 are in the series regime in both directions
     // FP32 pair-kernel operands, staged once per step by one thread per atom
     float4* xs;          // (x, y, z, 0) relative to the walker's first atom

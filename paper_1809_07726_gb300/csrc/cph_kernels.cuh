@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         sei = Real(V.sqe[P + i]);
     }
     const Real tau = Real(V.tau), iei = Real(V.inv_eps_in);
+    const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
+    const bool salt = V.kappa > 0; // pair sums then carry tau(f) and taud(f) per pair
     Acc fx = 0, fy = 0, fz = 0, adr = 0, egb = 0, ec = 0, elj = 0;
     int mp = V.mt_off[it.st];
     const int me = V.mt_off[it.st + 1];
@@ -235,18 +237,24 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
                 const Real e = Pr::expm(D);
                 const Real fi = Pr::rsqrt(r2 + (Ri * b.x) * e);
                 const Real qf3 = qq * fi * fi * fi;
-                pdr += qf3 * b.x * e * (Real(1) + D);
+                Real tf = Real(1), td = Real(1);
+                if (salt) {
+                    const Real es = ieo * Pr::expm(kap / fi);
+                    tf = iei - es;
+                    td = tf - kap * es / fi;
+                }
+                pdr += td * qf3 * b.x * e * (Real(1) + D);
                 const Real sig = sgi + b.z;
                 const Real sr2 = sig * sig * rinv2;
                 const Real sr6 = sr2 * sr2 * sr2;
                 const Real ep = sei * b.w;
                 const Real fs = iei * qq * rinv * rinv2 + Real(4) * ep * sr6 * (Real(12) * sr6 - Real(6)) * rinv2
-                              - tau * qf3 * (Real(1) - Real(0.25) * e);
+                              - (salt ? td : tau) * qf3 * (Real(1) - Real(0.25) * e);
                 px += fs * dx;
                 py += fs * dy;
                 pz += fs * dz;
                 if (ENERGY) {
-                    pgb.add(qq * fi);
+                    pgb.add(tf * qq * fi);
                     pc.add(qq * rinv);
                     plj.add(ep * sr6 * (sr6 - Real(1)));
                 }
@@ -277,19 +285,25 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
                     const Real e = Pr::expm(D);
                     const Real fi = Pr::rsqrt(r2 + (Ri * b.x) * e);
                     const Real qf3 = g * qq * fi * fi * fi;
-                    pdr += qf3 * b.x * e * (Real(1) + D);
+                    Real tf = Real(1), td = Real(1);
+                    if (salt) {
+                        const Real es = ieo * Pr::expm(kap / fi);
+                        tf = iei - es;
+                        td = tf - kap * es / fi;
+                    }
+                    pdr += td * qf3 * b.x * e * (Real(1) + D);
                     const Real sig = sgi + b.z;
                     const Real sr2 = sig * sig * rinv2;
                     const Real sr6 = sr2 * sr2 * sr2;
                     const Real ep = nb * sei * b.w;
                     const Real fs = nb * iei * qq * rinv * rinv2
                                   + Real(4) * ep * sr6 * (Real(12) * sr6 - Real(6)) * rinv2
-                                  - tau * qf3 * (Real(1) - Real(0.25) * e);
+                                  - (salt ? td : tau) * qf3 * (Real(1) - Real(0.25) * e);
                     px += fs * dx;
                     py += fs * dy;
                     pz += fs * dz;
                     if (ENERGY) {
-                        pgb.add(g * qq * fi);
+                        pgb.add(tf * g * qq * fi);
                         pc.add(nb * qq * rinv);
                         plj.add(ep * sr6 * (sr6 - Real(1)));
                     }
@@ -309,7 +323,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
     if (vi) {
         const double q = V.q[A + i] * V.sqrt_k;
         const double R = V.R[A + i];
-        const double dEdR = 0.5 * V.tau * (Pr::value(adr, kScaleE) + q * q / (R * R));
+        const double dEdR = 0.5 * (V.tau_pair * Pr::value(adr, kScaleE)
+                                   + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R));
         V.c[A + i] = dEdR * V.dRdpsi[A + i] * 0.5 * V.rt[P + i];
         V.Fd[3 * (A + i)] = Pr::value(fx, kScaleE);
         V.Fd[3 * (A + i) + 1] = Pr::value(fy, kScaleE);
@@ -320,7 +335,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         if (vi) {
             const double q = V.q[A + i] * V.sqrt_k;
             const double R = V.R[A + i];
-            e0 = __double2ll_rn(-0.5 * V.tau * (Pr::value(egb, kScaleE) + q * q / R) * kScaleE);
+            e0 = __double2ll_rn(-0.5 * (V.tau_pair * Pr::value(egb, kScaleE)
+                                        + salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / R) * kScaleE);
             e1 = __double2ll_rn(0.5 * V.inv_eps_in * Pr::value(ec, kScaleE) * kScaleE);
             e2 = __double2ll_rn(2.0 * Pr::value(elj, kScaleE) * kScaleE);
         }

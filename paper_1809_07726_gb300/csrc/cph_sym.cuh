@@ -140,14 +140,19 @@ struct GbMask {
     uint32_t sk[2][2], nb[2][2];
 };
 
-template <bool MASKED, bool ENERGY>
+// SALT: Debye-Hueckel screening; the GB terms then carry tau(f) (energy) and
+// taud(f) (derivatives) per pair, f = 1 / fi, and the finishing kernels
+// apply 1 instead of tau to the pair sums.
+template <bool MASKED, bool ENERGY, bool SALT>
 __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I)[2], float2 (&a)[2][4],
-                                        float2 (&ja)[4], const GbMask& m, float tau, float iei,
-                                        KSum<float>& egb, KSum<float>& ec, KSum<float>& elj) {
+                                        float2 (&ja)[4], const GbMask& m, float tau, float iei, float kappa,
+                                        float ieo, KSum<float>& egb, KSum<float>& ec, KSum<float>& elj) {
     const int src = (lane + 1) & 31;
     const float2 ln2 = splat<float2>(kLn2), one = splat<float2>(1.f), c12 = splat<float2>(12.f),
                  cm6 = splat<float2>(-6.f), mtau = splat<float2>(-tau), qtau4 = splat<float2>(0.25f * tau),
-                 ie = splat<float2>(iei);
+                 ie = splat<float2>(iei), mone = splat<float2>(-1.f), q25 = splat<float2>(0.25f),
+                 kap2 = splat<float2>(kappa), ieo2 = splat<float2>(ieo);
+    const float kl = kappa * kLog2e;
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k], D = sj.d[lane + k];
@@ -185,7 +190,15 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
             const float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
             const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
             const float2 qfe = __fmul2_rn(qf3, e);
-            const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
+            float2 tf = one, td = one;
+            if (SALT) {
+                const float2 f = __fmul2_rn(fa, fi); // effective distance
+                const float2 es = __fmul2_rn(ieo2, make_float2(exp2_ftz(-kl * f.x), exp2_ftz(-kl * f.y)));
+                tf = __ffma2_rn(es, mone, ie);                                 // tau(f)
+                td = __ffma2_rn(__fmul2_rn(kap2, f), __fmul2_rn(es, mone), tf); // taud(f)
+            }
+            float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
+            if (SALT) t = __fmul2_rn(t, td);
             a[u][3] = __ffma2_rn(t, Rj, a[u][3]);
             ja[3] = __ffma2_rn(t, I[u].R, ja[3]);
             const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
@@ -193,8 +206,9 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
             const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
             const float2 l6 = __fmul2_rn(ep4, sr6);
             const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
-            // -tau qf3 (1 - e/4)
-            const float2 w = __ffma2_rn(qtau4, qfe, __fmul2_rn(mtau, qf3));
+            // -tau qf3 (1 - e/4); with salt taud(f) in place of tau
+            const float2 w = SALT ? __fmul2_rn(td, __ffma2_rn(q25, qfe, __fmul2_rn(mone, qf3)))
+                                  : __ffma2_rn(qtau4, qfe, __fmul2_rn(mtau, qf3));
             const float2 fs = __ffma2_rn(__ffma2_rn(cq, rinv, lj), rinv2, w);
             a[u][0] = __ffma2_rn(fs, dx, a[u][0]);
             a[u][1] = __ffma2_rn(fs, dy, a[u][1]);
@@ -203,7 +217,8 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
             ja[1] = __ffma2_rn(fs, dy, ja[1]);
             ja[2] = __ffma2_rn(fs, dz, ja[2]);
             if (ENERGY) {
-                const float2 eg = __fmul2_rn(qq, fi), eco = __fmul2_rn(cq, rinv);
+                const float2 eg = SALT ? __fmul2_rn(tf, __fmul2_rn(qq, fi)) : __fmul2_rn(qq, fi);
+                const float2 eco = __fmul2_rn(cq, rinv);
                 const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
                 egb.add(eg.x);
                 egb.add(eg.y);
@@ -221,7 +236,7 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
     }
 }
 
-template <bool ENERGY>
+template <bool ENERGY, bool SALT>
 __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __restrict__ items, View V) {
     __shared__ GbJs sj[kSymG / 2];
     __shared__ __align__(16) float red[kSymG][4][kSymJ][4];
@@ -230,7 +245,8 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float tau = (float)V.tau, iei = (float)V.inv_eps_in;
+    const float tau = (float)V.tau, iei = (float)V.inv_eps_in, kappa = (float)V.kappa,
+                ieo = (float)V.inv_eps_out;
     int ii[2];
     bool vi[2];
     GbI2 I[2];
@@ -307,8 +323,8 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
                     for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, m.sk[u][h], m.nb[u][h]);
                 }
             }
-            if (masked) gb_tile<true, ENERGY>(sj[pr], lane, I, acc, ja, m, tau, iei, egb, ec, elj);
-            else gb_tile<false, ENERGY>(sj[pr], lane, I, acc, ja, m, tau, iei, egb, ec, elj);
+            if (masked) gb_tile<true, ENERGY, SALT>(sj[pr], lane, I, acc, ja, m, tau, iei, kappa, ieo, egb, ec, elj);
+            else gb_tile<false, ENERGY, SALT>(sj[pr], lane, I, acc, ja, m, tau, iei, kappa, ieo, egb, ec, elj);
             // per-tile conversion (each half is one tile): independent of the item's chunking
 #pragma unroll
             for (int u = 0; u < 2; ++u)
@@ -361,8 +377,9 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
         if (tid < 3) {
             double v = 0.0;
             for (int q = 0; q < kSymThreads / 32; ++q) v += ered[q][tid];
-            // GB pairs carry -tau; Coulomb already has 1/eps_in, LJ its factor 4
-            const double scale = (tid == 0) ? -V.tau : 1.0;
+            // GB pairs carry -tau (with salt, tau(f) per pair and -1 here); Coulomb already has
+            // 1/eps_in, LJ its factor 4
+            const double scale = (tid == 0) ? -V.tau_pair : 1.0;
             atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + tid],
                       (unsigned long long)__double2ll_rn(scale * v * kScaleE));
         }
@@ -378,13 +395,15 @@ __global__ void k_fin_c(View V, int a0, int n) {
     const int w = V.a_walker[a];
     const int P = V.sys_poff[V.w_sys[w]] + (a - V.w_off[w]);
     const double q = V.q[a] * V.sqrt_k, R = V.R[a];
-    const double dEdR = 0.5 * V.tau * ((double)V.dRfix[a] / kScaleE + q * q / (R * R));
+    const double dEdR = 0.5 * (V.tau_pair * ((double)V.dRfix[a] / kScaleE)
+                               + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R));
     const double c = dEdR * V.dRdpsi[a] * 0.5 * V.rt[P];
     V.c[a] = c;
     V.c32[a] = (float)c;
     if (ENERGY)
         atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 0],
-                  (unsigned long long)__double2ll_rn(-0.5 * V.tau * q * q / R * kScaleE));
+                  (unsigned long long)__double2ll_rn(-0.5 * salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa)
+                                                     * q * q / R * kScaleE));
 }
 
 // ========================================================= chain rule

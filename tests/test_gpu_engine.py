@@ -136,17 +136,20 @@ def _band(x, prec):
 
 
 @pytest.mark.parametrize("prec", [cphremd.PREC_FP32, cphremd.PREC_FP64])
-def test_mc_sweep_matches_oracle(prec):
+@pytest.mark.parametrize("kappa", [0.0, 0.1])
+def test_mc_sweep_matches_oracle(prec, kappa):
     """One protonation + redox sweep on the 2400-atom system with 20 pH sites:
-    dU against the oracle's full recomputation, identical decisions."""
+    dU against the oracle's full recomputation, identical decisions; without
+    salt and with Debye-Hueckel screening (kappa = 0.1 / A)."""
     systems, grid = synth.config_c3()
     grid = synth.Grid(grid.E[[0, 3, 5, 7]], grid.pH[[0, 4]], grid.T, np.zeros(8, np.int32),
                       order=("E", "pH"))
-    eng = cphremd.init_system(systems, grid, seed=11, precision=prec)
+    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, kappa)
+    eng = cphremd.init_system(systems, grid, seed=11, precision=prec, gb=gb)
     eng.set_step(10)
     eng.mc_titrate(cphremd.MC_BOTH)
     recs = eng.mc_records()
-    W = oracle.Walkers(systems, grid, seed=11)
+    W = oracle.Walkers(systems, grid, seed=11, gb=oracle.GBParams(kappa=kappa))
     for w in range(grid.n_slots):
         oracle.mc_sweep(W, w, "ph", 10)
         oracle.mc_sweep(W, w, "redox", 10)
@@ -324,10 +327,12 @@ def test_checkpoint_restart_continues_bitwise(ragged_systems):
     assert err.value.code == cphremd.E_INVALID
 
 
-# OBC model II ("igb=5"), and model I with other dielectric constants: the
-# GB variants are parameter sets of the same kernels
-GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85),
-               dict(eps_in=2.0, eps_out=80.0, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125)]
+# OBC model II ("igb=5"), model I with other dielectric constants, and model I
+# with salt screening: the GB variants are parameter sets of the same kernels
+GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85, kappa=0.0),
+               dict(eps_in=2.0, eps_out=80.0, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125, kappa=0.0),
+               dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125,
+                    kappa=0.1)]  # Debye-Hueckel salt screening
 
 
 @pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
@@ -335,7 +340,8 @@ GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, 
 @pytest.mark.parametrize("v", GB_VARIANTS)
 def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr):
     grid = _grid_for(ragged_systems)
-    gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"])
+    gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"],
+                          v["kappa"])
     eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec, gb=gb)
     eng.evaluate()
     og = oracle.GBParams(**v)

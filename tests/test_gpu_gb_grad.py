@@ -102,3 +102,14 @@ def test_obc2_energy_and_gradient_match_oracle():
         assert _rel_rms(dx[r], gx) <= 1e-5
         assert _rel_rms(dq[r], gq) <= 1e-5
         assert _rel_rms(dr[r], gr) <= 1e-5
+
+
+def test_salt_is_refused_by_the_differentiable_energy():
+    import torch
+    s, x, q, rho = _batch(1, 40, 3)
+    xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
+    st = _torch(s.screen, torch.float32)
+    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, 0.1)
+    with pytest.raises(cphremd.CphError) as e:
+        cphremd.gb_energy(xt, qt, rt, st, gb=gb)
+    assert e.value.code == cphremd.E_INVALID
