@@ -16,10 +16,15 @@ Schedule of global step t (x_t are the positions after t MD steps):
      is counted at the walker's current condition, and the walker's visit to
      that condition (the per-condition fractions that eqs (1) and (2) are
      fitted to in the results, and Figure 7's visitation counts);
-  6. Langevin step to x_{t+1} at the walker's current temperature.
+  6. Langevin step to x_{t+1} at the walker's current temperature, followed,
+     when SHAKE is on, by SHAKE on every bond that involves a hydrogen (an
+     atom lighter than 2 amu): those bonds are held at their r0 and their
+     harmonic terms are left out (the Implicit Solvent Calculations section
+     runs SHAKE at 2 fs).
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
@@ -55,9 +60,16 @@ class Walkers:
     exchange_every: int = 100
     gb: GBParams = field(default_factory=GBParams)
     t: int = 0
+    shake: bool = False
+    shake_tol: float = 1e-10
 
     def __post_init__(self):
-        self.osys = [OSystem(s) for s in self.systems]
+        if self.shake:
+            self.clusters = [shake_clusters(s) for s in self.systems]
+            self.osys = [OSystem(dataclasses.replace(s, bond_k=np.where(_h_bond(s), 0.0, s.bond_k)))
+                         for s in self.systems]
+        else:
+            self.osys = [OSystem(s) for s in self.systems]
         self.uref = [reference_energies(o, s, self.gb) for o, s in zip(self.osys, self.systems)]
         ns = self.grid.n_slots
         self.sys_of = np.asarray(self.grid.system_of_slot, np.int64).copy()
@@ -229,6 +241,55 @@ def exchange_attempt(W: Walkers, dim: str, t: int):
                     W.v[wj] *= math.sqrt(Ti / Tj)
 
 
+def _h_bond(sysd):
+    m = np.asarray(sysd.mass)
+    b = np.asarray(sysd.bonds).reshape(-1, 2)
+    return (m[b[:, 0]] < 2.0) | (m[b[:, 1]] < 2.0)
+
+
+def shake_clusters(sysd):
+    """The constrained bonds (those that involve an atom lighter than 2 amu)
+    grouped by their heavy atom, in atom order: [(heavy, [(h, r0), ...]), ...],
+    each group's hydrogens in bond-list order."""
+    m = np.asarray(sysd.mass)
+    groups = {}
+    for (a, b), r0, hb in zip(np.asarray(sysd.bonds).reshape(-1, 2), sysd.bond_r0, _h_bond(sysd)):
+        if not hb:
+            continue
+        heavy, h = (int(a), int(b)) if m[b] < 2.0 else (int(b), int(a))
+        if m[heavy] < 2.0:
+            raise ValueError("a bond between two hydrogens cannot be constrained")
+        groups.setdefault(heavy, []).append((h, float(r0)))
+    return sorted(groups.items())
+
+
+def shake(x_old, x, v, mass, clusters, dt, tol, max_iter=1000):
+    """SHAKE (Ryckaert, Ciccotti & Berendsen 1977) after a leapfrog step from
+    x_old: each constraint in turn moves its two atoms along the old bond
+    vector, in inverse proportion to their masses, until every constrained
+    distance d satisfies |d0^2 - d^2| <= 2 tol d0^2; a cluster (one heavy atom
+    and its hydrogens) is swept until none of its constraints moves.  The
+    velocities take the same displacement divided by dt."""
+    x_start = x.copy()
+    for heavy, hs in clusters:
+        for _ in range(max_iter):
+            done = True
+            for h, d0 in hs:
+                rij = x[heavy] - x[h]
+                diff = d0 * d0 - float(rij @ rij)
+                if abs(diff) > 2.0 * tol * d0 * d0:
+                    done = False
+                    rold = x_old[heavy] - x_old[h]
+                    g = diff / (2.0 * float(rold @ rij) * (1.0 / mass[heavy] + 1.0 / mass[h]))
+                    x[heavy] += g * rold / mass[heavy]
+                    x[h] -= g * rold / mass[h]
+            if done:
+                break
+        else:
+            raise RuntimeError("SHAKE did not converge")
+    v += (x - x_start) / dt
+
+
 def run_schedule(W: Walkers, n_steps: int, walkers=None):
     """Advance every walker (or the listed subset, for timing samples) by
     n_steps of the schedule in the module docstring."""
@@ -273,7 +334,10 @@ def run_schedule(W: Walkers, n_steps: int, walkers=None):
         def step(w):
             o = W.osys[W.sys_of[w]]
             T = W.cond(w)[2]
+            x_old = W.x[w].copy() if W.shake else None
             langevin(W.x[w], W.v[w], W.F[w], o.mass, W.dt, W.gamma, T, W.seed, w, t)
+            if W.shake:
+                shake(x_old, W.x[w], W.v[w], o.mass, W.clusters[W.sys_of[w]], W.dt, W.shake_tol)
 
         W._map(step, ws)
         W.t += 1

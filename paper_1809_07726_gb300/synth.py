@@ -265,6 +265,97 @@ def slot_index(iE: int, ipH: int, iT: int, nE: int, npH: int) -> int:
     return iE + nE * (ipH + npH * iT)
 
 
+H_MASS, H_RHO, H_SCREEN, H_SIGMA, H_EPS, H_Q = 1.008, 1.2, 0.85, 1.07, 0.0157, 0.1
+XH_K, XH_R0 = 340.0, 1.09                 # bond X-H
+XXH_K, HXH_K, TETRA = 50.0, 35.0, math.acos(-1.0 / 3.0)
+
+
+def add_hydrogens(s: System, frac: float, seed: int) -> System:
+    """A copy of a heavy-atom system with hydrogens: a fraction ``frac`` of the
+    chain atoms carry one or two hydrogens (chain ends three), each 1.09 A
+    from its heavy atom, pointing away from the chain neighbours at
+    tetrahedral angles, and placed only where it keeps >= 1.6 A from every
+    other atom.  A hydrogen takes +0.1 e from its heavy atom (net charge
+    unchanged).  Bonds X-H (k 340, r0 1.09) and angles X-X-H (k 50) and H-X-H
+    (k 35) at the tetrahedral angle join the force field; hydrogens follow
+    their heavy atom in the atom order, and site atoms keep their identity."""
+    rng = np.random.default_rng(seed)
+    n = s.n
+    nbr = [[] for _ in range(n)]
+    for a, b in s.bonds:
+        nbr[int(a)].append(int(b))
+        nbr[int(b)].append(int(a))
+    placed = [list(r) for r in s.x]
+    hs = [[] for _ in range(n)]
+    carry = rng.uniform(size=n) < frac
+
+    def clear(p, skip):
+        d = np.linalg.norm(np.asarray(placed) - p, axis=1)
+        d[skip] = np.inf
+        return d.min() >= 1.6
+
+    for i in range(n):
+        if not carry[i] or not nbr[i]:
+            continue
+        u = [(s.x[j] - s.x[i]) / np.linalg.norm(s.x[j] - s.x[i]) for j in nbr[i]]
+        away = -np.sum(u, axis=0)
+        away /= np.linalg.norm(away)
+        if len(u) == 1:  # chain end: three hydrogens around the bond axis
+            ref = np.cross(away, rng.normal(size=3))
+            ref /= np.linalg.norm(ref)
+            oth = np.cross(away, ref)
+            # tetrahedral: each X-H makes 109.47 deg with the X-neighbour bond
+            cz, sz = -math.cos(TETRA), math.sin(TETRA)
+            dirs = [cz * away + sz * (math.cos(t) * ref + math.sin(t) * oth)
+                    for t in (0.0, 2.0943951, 4.1887902)]
+        else:
+            nrm = np.cross(u[0], u[1])
+            nrm /= np.linalg.norm(nrm)
+            h = 0.5 * TETRA
+            two = [math.cos(h) * away + math.sin(h) * nrm, math.cos(h) * away - math.sin(h) * nrm]
+            dirs = two if rng.uniform() < 0.5 else [away]
+        for d in dirs:
+            p = s.x[i] + XH_R0 * d / np.linalg.norm(d)
+            if clear(p, [i]):
+                placed.append(list(p))
+                hs[i].append(p)
+    # new order: each heavy atom followed by its hydrogens
+    new_of = np.zeros(n, np.int64)
+    xs, mass, q, rho, scr, sig, eps = [], [], [], [], [], [], []
+    bonds, bk, br0, angles, ak, at0 = [], [], [], [], [], []
+    k = 0
+    h_idx = [[] for _ in range(n)]
+    for i in range(n):
+        new_of[i] = k
+        xs.append(s.x[i]); mass.append(s.mass[i]); q.append(s.q[i] - H_Q * len(hs[i]))
+        rho.append(s.rho[i]); scr.append(s.screen[i]); sig.append(s.sigma[i]); eps.append(s.eps[i])
+        k += 1
+        for p in hs[i]:
+            h_idx[i].append(k)
+            xs.append(p); mass.append(H_MASS); q.append(H_Q); rho.append(H_RHO); scr.append(H_SCREEN)
+            sig.append(H_SIGMA); eps.append(H_EPS)
+            k += 1
+    for (a, b), kk, r0 in zip(s.bonds, s.bond_k, s.bond_r0):
+        bonds.append((new_of[a], new_of[b])); bk.append(kk); br0.append(r0)
+    for (a, b, c), kk, t0 in zip(s.angles, s.angle_k, s.angle_t0):
+        angles.append((new_of[a], new_of[b], new_of[c])); ak.append(kk); at0.append(t0)
+    for i in range(n):
+        for hh in h_idx[i]:
+            bonds.append((new_of[i], hh)); bk.append(XH_K); br0.append(XH_R0)
+            for j in nbr[i]:
+                angles.append((new_of[j], new_of[i], hh)); ak.append(XXH_K); at0.append(TETRA)
+        for a_ in range(len(h_idx[i])):
+            for b_ in range(a_ + 1, len(h_idx[i])):
+                angles.append((h_idx[i][a_], new_of[i], h_idx[i][b_])); ak.append(HXH_K); at0.append(TETRA)
+    sites = [Site(st.kind, new_of[st.atoms].astype(np.int32), st.q.copy(), st.n_prot.copy(),
+                  st.n_elec.copy(), st.ref, st.init_state) for st in s.sites]
+    return System(x=np.array(xs), mass=np.array(mass), q=np.array(q), rho=np.array(rho),
+                  screen=np.array(scr), sigma=np.array(sig), eps=np.array(eps),
+                  bonds=np.array(bonds, np.int32).reshape(-1, 2), bond_k=np.array(bk),
+                  bond_r0=np.array(br0), angles=np.array(angles, np.int32).reshape(-1, 3),
+                  angle_k=np.array(ak), angle_t0=np.array(at0), sites=sites, seed=s.seed)
+
+
 def titratable_ion(kind: str, ref: float, rho: float = 1.6) -> System:
     """One atom that is a whole titratable site.  pH: state 0 protonated
     (q = 0, one proton), state 1 deprotonated (q = -1).  Redox: state 0
@@ -284,6 +375,17 @@ def titratable_ion(kind: str, ref: float, rho: float = 1.6) -> System:
                   bonds=np.zeros((0, 2), np.int32), bond_k=z[:0].copy(), bond_r0=z[:0].copy(),
                   angles=np.zeros((0, 3), np.int32), angle_k=z[:0].copy(),
                   angle_t0=z[:0].copy(), sites=[site])
+
+
+def config_h():
+    """A 128-heavy-atom chain with hydrogens on about half its atoms (about 240
+    atoms, the size of the paper's NAcMP8 + His peptide system), 2 pH sites
+    and 1 redox site; 4 walkers along E at pH 7, 300 K.  For SHAKE."""
+    s = add_hydrogens(make_system(128, 8, n_ph=2, ph_states=(2, 2), ph_atoms=(6, 6),
+                                  ph_pka=[4.4, 4.85]), 0.55, 8)
+    g = Grid(np.linspace(-0.26, -0.14, 4), np.array([7.0]), np.array([300.0]),
+             np.zeros(4, np.int32), order=("E",))
+    return [s], g
 
 
 # ---------------------------------------------------------------------------
