@@ -157,6 +157,16 @@ typedef struct cph_run_params {
     int mc_ph_every;                /* protonation sweep interval in steps (0 = never) */
     int mc_redox_every;             /* redox sweep interval in steps (0 = never) */
     int exchange_every;             /* steps between exchange attempts (0 = never) */
+    /* SHAKE (Implicit Solvent Calculations section: 2 fs steps with the
+     * lengths of all bonds to hydrogen constrained).  1: after every Langevin
+     * step, each bond that involves an atom lighter than 2 amu is held at its
+     * r0 by SHAKE (iterated along the old bond vectors until
+     * |r0^2 - r^2| <= 2 shake_tol r0^2; velocities take the displacement / dt),
+     * and those bonds' harmonic terms are left out.  A bond between two such
+     * atoms, or more than 8 on one heavy atom, is refused.  0: no
+     * constraints. */
+    int shake;
+    double shake_tol;               /* > 0 when shake = 1, e.g. 1e-8 */
 } cph_run_params;
 
 typedef struct cph_engine cph_engine; /* opaque */

@@ -65,7 +65,7 @@ class GBParams(C.Structure):
 class RunParams(C.Structure):
     _fields_ = [("gb", GBParams), ("dt", C.c_double), ("gamma_ln", C.c_double),
                 ("precision", C.c_int), ("mc_ph_every", C.c_int), ("mc_redox_every", C.c_int),
-                ("exchange_every", C.c_int)]
+                ("exchange_every", C.c_int), ("shake", C.c_int), ("shake_tol", C.c_double)]
 
 
 class MCRecord(C.Structure):
@@ -425,7 +425,7 @@ def fit_hill(kind, x, f, T=300.0, v=1.0):
 
 def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.0,
                 mc_ph_every=10, mc_redox_every=10, exchange_every=100, gb=None,
-                velocities=None) -> Engine:
+                velocities=None, shake=False, shake_tol=1e-10) -> Engine:
     """cph_init_system for a list of ``synth.System`` and a ``synth.Grid``."""
     keep = _Keep()
     descs = (SystemDesc * len(systems))()
@@ -439,7 +439,7 @@ def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.
     for k, name in enumerate(grid.order):
         g.order[k] = DIM_NAMES[name]
     p = RunParams(gb or default_gb(), dt, gamma_ln, precision, mc_ph_every, mc_redox_every,
-                  exchange_every)
+                  exchange_every, 1 if shake else 0, shake_tol)
     out = C.c_void_p()
     rc = lib().cph_init_system(C.cast(descs, C.c_void_p), len(systems), C.byref(g), C.byref(p),
                                C.c_uint64(seed), C.byref(out))

@@ -432,6 +432,8 @@ struct cph_engine {
     DevBuf mem;
     int precision = CPH_PREC_FP32;
     int launch_mode = 0; // 0 batched, 1 per replica
+    int n_shk = 0;                  // SHAKE work items (walker, cluster); 0 when off
+    std::vector<int> h_shk_w_off;   // per-walker ranges of the SHAKE items
     int mc_ph = 0, mc_redox = 0, ex_every = 0;
     long long h_step = 0;
     int n_sys = 0;
@@ -728,12 +730,19 @@ int launch_langevin(cph_engine* E, int s_off, cudaStream_t st) {
         else
             k_langevin<double><<<(n + bs - 1) / bs, bs, 0, s>>>(E->V, s_off, a0, n);
     };
+    auto shk = [&](int i0, int n, cudaStream_t s) {
+        if (n > 0) k_shake<<<(n + 127) / 128, 128, 0, s>>>(E->V, i0, n);
+    };
     if (E->launch_mode == 0) {
         one(0, E->V.total_atoms, st);
+        shk(0, E->n_shk, st);
     } else {
         TRY(fan_out(E, st));
-        for (int w = 0; w < E->V.W; ++w)
-            one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], lane_stream(E, w, st));
+        for (int w = 0; w < E->V.W; ++w) {
+            cudaStream_t s = lane_stream(E, w, st);
+            one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], s);
+            if (E->n_shk) shk(E->h_shk_w_off[w], E->h_shk_w_off[w + 1] - E->h_shk_w_off[w], s);
+        }
         TRY(fan_in(E, st));
     }
     CK(cudaGetLastError());
@@ -898,6 +907,11 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     std::vector<int> excl_off(1, 0), excl_j, bond_off(1, 0), bond_idx, bond_ij, ang_off(1, 0),
         ang_idx, ang_ijk;
     std::vector<double> bond_k, bond_r0, ang_k, ang_t0;
+    // SHAKE clusters (system-local atom indices), concatenated over systems
+    std::vector<int> shk_heavy, shk_off{0}, shk_h, shk_sys_off{0};
+    std::vector<double> shk_d;
+    if (p->shake && !(p->shake_tol > 0) )
+        return fail(nullptr, CPH_E_INVALID, "shake_tol must be > 0 when shake is on");
     std::vector<int> site_kind, site_nat, site_aoff, site_atoms, site_nst, site_qoff, site_noff,
         site_np, site_ne, site_sys, site_init;
     std::vector<double> site_q, site_ref;
@@ -933,6 +947,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         if (d.n_bonds < 0 || (d.n_bonds > 0 && (!d.bonds || !d.bond_k || !d.bond_r0)))
             return fail(nullptr, CPH_E_INVALID, "system %d: bad bond arrays", s);
         const int bond_base = (int)bond_k.size();
+        std::vector<std::vector<std::pair<int, double>>> hyd(N); // SHAKE: hydrogens per heavy atom
         for (int b = 0; b < d.n_bonds; ++b) {
             int i = d.bonds[2 * b], j = d.bonds[2 * b + 1];
             if (i < 0 || j < 0 || i >= N || j >= N || i == j)
@@ -941,9 +956,35 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
             nb[j].push_back(i);
             bond_ij.push_back(i);
             bond_ij.push_back(j);
-            bond_k.push_back(d.bond_k[b]);
+            const bool hi = d.mass[i] < 2.0, hj = d.mass[j] < 2.0;
+            const bool con = p->shake && (hi || hj);
+            if (con) {
+                if (hi && hj)
+                    return fail(nullptr, CPH_E_INVALID, "system %d: bond %d joins two hydrogens (cannot be constrained)", s, b);
+                if (!(d.bond_r0[b] > 0))
+                    return fail(nullptr, CPH_E_INVALID, "system %d: constrained bond %d needs r0 > 0", s, b);
+                hyd[hi ? j : i].push_back({hi ? i : j, d.bond_r0[b]});
+            }
+            bond_k.push_back(con ? 0.0 : d.bond_k[b]); // constrained: no harmonic term
             bond_r0.push_back(d.bond_r0[b]);
         }
+        // clusters must not share atoms (one thread owns each): a hydrogen may be
+        // constrained to one heavy atom only
+        std::vector<char> owned(N, 0);
+        for (int a = 0; a < N; ++a) {
+            if (hyd[a].empty()) continue;
+            if (hyd[a].size() > 8)
+                return fail(nullptr, CPH_E_INVALID, "system %d: atom %d carries more than 8 constrained hydrogens", s, a);
+            shk_heavy.push_back(a);
+            for (auto& hd : hyd[a]) {
+                if (owned[hd.first]++)
+                    return fail(nullptr, CPH_E_INVALID, "system %d: hydrogen %d is bonded to two heavy atoms", s, hd.first);
+                shk_h.push_back(hd.first);
+                shk_d.push_back(hd.second);
+            }
+            shk_off.push_back((int)shk_h.size());
+        }
+        shk_sys_off.push_back((int)shk_heavy.size());
         std::vector<std::set<int>> ex(N);
         for (int i = 0; i < N; ++i)
             for (int j : nb[i]) {
@@ -1245,6 +1286,27 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     }
     TRY(alloc0(E, 1, &d)); V.ex_n = d;
     TRY(alloc0(E, std::max<size_t>(1, (size_t)w_site_off[W] * CPH_MAX_STATES), &dl)); V.occ = dl;
+    if (p->shake) {
+        std::vector<int> iw, ic;
+        E->h_shk_w_off.assign(1, 0);
+        for (int w = 0; w < W; ++w) {
+            const int sy = E->h_w_sys[w];
+            for (int c = shk_sys_off[sy]; c < shk_sys_off[sy + 1]; ++c) {
+                iw.push_back(w);
+                ic.push_back(c);
+            }
+            E->h_shk_w_off.push_back((int)iw.size());
+        }
+        TRY(upload(E, shk_heavy, &d)); V.shk_heavy = d;
+        TRY(upload(E, shk_off, &d)); V.shk_off = d;
+        TRY(upload(E, shk_h, &d)); V.shk_h = d;
+        TRY(upload(E, shk_d, &dd)); V.shk_d = dd;
+        TRY(upload(E, iw, &d)); V.shk_item_w = d;
+        TRY(upload(E, ic, &d)); V.shk_item_c = d;
+        TRY(alloc0(E, 3 * (size_t)total, &dd)); V.xprev = dd;
+        V.shake_tol = p->shake_tol;
+        E->n_shk = (int)iw.size();
+    }
     TRY(alloc0(E, (size_t)W * W, &dl)); V.visits = dl;
     TRY(alloc0(E, 1, &dl)); V.n_obs = dl;
     std::vector<double> gE(grid->E, grid->E + grid->nE), gpH(grid->pH, grid->pH + grid->npH),
@@ -1772,7 +1834,9 @@ int cph_status(cph_engine* e, void* stream) {
     int st = 0;
     TRY(copy_out(e, &st, e->V.status, sizeof(int), stream));
     if (st)
-        return fail(e, CPH_E_NONFINITE, "non-finite value produced (flags %d: 1 force, 2 position, 4 pair sum)", st);
+        return fail(e, CPH_E_NONFINITE,
+                    "non-finite value produced or SHAKE unsettled (flags %d: 1 force, 2 position, 4 pair sum, "
+                    "8 SHAKE did not converge)", st);
     return CPH_OK;
 }
 

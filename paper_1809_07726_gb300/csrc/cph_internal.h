@@ -80,6 +80,12 @@ struct View {
     // kernels apply to pair sums (tau without salt; 1 with salt, whose pair
     // kernels carry tau(f) per pair)
     double kappa, inv_eps_out, tau_pair;
+    // SHAKE: clusters (one heavy atom and its hydrogens) per system, work
+    // items (walker, cluster), positions before the Langevin step
+    const int *shk_heavy, *shk_off, *shk_h, *shk_item_w, *shk_item_c;
+    const double* shk_d;
+    double* xprev; // null when SHAKE is off
+    double shake_tol;
     float rfar2; // pairs with r^2 >= rfar2 are in the series regime in both directions
     // FP32 pair-kernel operands, staged once per step by one thread per atom
     float4* xs;          // (x, y, z, 0) relative to the walker's first atom

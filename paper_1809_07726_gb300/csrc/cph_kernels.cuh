@@ -567,11 +567,74 @@ __global__ void k_langevin(View V, int s_off, int a0, int n) {
     for (int c = 0; c < 3; ++c) {
         const double vn = (c1 * (V.v[3 * a + c] * vs) + V.dt * kAccel * V.F[3 * a + c] / m + sd * (double)z[c]) * c2;
         V.v[3 * a + c] = vn;
+        if (V.xprev) V.xprev[3 * a + c] = V.x[3 * a + c]; // SHAKE's reference bond vectors
         const double xn = V.x[3 * a + c] + V.dt * vn;
         V.x[3 * a + c] = xn;
         ok = ok && isfinite(xn);
     }
     if (!ok) atomicOr(V.status, 2);
+}
+
+// SHAKE (Ryckaert, Ciccotti & Berendsen 1977) after the leapfrog step, one
+// thread per (walker, cluster of one heavy atom and its hydrogens): each
+// constraint in turn moves its two atoms along the bond vector before the
+// step, in inverse proportion to their masses, until none of the cluster's
+// constraints moves (|d0^2 - d^2| <= 2 tol d0^2); velocities take the
+// displacement / dt.  The sweeps are bounded; a cluster that does not settle
+// raises status flag 8.
+constexpr int kShakeMaxH = 8, kShakeMaxIter = 1000;
+
+__global__ void k_shake(View V, int i0, int n) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int it = i0 + l;
+    const int w = V.shk_item_w[it], c = V.shk_item_c[it];
+    const int A = V.w_off[w], P = V.sys_poff[V.w_sys[w]];
+    const int h0 = V.shk_off[c], nh = V.shk_off[c + 1] - h0;
+    int at[kShakeMaxH + 1];
+    double xo[kShakeMaxH + 1][3], xn[kShakeMaxH + 1][3], x0[kShakeMaxH + 1][3], im[kShakeMaxH + 1];
+    at[0] = V.shk_heavy[c];
+    for (int k = 0; k < nh; ++k) at[k + 1] = V.shk_h[h0 + k];
+    for (int k = 0; k <= nh; ++k) {
+        const int a = A + at[k];
+        im[k] = 1.0 / V.mass[P + at[k]];
+        for (int d = 0; d < 3; ++d) {
+            xo[k][d] = V.xprev[3 * a + d];
+            xn[k][d] = x0[k][d] = V.x[3 * a + d];
+        }
+    }
+    const double tol2 = 2.0 * V.shake_tol;
+    bool done = false;
+    for (int iter = 0; iter < kShakeMaxIter && !done; ++iter) {
+        done = true;
+        for (int k = 1; k <= nh; ++k) {
+            const double d0 = V.shk_d[h0 + k - 1];
+            double rij[3], rold[3], r2 = 0.0, dot = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                rij[d] = xn[0][d] - xn[k][d];
+                rold[d] = xo[0][d] - xo[k][d];
+                r2 += rij[d] * rij[d];
+                dot += rold[d] * rij[d];
+            }
+            const double diff = d0 * d0 - r2;
+            if (fabs(diff) > tol2 * d0 * d0) {
+                done = false;
+                const double g = diff / (2.0 * dot * (im[0] + im[k]));
+                for (int d = 0; d < 3; ++d) {
+                    xn[0][d] += g * rold[d] * im[0];
+                    xn[k][d] -= g * rold[d] * im[k];
+                }
+            }
+        }
+    }
+    if (!done) atomicOr(V.status, 8);
+    for (int k = 0; k <= nh; ++k) {
+        const int a = A + at[k];
+        for (int d = 0; d < 3; ++d) {
+            V.x[3 * a + d] = xn[k][d];
+            V.v[3 * a + d] += (xn[k][d] - x0[k][d]) / V.dt;
+        }
+    }
 }
 
 // velocities *= vscale[walker] (a stand-alone T exchange)
