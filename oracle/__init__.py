@@ -65,7 +65,7 @@ def build(force: bool = False) -> str:
 class OGB(C.Structure):
     _fields_ = [("eps_in", C.c_double), ("eps_out", C.c_double), ("offset", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("kappa", C.c_double)]
+                ("kappa", C.c_double), ("sa_gamma", C.c_double), ("sa_probe", C.c_double)]
 
 
 class OSYS(C.Structure):
@@ -111,18 +111,22 @@ class GBParams:
     """OBC model I ("igb=2") values: offset 0.09 A, (alpha, beta, gamma) =
     (0.8, 0.0, 2.909125); eps_in = 1, eps_out = 78.5; no salt (kappa = 0).
     With kappa > 0 every GB term -k q_i q_j tau / f takes tau(f) = 1/eps_in -
-    exp(-kappa f)/eps_out (Debye-Hueckel screening of the reaction field)."""
+    exp(-kappa f)/eps_out (Debye-Hueckel screening of the reaction field).
+    With sa_gamma > 0 the GB term also holds the nonpolar surface energy in the
+    ACE approximation, sum_i 4 pi sa_gamma (rho_i + sa_probe)^2 (rho_i/R_i)^6."""
     eps_in: float = 1.0
     eps_out: float = 78.5
     offset: float = 0.09
     alpha: float = 0.8
     beta: float = 0.0
     gamma: float = 2.909125
-    kappa: float = 0.0   # salt screening (Debye-Hueckel), 1/A; 0 = no salt
+    kappa: float = 0.0     # salt screening (Debye-Hueckel), 1/A; 0 = no salt
+    sa_gamma: float = 0.0  # nonpolar surface term (ACE), kcal/mol/A^2; 0 = off
+    sa_probe: float = 1.4  # solvent probe radius of the surface term, A
 
     def c(self) -> OGB:
         return OGB(self.eps_in, self.eps_out, self.offset, self.alpha, self.beta, self.gamma,
-                   self.kappa)
+                   self.kappa, self.sa_gamma, self.sa_probe)
 
 
 def exclusion_matrix(n: int, bonds: np.ndarray, extra=None) -> np.ndarray:

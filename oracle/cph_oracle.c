@@ -34,7 +34,17 @@
 typedef struct {
     double eps_in, eps_out, offset, alpha, beta, gamma;
     double kappa; /* Debye-Hueckel screening length inverse, 1/A (0: no salt) */
+    double sa_gamma, sa_probe; /* nonpolar surface term (ACE), kcal/mol/A^2 and A (0: off) */
 } ogb;
+
+/* Nonpolar surface term in the ACE approximation (Schaefer & Karplus 1996):
+ * E_SA,i = 4 pi gamma (rho_i + r_probe)^2 (rho_i / R_i)^6, which depends on the
+ * Born radius R_i: dE_SA,i/dR_i = -6 E_SA,i / R_i. */
+static double sa_energy(const ogb *g, double rho, double R) {
+    if (g->sa_gamma == 0.0) return 0.0;
+    const double a = rho + g->sa_probe, t = rho / R;
+    return 4.0 * 3.14159265358979323846 * g->sa_gamma * a * a * t * t * t * t * t * t;
+}
 
 typedef struct {
     int n;
@@ -201,6 +211,9 @@ void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
     for (int i = 0; i < n; i++) {
         egb += -0.5 * O_KCOUL * gb_tauf(g, R[i]) * q[i] * q[i] / R[i];
         dEdR[i] += 0.5 * O_KCOUL * gb_taud(g, R[i]) * q[i] * q[i] / (R[i] * R[i]);
+        const double esa = sa_energy(g, S->rho[i], R[i]); /* reported with E_GB */
+        egb += esa;
+        dEdR[i] += -6.0 * esa / R[i];
     }
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {
@@ -323,6 +336,11 @@ void o_gb_grad(int n, const double *x, const double *q, const double *rho,
         e += -0.5 * O_KCOUL * ts * q[i] * q[i] / R[i];
         gq[i] += -O_KCOUL * ts * q[i] / R[i];
         dEdR[i] += 0.5 * O_KCOUL * gb_taud(g, R[i]) * q[i] * q[i] / (R[i] * R[i]);
+        const double esa = sa_energy(g, rho[i], R[i]);
+        e += esa;
+        dEdR[i] += -6.0 * esa / R[i];
+        /* explicit rho dependence of E_SA at fixed R */
+        if (esa != 0.0) gr[i] += esa * (2.0 / (rho[i] + g->sa_probe) + 6.0 / rho[i]);
     }
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {

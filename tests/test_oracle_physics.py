@@ -326,3 +326,45 @@ def test_salt_forces_and_gradient_match_central_differences(small_chain):
         fd = (oracle.gb_grad(x, s.q, rp, s.screen, gb)[0]
               - oracle.gb_grad(x, s.q, rm, s.screen, gb)[0]) / (2 * h)
         assert dr[i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dr).max())
+
+
+# ---------------------------------------------------------------- nonpolar surface term
+
+def test_sa_term_isolated_atom():
+    """ACE surface term of a lone atom (psi = 0, R = rho - offset):
+    4 pi gamma (rho + probe)^2 (rho / R)^6 on top of the Born energy."""
+    gb = GBParams(sa_gamma=0.005, sa_probe=1.4)
+    q, rho = 0.5, 1.8
+    s, o = _one_system(1, [[0.0, 0.0, 0.0]], [q], [rho])
+    terms = oracle.energy(o, s.x, s.q, gb)[0]
+    R = rho - gb.offset
+    born = -0.5 * KCOUL * (1 / gb.eps_in - 1 / gb.eps_out) * q * q / R
+    sa = 4 * math.pi * 0.005 * (rho + 1.4) ** 2 * (rho / R) ** 6
+    assert terms[0] == pytest.approx(born + sa, rel=1e-14)
+
+
+def test_sa_forces_and_gradient_match_central_differences(small_chain):
+    s, o, x = small_chain
+    gb = GBParams(sa_gamma=0.007, sa_probe=1.4)
+    terms, F, _, _ = oracle.energy(o, x, s.q, gb)
+    E, dx, dq, dr = oracle.gb_grad(x, s.q, s.rho, s.screen, gb)
+    assert E == pytest.approx(terms[0], rel=1e-13)
+    h = 1e-5
+    rng = np.random.default_rng(8)
+    for i in rng.choice(s.n, 6, replace=False):
+        c = int(rng.integers(3))
+        xp, xm = x.copy(), x.copy()
+        xp[i, c] += h
+        xm[i, c] -= h
+        fd = -(oracle.energy(o, xp, s.q, gb, forces=False)[0][5]
+               - oracle.energy(o, xm, s.q, gb, forces=False)[0][5]) / (2 * h)
+        assert F[i, c] == pytest.approx(fd, rel=2e-6, abs=2e-6 * np.abs(F).max())
+        fdx = (oracle.gb_grad(xp, s.q, s.rho, s.screen, gb)[0]
+               - oracle.gb_grad(xm, s.q, s.rho, s.screen, gb)[0]) / (2 * h)
+        assert dx[i, c] == pytest.approx(fdx, rel=1e-6, abs=1e-7 * np.abs(dx).max())
+        rp, rm = s.rho.copy(), s.rho.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (oracle.gb_grad(x, s.q, rp, s.screen, gb)[0]
+              - oracle.gb_grad(x, s.q, rm, s.screen, gb)[0]) / (2 * h)
+        assert dr[i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dr).max())
