@@ -141,12 +141,17 @@ typedef struct cph_grid_desc {
  * tau(f) = 1/eps_in - exp(-kappa f)/eps_out (f = R for the self terms); the
  * paper states no salt, and 0 (the default) gives the constant
  * 1/eps_in - 1/eps_out.  The differentiable energy (cph_gb_energy*) takes
- * kappa = 0 only. */
+ * kappa = 0 only; it includes the surface term. */
 typedef struct cph_gb_params {
     double eps_in, eps_out;
     double offset;                  /* rho_tilde = rho - offset */
     double alpha, beta, gamma;      /* tanh(alpha psi - beta psi^2 + gamma psi^3) */
     double kappa;                   /* salt screening, 1/A (0 = none) */
+    /* nonpolar surface term in the ACE approximation (Schaefer & Karplus),
+     * reported with E_GB: sum_i 4 pi sa_gamma (rho_i + sa_probe)^2
+     * (rho_i / R_i)^6; sa_gamma in kcal/mol/A^2 (0 = off, e.g. 0.005),
+     * sa_probe in A (e.g. 1.4) */
+    double sa_gamma, sa_probe;
 } cph_gb_params;
 
 typedef struct cph_run_params {

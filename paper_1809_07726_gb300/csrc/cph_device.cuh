@@ -97,6 +97,15 @@ __host__ __device__ inline double salt_taud(double f, double iei, double ieo, do
     return iei - es - kappa * f * es;
 }
 
+// ------------------------------------------------- nonpolar surface term
+// ACE approximation (Schaefer & Karplus 1996): E_SA = 4 pi gamma (rho + probe)^2
+// (rho / R)^6 per atom; dE_SA/dR = -6 E_SA / R.  gamma = 0: off.
+__host__ __device__ inline double sa_ace(double gamma, double probe, double rho, double R) {
+    if (gamma == 0.0) return 0.0;
+    const double a = rho + probe, t = rho / R, t3 = t * t * t;
+    return 4.0 * 3.14159265358979323846 * gamma * a * a * t3 * t3;
+}
+
 // --------------------------------------------------------- fixed point
 __device__ inline long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
 __device__ inline long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }

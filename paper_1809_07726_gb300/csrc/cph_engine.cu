@@ -882,6 +882,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     if (!sys || n_sys < 1 || !grid || !p) return fail(nullptr, CPH_E_INVALID, "missing descriptor");
     if (p->precision != CPH_PREC_FP32 && p->precision != CPH_PREC_FP64)
         return fail(nullptr, CPH_E_INVALID, "unknown precision %d", p->precision);
+    if (!std::isfinite(p->gb.sa_gamma) || !(p->gb.sa_probe >= 0) || !std::isfinite(p->gb.sa_probe))
+        return fail(nullptr, CPH_E_INVALID, "surface term: sa_gamma must be finite, sa_probe finite and >= 0");
     if (!(p->gb.kappa >= 0) || !std::isfinite(p->gb.kappa))
         return fail(nullptr, CPH_E_INVALID, "salt screening kappa must be finite and >= 0");
     if (!(p->dt > 0) || !(p->gamma_ln >= 0) || !(p->gb.eps_in > 0) || !(p->gb.eps_out > 0))
@@ -1323,6 +1325,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.kappa = p->gb.kappa;
     V.inv_eps_out = 1.0 / p->gb.eps_out;
     V.tau_pair = p->gb.kappa > 0 ? 1.0 : V.tau;
+    V.sa_gamma = p->gb.sa_gamma;
+    V.sa_probe = p->gb.sa_probe;
     V.inv_eps_in = 1.0 / p->gb.eps_in;
     V.sqrt_k = std::sqrt(kCoulomb);
     V.alpha = p->gb.alpha;

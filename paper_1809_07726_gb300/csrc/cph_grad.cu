@@ -87,6 +87,8 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     if (((uintptr_t)ws & 255u) != 0) return gfail(CPH_E_INVALID, "cph_gb_energy: workspace must be 256-byte aligned");
     if (wsb < ws_bytes(n_rep, n)) return gfail(CPH_E_INVALID, "cph_gb_energy: workspace too small");
     if (!(gb->eps_in > 0) || !(gb->eps_out > 0)) return gfail(CPH_E_INVALID, "cph_gb_energy: bad dielectric");
+    if (!std::isfinite(gb->sa_gamma) || !(gb->sa_probe >= 0))
+        return gfail(CPH_E_INVALID, "cph_gb_energy: bad surface-term parameters");
     if (gb->kappa != 0.0)
         return gfail(CPH_E_INVALID, "cph_gb_energy: salt screening (kappa > 0) is not supported here");
     g = SView{};
@@ -105,6 +107,8 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     g.beta = gb->beta;
     g.gamma = gb->gamma;
     g.offset = gb->offset;
+    g.sa_gamma = gb->sa_gamma;
+    g.sa_probe = gb->sa_probe;
     ws_carve_sym(g, ws);
     return CPH_OK;
 }

@@ -33,6 +33,7 @@ struct SView {
     int n_rep, n, n_itile, n_jtile, n_chunk;
     const float *x, *q, *rho, *screen;
     double tau, sqrt_k, alpha, beta, gamma, offset;
+    double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
     // per replica-atom (index r * n + a); int64 slots alias double slots that
     // are not live at the same time (see ws_carve_sym)
     double *psi, *R, *dEdR, *c, *dq, *gpsi;
@@ -431,9 +432,11 @@ __global__ void k_gfin_c(SView g) {
     const size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= (size_t)g.n_rep * g.n) return;
     const double q = (double)g.q[a] * g.sqrt_k, R = g.R[a];
-    atomicAdd((unsigned long long*)&g.eacc[a / g.n], (unsigned long long)__double2ll_rn(-0.5 * g.tau * q * q / R * kScaleE));
+    const double esa = sa_ace(g.sa_gamma, g.sa_probe, (double)g.rho[a], R);
+    atomicAdd((unsigned long long*)&g.eacc[a / g.n],
+              (unsigned long long)__double2ll_rn((-0.5 * g.tau * q * q / R + esa) * kScaleE));
     if (!BACKWARD) return;
-    const double dEdR = 0.5 * g.tau * ((double)g.dRfix[a] / kScaleE + q * q / (R * R));
+    const double dEdR = 0.5 * g.tau * ((double)g.dRfix[a] / kScaleE + q * q / (R * R)) - 6.0 * esa / R;
     const double rt = (double)g.rho[a] - g.offset;
     const double gpsi = dEdR * g.gpsi[a]; // gpsi slot held dR/dpsi
     const double dq = -g.tau * g.sqrt_k * ((double)g.dqfix[a] / kScaleE + q / R);
@@ -705,9 +708,11 @@ __global__ void k_gfin_out(SView g) {
     const double up = g.dE[r];
     const double rho = g.rho[a], rt = rho - g.offset, R = g.R[a], psi = g.psi[a];
     const double th = tanh(psi * (g.alpha + psi * (-g.beta + psi * g.gamma)));
+    const double esa = sa_ace(g.sa_gamma, g.sa_probe, rho, R); // explicit rho dependence at fixed R
     const double dr = g.dEdR[a] * R * R * (1.0 / (rt * rt) - th / (rho * rho)) + g.gpsi[a] * psi / rt +
                       g.c[a] * ((double)g.artfix[a] / kScaleE) +
-                      (double)g.screen[a % g.n] * ((double)g.asfix[a] / kScaleE);
+                      (double)g.screen[a % g.n] * ((double)g.asfix[a] / kScaleE) +
+                      (esa != 0.0 ? esa * (2.0 / (rho + g.sa_probe) + 6.0 / rho) : 0.0);
     g.dx[3 * a] = (float)(up * ((double)g.gfix[3 * a] / kScaleE));
     g.dx[3 * a + 1] = (float)(up * ((double)g.gfix[3 * a + 1] / kScaleE));
     g.dx[3 * a + 2] = (float)(up * ((double)g.gfix[3 * a + 2] / kScaleE));

@@ -80,6 +80,7 @@ struct View {
     // kernels apply to pair sums (tau without salt; 1 with salt, whose pair
     // kernels carry tau(f) per pair)
     double kappa, inv_eps_out, tau_pair;
+    double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
     // SHAKE: clusters (one heavy atom and its hydrogens) per system, work
     // items (walker, cluster), positions before the Langevin step
     const int *shk_heavy, *shk_off, *shk_h, *shk_item_w, *shk_item_c;

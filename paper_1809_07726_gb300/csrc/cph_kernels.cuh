@@ -324,7 +324,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         const double q = V.q[A + i] * V.sqrt_k;
         const double R = V.R[A + i];
         const double dEdR = 0.5 * (V.tau_pair * Pr::value(adr, kScaleE)
-                                   + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R));
+                                   + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R))
+                          - 6.0 * sa_ace(V.sa_gamma, V.sa_probe, V.rho[P + i], R) / R;
         V.c[A + i] = dEdR * V.dRdpsi[A + i] * 0.5 * V.rt[P + i];
         V.Fd[3 * (A + i)] = Pr::value(fx, kScaleE);
         V.Fd[3 * (A + i) + 1] = Pr::value(fy, kScaleE);
@@ -335,8 +336,9 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         if (vi) {
             const double q = V.q[A + i] * V.sqrt_k;
             const double R = V.R[A + i];
-            e0 = __double2ll_rn(-0.5 * (V.tau_pair * Pr::value(egb, kScaleE)
-                                        + salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / R) * kScaleE);
+            e0 = __double2ll_rn((-0.5 * (V.tau_pair * Pr::value(egb, kScaleE)
+                                         + salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / R)
+                                 + sa_ace(V.sa_gamma, V.sa_probe, V.rho[P + i], R)) * kScaleE);
             e1 = __double2ll_rn(0.5 * V.inv_eps_in * Pr::value(ec, kScaleE) * kScaleE);
             e2 = __double2ll_rn(2.0 * Pr::value(elj, kScaleE) * kScaleE);
         }

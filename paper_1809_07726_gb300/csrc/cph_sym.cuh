@@ -395,15 +395,17 @@ __global__ void k_fin_c(View V, int a0, int n) {
     const int w = V.a_walker[a];
     const int P = V.sys_poff[V.w_sys[w]] + (a - V.w_off[w]);
     const double q = V.q[a] * V.sqrt_k, R = V.R[a];
+    const double esa = sa_ace(V.sa_gamma, V.sa_probe, V.rho[P], R);
     const double dEdR = 0.5 * (V.tau_pair * ((double)V.dRfix[a] / kScaleE)
-                               + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R));
+                               + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R))
+                      - 6.0 * esa / R;
     const double c = dEdR * V.dRdpsi[a] * 0.5 * V.rt[P];
     V.c[a] = c;
     V.c32[a] = (float)c;
     if (ENERGY)
         atomicAdd((unsigned long long*)&V.eacc[w * kEAcc + 0],
-                  (unsigned long long)__double2ll_rn(-0.5 * salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa)
-                                                     * q * q / R * kScaleE));
+                  (unsigned long long)__double2ll_rn((-0.5 * salt_tau(R, V.inv_eps_in, V.inv_eps_out, V.kappa)
+                                                      * q * q / R + esa) * kScaleE));
 }
 
 // ========================================================= chain rule

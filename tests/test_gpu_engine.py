@@ -327,12 +327,15 @@ def test_checkpoint_restart_continues_bitwise(ragged_systems):
     assert err.value.code == cphremd.E_INVALID
 
 
-# OBC model II ("igb=5"), model I with other dielectric constants, and model I
-# with salt screening: the GB variants are parameter sets of the same kernels
+# OBC model II ("igb=5"), model I with other dielectric constants, model I with
+# salt screening, and model II with salt and the surface term: the GB variants
+# are parameter sets of the same kernels
 GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85, kappa=0.0),
                dict(eps_in=2.0, eps_out=80.0, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125, kappa=0.0),
                dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125,
-                    kappa=0.1)]  # Debye-Hueckel salt screening
+                    kappa=0.1),  # Debye-Hueckel salt screening
+               dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85,
+                    kappa=0.05, sa_gamma=0.005, sa_probe=1.4)]  # + ACE surface term
 
 
 @pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
@@ -341,7 +344,7 @@ GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, 
 def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr):
     grid = _grid_for(ragged_systems)
     gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"],
-                          v["kappa"])
+                          v["kappa"], v.get("sa_gamma", 0.0), v.get("sa_probe", 1.4))
     eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec, gb=gb)
     eng.evaluate()
     og = oracle.GBParams(**v)

@@ -113,3 +113,24 @@ def test_salt_is_refused_by_the_differentiable_energy():
     with pytest.raises(cphremd.CphError) as e:
         cphremd.gb_energy(xt, qt, rt, st, gb=gb)
     assert e.value.code == cphremd.E_INVALID
+
+
+def test_surface_term_energy_and_gradient_match_oracle():
+    """The ACE surface term through the differentiable energy (energy, and the
+    gradient including the explicit rho dependence)."""
+    import torch
+    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, 0.0, 0.006, 1.4)
+    s, x, q, rho = _batch(2, 257, 31)
+    xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
+    st = _torch(s.screen, torch.float32)
+    E = cphremd.gb_energy(xt, qt, rt, st, gb=gb).cpu().numpy()
+    dx, dq, dr = (t.cpu().numpy().astype(np.float64) for t in cphremd.gb_energy_backward(
+        xt, qt, rt, st, torch.ones(2, dtype=torch.float64, device="cuda:0"), gb=gb))
+    for r in range(2):
+        xr, qr, rr = (a[r].astype(np.float32).astype(np.float64) for a in (x, q, rho))
+        Eo, gx, gq, gr = oracle.gb_grad(xr, qr, rr, s.screen.astype(np.float32).astype(np.float64),
+                                        oracle.GBParams(sa_gamma=0.006, sa_probe=1.4))
+        assert abs(E[r] - Eo) <= 1e-6 * abs(Eo), (E[r], Eo)
+        assert _rel_rms(dx[r], gx) <= 1e-5
+        assert _rel_rms(dq[r], gq) <= 1e-5
+        assert _rel_rms(dr[r], gr) <= 1e-5
