@@ -65,7 +65,8 @@ def build(force: bool = False) -> str:
 class OGB(C.Structure):
     _fields_ = [("eps_in", C.c_double), ("eps_out", C.c_double), ("offset", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("kappa", C.c_double), ("sa_gamma", C.c_double), ("sa_probe", C.c_double)]
+                ("kappa", C.c_double), ("sa_gamma", C.c_double), ("sa_probe", C.c_double),
+                ("rgbmax", C.c_double)]
 
 
 class OSYS(C.Structure):
@@ -86,6 +87,9 @@ def lib():
         d, vp, i, u32, u64 = C.c_double, C.c_void_p, C.c_int, C.c_uint32, C.c_uint64
         L.o_hct.restype = d
         L.o_hct.argtypes = [d, d, d]
+        for f in (L.o_hct_rc, L.o_hct_dr_rc, L.o_hct_drt_rc, L.o_hct_ds_rc):
+            f.restype = d
+            f.argtypes = [d, d, d, d]
         for f in (L.o_hct_dr, L.o_hct_drt, L.o_hct_ds):
             f.restype = d
             f.argtypes = [d, d, d]
@@ -123,10 +127,11 @@ class GBParams:
     kappa: float = 0.0     # salt screening (Debye-Hueckel), 1/A; 0 = no salt
     sa_gamma: float = 0.0  # nonpolar surface term (ACE), kcal/mol/A^2; 0 = off
     sa_probe: float = 1.4  # solvent probe radius of the surface term, A
+    rgbmax: float = 0.0    # Born-radius cutoff, A; 0 = none
 
     def c(self) -> OGB:
         return OGB(self.eps_in, self.eps_out, self.offset, self.alpha, self.beta, self.gamma,
-                   self.kappa, self.sa_gamma, self.sa_probe)
+                   self.kappa, self.sa_gamma, self.sa_probe, self.rgbmax)
 
 
 def exclusion_matrix(n: int, bonds: np.ndarray, extra=None) -> np.ndarray:
@@ -189,20 +194,22 @@ class OSystem:
 
 # ------------------------------------------------------------ pair physics
 
-def hct(r, rt, s):
-    return lib().o_hct(r, rt, s)
+def hct(r, rt, s, rc=0.0):
+    """Descreening integral H(r, rt, s); rc > 0 cuts it at that radius
+    (Born-radius cutoff, AMBER's rgbmax)."""
+    return lib().o_hct_rc(r, rt, s, rc)
 
 
-def hct_dr(r, rt, s):
-    return lib().o_hct_dr(r, rt, s)
+def hct_dr(r, rt, s, rc=0.0):
+    return lib().o_hct_dr_rc(r, rt, s, rc)
 
 
-def hct_drt(r, rt, s):
-    return lib().o_hct_drt(r, rt, s)
+def hct_drt(r, rt, s, rc=0.0):
+    return lib().o_hct_drt_rc(r, rt, s, rc)
 
 
-def hct_ds(r, rt, s):
-    return lib().o_hct_ds(r, rt, s)
+def hct_ds(r, rt, s, rc=0.0):
+    return lib().o_hct_ds_rc(r, rt, s, rc)
 
 
 def born(x, rho, screen, gb: GBParams = GBParams()):

@@ -35,6 +35,7 @@ typedef struct {
     double eps_in, eps_out, offset, alpha, beta, gamma;
     double kappa; /* Debye-Hueckel screening length inverse, 1/A (0: no salt) */
     double sa_gamma, sa_probe; /* nonpolar surface term (ACE), kcal/mol/A^2 and A (0: off) */
+    double rgbmax;             /* Born-radius cutoff, A (0: none) */
 } ogb;
 
 /* Nonpolar surface term in the ACE approximation (Schaefer & Karplus 1996):
@@ -67,20 +68,20 @@ static double dist(const double *x, int i, int j, double d[3]) {
 
 /* ------------------------------------------------------------------ HCT */
 
-/* H(r, rt, s): zero when the ball rt swallows sphere s; otherwise the closed
- * form with L = max(rt, |r - s|), U = r + s, plus 2(1/rt - 1/L) when the ball
- * rt lies wholly inside sphere s. */
-double o_hct(double r, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s;
-    double L = fabs(r - s);
-    if (rt > L) L = rt;
-    double h = 1.0 / L - 1.0 / U
-             + 0.25 * r * (1.0 / (U * U) - 1.0 / (L * L))
-             + 0.5 / r * log(L / U)
-             + 0.25 * s * s / r * (1.0 / (L * L) - 1.0 / (U * U));
-    if (rt < s - r) h += 2.0 * (1.0 / rt - 1.0 / L);
-    return h;
+/* H(r, rt, s) is the descreening integral 2 int_L^U f(t) / t^2 dt over the
+ * shells t around an atom of offset radius rt, f(t) the fraction of shell t
+ * inside a sphere of radius s at distance r: L = max(rt, |r - s|), U = r + s,
+ * closed form below, plus 2(1/rt - 1/L) when the ball rt lies wholly inside
+ * sphere s (those shells are fully covered); zero when the ball swallows the
+ * sphere.  With a Born-radius cutoff rc > 0 (AMBER's rgbmax) only shells
+ * t <= rc count: U = min(r + s, rc) and the covered shells end at rc.  The
+ * derivatives are total ones: L and U move with r and s (the integrand
+ * vanishes on those moving boundaries, but not at a fixed U = rc). */
+static double hct_closed(double r, double s, double L, double U) {
+    return 1.0 / L - 1.0 / U
+         + 0.25 * r * (1.0 / (U * U) - 1.0 / (L * L))
+         + 0.5 / r * log(L / U)
+         + 0.25 * s * s / r * (1.0 / (L * L) - 1.0 / (U * U));
 }
 
 /* Partial derivatives of the closed form with respect to its explicit r, s,
@@ -102,44 +103,94 @@ static int hct_L(double r, double rt, double s, double *L) {
     return 0;
 }
 
-/* dH/dr, total (L and U follow r). */
-double o_hct_dr(double r, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s, L;
+/* U and whether it moves with r and s (1) or sits at the cutoff (0). */
+static double hct_U(double r, double s, double rc, int *moving) {
+    double U = r + s;
+    if (rc > 0.0 && U > rc) { *moving = 0; return rc; }
+    *moving = 1;
+    return U;
+}
+
+/* End of the fully covered shells (ball inside sphere s), capped at rc. */
+static double hct_top(double r, double s, double rc, int *capped) {
+    double top = s - r;
+    *capped = 0;
+    if (rc > 0.0 && rc < top) { top = rc; *capped = 1; }
+    return top;
+}
+
+double o_hct_rc(double r, double rt, double s, double rc) {
+    int mv, cap;
+    double U = hct_U(r, s, rc, &mv), L;
+    hct_L(r, rt, s, &L);
+    double h = (L < U) ? hct_closed(r, s, L, U) : 0.0;
+    if (rt < s - r) {
+        double top = hct_top(r, s, rc, &cap);
+        if (rt < top) h += 2.0 * (1.0 / rt - 1.0 / top);
+    }
+    return h;
+}
+
+/* dH/dr, total. */
+double o_hct_dr_rc(double r, double rt, double s, double rc) {
+    int mv, cap;
+    double U = hct_U(r, s, rc, &mv), L;
     int Lrt = hct_L(r, rt, s, &L);
-    double dL = Lrt ? 0.0 : (r > s ? 1.0 : -1.0);
-    double hr, hs, hL, hU;
-    hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
-    double d = hr + hL * dL + hU * 1.0;
-    if (rt < s - r) d += 2.0 / (L * L) * dL;
+    double d = 0.0;
+    if (L < U) {
+        double dL = Lrt ? 0.0 : (r > s ? 1.0 : -1.0);
+        double hr, hs, hL, hU;
+        hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
+        d = hr + hL * dL + hU * (mv ? 1.0 : 0.0);
+    }
+    if (rt < s - r) {
+        double top = hct_top(r, s, rc, &cap);
+        if (rt < top && !cap) d += -2.0 / (top * top); /* d(-2/top)/dr, top = s - r */
+    }
     return d;
 }
 
 /* dH/d(rt), total. */
-double o_hct_drt(double r, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s, L;
+double o_hct_drt_rc(double r, double rt, double s, double rc) {
+    int mv, cap;
+    double U = hct_U(r, s, rc, &mv), L;
     int Lrt = hct_L(r, rt, s, &L);
-    double dL = Lrt ? 1.0 : 0.0;
-    double hr, hs, hL, hU;
-    hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
-    double d = hL * dL;
-    if (rt < s - r) d += -2.0 / (rt * rt) + 2.0 / (L * L) * dL;
+    double d = 0.0;
+    if (L < U && Lrt) {
+        double hr, hs, hL, hU;
+        hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
+        d = hL;
+    }
+    if (rt < s - r) {
+        double top = hct_top(r, s, rc, &cap);
+        if (rt < top) d += -2.0 / (rt * rt);
+    }
     return d;
 }
 
 /* dH/ds, total. */
-double o_hct_ds(double r, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s, L;
+double o_hct_ds_rc(double r, double rt, double s, double rc) {
+    int mv, cap;
+    double U = hct_U(r, s, rc, &mv), L;
     int Lrt = hct_L(r, rt, s, &L);
-    double dL = Lrt ? 0.0 : (s > r ? 1.0 : -1.0);
-    double hr, hs, hL, hU;
-    hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
-    double d = hs + hL * dL + hU * 1.0;
-    if (rt < s - r) d += 2.0 / (L * L) * dL;
+    double d = 0.0;
+    if (L < U) {
+        double dL = Lrt ? 0.0 : (s > r ? 1.0 : -1.0);
+        double hr, hs, hL, hU;
+        hct_partials(r, s, L, U, &hr, &hs, &hL, &hU);
+        d = hs + hL * dL + hU * (mv ? 1.0 : 0.0);
+    }
+    if (rt < s - r) {
+        double top = hct_top(r, s, rc, &cap);
+        if (rt < top && !cap) d += 2.0 / (top * top); /* d(-2/top)/ds, top = s - r */
+    }
     return d;
 }
+
+double o_hct(double r, double rt, double s) { return o_hct_rc(r, rt, s, 0.0); }
+double o_hct_dr(double r, double rt, double s) { return o_hct_dr_rc(r, rt, s, 0.0); }
+double o_hct_drt(double r, double rt, double s) { return o_hct_drt_rc(r, rt, s, 0.0); }
+double o_hct_ds(double r, double rt, double s) { return o_hct_ds_rc(r, rt, s, 0.0); }
 
 /* ----------------------------------------------------------- Born radii */
 
@@ -154,7 +205,7 @@ void o_born(int n, const double *x, const double *rho, const double *screen,
             double d[3];
             double r = dist(x, i, j, d);
             double sj = screen[j] * (rho[j] - g->offset);
-            sum += o_hct(r, rti, sj);
+            sum += o_hct_rc(r, rti, sj, g->rgbmax);
         }
         double p = 0.5 * rti * sum;
         double th = tanh(g->alpha * p - g->beta * p * p + g->gamma * p * p * p);
@@ -258,7 +309,7 @@ void o_energy(const osys *S, const ogb *g, const double *x, const double *q,
             double d[3];
             double r = dist(x, k, j, d);
             double sj = S->screen[j] * (S->rho[j] - g->offset);
-            double gr = ck * o_hct_dr(r, rtk, sj);
+            double gr = ck * o_hct_dr_rc(r, rtk, sj, g->rgbmax);
             for (int c = 0; c < 3; c++) {
                 Fl[3 * k + c] -= gr * d[c] / r;
                 Fl[3 * j + c] += gr * d[c] / r;
@@ -382,13 +433,13 @@ void o_gb_grad(int n, const double *x, const double *q, const double *rho,
             double d[3];
             double r = dist(x, k, j, d);
             double sj = screen[j] * (rho[j] - g->offset);
-            double hdr = o_hct_dr(r, rtk, sj);
+            double hdr = o_hct_dr_rc(r, rtk, sj, g->rgbmax);
             for (int c = 0; c < 3; c++) {
                 gx[3 * k + c] += gpsi * 0.5 * rtk * hdr * d[c] / r;
                 gx[3 * j + c] -= gpsi * 0.5 * rtk * hdr * d[c] / r;
             }
-            gr[k] += gpsi * 0.5 * rtk * o_hct_drt(r, rtk, sj);
-            gr[j] += gpsi * 0.5 * rtk * o_hct_ds(r, rtk, sj) * screen[j];
+            gr[k] += gpsi * 0.5 * rtk * o_hct_drt_rc(r, rtk, sj, g->rgbmax);
+            gr[j] += gpsi * 0.5 * rtk * o_hct_ds_rc(r, rtk, sj, g->rgbmax) * screen[j];
         }
     }
     *E = e;

@@ -13,16 +13,17 @@ from oracle import GBParams, KCOUL
 from paper_1809_07726_gb300 import synth
 
 
-def shell_integral(r, rt, s):
+def shell_integral(r, rt, s, rc=None):
     """H(r, rt, s) from geometry alone: for each shell of radius t >= rt about
     atom i, the fraction of the shell inside sphere j (radius s, centre at
     distance r) is (1 - c0)/2 with c0 = clip((t^2 + r^2 - s^2)/(2 t r), -1, 1);
-    H = 2 * (1/4pi) * int 4 pi t^2 frac / t^4 dt."""
+    H = 2 * (1/4pi) * int 4 pi t^2 frac / t^4 dt, over shells t <= rc when a
+    cutoff rc is given."""
     def f(t):
         c0 = (t * t + r * r - s * s) / (2.0 * t * r)
         c0 = min(1.0, max(-1.0, c0))
         return (1.0 - c0) / (t * t)
-    hi = r + s
+    hi = r + s if rc is None else min(r + s, rc)
     if rt >= hi:
         return 0.0
     pts = [p for p in (abs(r - s), s - r) if rt < p < hi]
@@ -367,4 +368,67 @@ def test_sa_forces_and_gradient_match_central_differences(small_chain):
         rm[i] -= h
         fd = (oracle.gb_grad(x, s.q, rp, s.screen, gb)[0]
               - oracle.gb_grad(x, s.q, rm, s.screen, gb)[0]) / (2 * h)
+        assert dr[i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dr).max())
+
+
+
+# ---------------------------------------------------------------- Born-radius cutoff
+
+CUT_CASES = [
+    # (r, rt, s, rc): sphere straddling the cutoff, wholly beyond it, wholly inside it
+    (9.0, 1.4, 1.5, 10.0),
+    (10.2, 1.4, 1.5, 10.0),
+    (11.6, 1.4, 1.5, 10.0),
+    (6.0, 1.4, 1.2, 10.0),
+    (4.5, 1.2, 1.8, 5.0),
+]
+
+
+@pytest.mark.parametrize("r,rt,s,rc", CUT_CASES)
+def test_hct_cutoff_matches_truncated_shell_quadrature(r, rt, s, rc):
+    h = oracle.hct(r, rt, s, rc)
+    ref = shell_integral(r, rt, s, rc)
+    assert h == pytest.approx(ref, rel=1e-10, abs=1e-14)
+    if r - s >= rc:
+        assert h == 0.0
+    if r + s <= rc:
+        assert h == oracle.hct(r, rt, s)
+
+
+@pytest.mark.parametrize("r,rt,s,rc", CUT_CASES[:2] + CUT_CASES[3:])
+def test_hct_cutoff_derivatives_match_finite_differences(r, rt, s, rc):
+    h = 1e-6
+    H = lambda a, b, c: oracle.hct(a, b, c, rc)
+    assert oracle.hct_dr(r, rt, s, rc) == pytest.approx((H(r + h, rt, s) - H(r - h, rt, s)) / (2 * h),
+                                                        rel=1e-6, abs=1e-10)
+    assert oracle.hct_drt(r, rt, s, rc) == pytest.approx((H(r, rt + h, s) - H(r, rt - h, s)) / (2 * h),
+                                                         rel=1e-6, abs=1e-10)
+    assert oracle.hct_ds(r, rt, s, rc) == pytest.approx((H(r, rt, s + h) - H(r, rt, s - h)) / (2 * h),
+                                                        rel=1e-6, abs=1e-10)
+
+
+def test_cutoff_forces_and_gradient_match_central_differences(small_chain):
+    """A cutoff that cuts: the chain spans ~15 A, rgbmax = 6 A."""
+    s, o, x = small_chain
+    gb = GBParams(rgbmax=6.0)
+    terms, F, R, _ = oracle.energy(o, x, s.q, gb)
+    R0 = oracle.energy(o, x, s.q, GBParams())[2]
+    assert (R < R0).any() and (R <= R0 + 1e-12).all()  # less descreening: no radius grows
+    E, dx, dq, dr = oracle.gb_grad(x, s.q, s.rho, s.screen, gb)
+    assert E == pytest.approx(terms[0], rel=1e-13)
+    hh = 1e-5
+    rng = np.random.default_rng(11)
+    for i in rng.choice(s.n, 6, replace=False):
+        c = int(rng.integers(3))
+        xp, xm = x.copy(), x.copy()
+        xp[i, c] += hh
+        xm[i, c] -= hh
+        fd = -(oracle.energy(o, xp, s.q, gb, forces=False)[0][5]
+               - oracle.energy(o, xm, s.q, gb, forces=False)[0][5]) / (2 * hh)
+        assert F[i, c] == pytest.approx(fd, rel=2e-6, abs=2e-6 * np.abs(F).max())
+        rp, rm = s.rho.copy(), s.rho.copy()
+        rp[i] += hh
+        rm[i] -= hh
+        fd = (oracle.gb_grad(x, s.q, rp, s.screen, gb)[0]
+              - oracle.gb_grad(x, s.q, rm, s.screen, gb)[0]) / (2 * hh)
         assert dr[i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dr).max())
