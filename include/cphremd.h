@@ -152,6 +152,12 @@ typedef struct cph_gb_params {
      * (rho_i / R_i)^6; sa_gamma in kcal/mol/A^2 (0 = off, e.g. 0.005),
      * sa_probe in A (e.g. 1.4) */
     double sa_gamma, sa_probe;
+    /* Born-radius cutoff in A (AMBER's rgbmax; 0 = none): only descreening
+     * shells at distance t <= rgbmax from an atom count in its OBC integral
+     * sum psi, i.e. the HCT integrals run to min(r + s, rgbmax) and
+     * the fully covered shells of a ball inside a sphere end at rgbmax.
+     * Finite and >= 0, else CPH_E_INVALID. */
+    double rgbmax;
 } cph_gb_params;
 
 typedef struct cph_run_params {

@@ -59,7 +59,8 @@ class GridDesc(C.Structure):
 class GBParams(C.Structure):
     _fields_ = [("eps_in", C.c_double), ("eps_out", C.c_double), ("offset", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("kappa", C.c_double), ("sa_gamma", C.c_double), ("sa_probe", C.c_double)]
+                ("kappa", C.c_double), ("sa_gamma", C.c_double), ("sa_probe", C.c_double),
+                ("rgbmax", C.c_double)]
 
 
 class RunParams(C.Structure):
@@ -82,8 +83,8 @@ class ExRecord(C.Structure):
 
 def default_gb() -> GBParams:
     """OBC "igb=2": offset 0.09, (alpha, beta, gamma) = (0.8, 0, 2.909125), eps 1 / 78.5, no salt,
-    no surface term (probe 1.4 A when one is switched on)."""
-    return GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, 0.0, 0.0, 1.4)
+    no surface term (probe 1.4 A when one is switched on), no Born-radius cutoff."""
+    return GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, 0.0, 0.0, 1.4, 0.0)
 
 
 _lib = None

@@ -23,6 +23,7 @@
 //     dH/drt = ((L - r)^2 - s^2)/(2 r L^3) when L = rt, -2/rt^2 when the ball
 //              lies inside sphere s, else 0.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -180,16 +181,25 @@ template <class T> __device__ __forceinline__ T hct_series_ds(T y) { // S
     return p;
 }
 
-__device__ __forceinline__ bool hct_far(float r, float rt, float s) {
-    return (r - s >= rt) && (s <= kHctXmax * r);
+// Born-radius cutoff rc (AMBER's rgbmax; infinity = none): only shells
+// t <= rc descreen, so U = min(r + s, rc), the covered shells of a ball inside
+// sphere s end at min(s - r, rc), and H = 0 once L >= U.  The derivative forms
+// below hold for a moving or a fixed U alike (the integrand vanishes on the
+// moving boundaries), except that the covered-shell term stops moving with r
+// and s once capped.  With the ball inside sphere s (L = s - r) the closed
+// part's dependence on L cancels that of the covered shells, so dH/dr and
+// dH/ds are the closed part's explicit partials alone; once the covered
+// shells are capped at rc the closed part is empty and both vanish.
+__device__ __forceinline__ bool hct_far(float r, float rt, float s, float rc = INFINITY) {
+    return (r - s >= rt) && (s <= kHctXmax * r) && (r + s <= rc);
 }
 
 struct HctClosed {
     float iL, iU, lg;
 };
 
-__device__ __forceinline__ HctClosed hct_closed(float r, float rt, float s) {
-    float U = r + s;
+__device__ __forceinline__ HctClosed hct_closed(float r, float rt, float s, float rc) {
+    float U = fminf(r + s, rc);
     float L = fmaxf(rt, fabsf(r - s));
     float iLU = __fdividef(1.f, L * U);
     HctClosed h;
@@ -199,85 +209,109 @@ __device__ __forceinline__ HctClosed hct_closed(float r, float rt, float s) {
     return h;
 }
 
-__device__ __forceinline__ float hct(float r, float rinv, float rt, float irt, float s) {
-    if (hct_far(r, rt, s)) {
+// whether the closed-form part is empty (L >= U)
+__device__ __forceinline__ bool hct_empty(float r, float rt, float s, float rc) {
+    return fmaxf(rt, fabsf(r - s)) >= fminf(r + s, rc);
+}
+
+__device__ __forceinline__ float hct(float r, float rinv, float rt, float irt, float s, float rc = INFINITY) {
+    if (hct_far(r, rt, s, rc)) {
         float x = s * rinv, y = x * x;
         return x * y * hct_series_h(y) * rinv;
     }
-    if (rt >= r + s) return 0.f;
-    HctClosed c = hct_closed(r, rt, s);
-    float h = (c.iL - c.iU) * fmaf((c.iL + c.iU) * 0.25f * rinv, (s - r) * (s + r), 1.f)
-            + 0.5f * rinv * c.lg;
-    if (rt < s - r) h += 2.f * (irt - c.iL);
+    float h = 0.f;
+    if (!hct_empty(r, rt, s, rc)) {
+        HctClosed c = hct_closed(r, rt, s, rc);
+        h = (c.iL - c.iU) * fmaf((c.iL + c.iU) * 0.25f * rinv, (s - r) * (s + r), 1.f) + 0.5f * rinv * c.lg;
+    }
+    if (rt < s - r) {
+        const float top = fminf(s - r, rc);
+        if (rt < top) h += 2.f * (irt - __fdividef(1.f, top));
+    }
     return h;
 }
 
-__device__ __forceinline__ float hct_dr(float r, float rinv, float rt, float s) {
+__device__ __forceinline__ float hct_dr(float r, float rinv, float rt, float s, float rc = INFINITY) {
     float rinv2 = rinv * rinv;
-    if (hct_far(r, rt, s)) {
+    if (hct_far(r, rt, s, rc)) {
         float x = s * rinv, y = x * x;
         return -x * y * hct_series_dr(y) * rinv2;
     }
-    if (rt >= r + s) return 0.f;
-    HctClosed c = hct_closed(r, rt, s);
-    return -0.25f * (c.iL - c.iU) * (c.iL + c.iU) * fmaf(s * s, rinv2, 1.f)
-           - 0.5f * c.lg * rinv2;
+    float d = 0.f;
+    if (!hct_empty(r, rt, s, rc)) {
+        HctClosed c = hct_closed(r, rt, s, rc);
+        d = -0.25f * (c.iL - c.iU) * (c.iL + c.iU) * fmaf(s * s, rinv2, 1.f) - 0.5f * c.lg * rinv2;
+    }
+    return d;
 }
 
-__device__ __forceinline__ float hct_ds(float r, float rinv, float rt, float s) {
-    if (hct_far(r, rt, s)) {
+__device__ __forceinline__ float hct_ds(float r, float rinv, float rt, float s, float rc = INFINITY) {
+    if (hct_far(r, rt, s, rc)) {
         float x = s * rinv, y = x * x;
         return y * hct_series_ds(y) * rinv * rinv;
     }
-    if (rt >= r + s) return 0.f;
-    HctClosed c = hct_closed(r, rt, s);
-    return 0.5f * s * rinv * (c.iL - c.iU) * (c.iL + c.iU);
+    float d = 0.f;
+    if (!hct_empty(r, rt, s, rc)) {
+        HctClosed c = hct_closed(r, rt, s, rc);
+        d = 0.5f * s * rinv * (c.iL - c.iU) * (c.iL + c.iU);
+    }
+    return d;
 }
 
-__device__ __forceinline__ float hct_drt(float r, float rt, float irt, float s) {
-    if (hct_far(r, rt, s) || rt >= r + s) return 0.f;
-    if (rt < s - r) return -2.f * irt * irt;
-    if (rt > fabsf(r - s)) {
+__device__ __forceinline__ float hct_drt(float r, float rt, float irt, float s, float rc = INFINITY) {
+    if (hct_far(r, rt, s, rc)) return 0.f;
+    float d = 0.f;
+    if (rt < s - r) {
+        if (rt < fminf(s - r, rc)) d = -2.f * irt * irt;
+    } else if (rt > fabsf(r - s) && !hct_empty(r, rt, s, rc)) {
         float a = rt - r;
-        return (a * a - s * s) * 0.5f * __fdividef(1.f, r) * irt * irt * irt;
+        d = (a * a - s * s) * 0.5f * __fdividef(1.f, r) * irt * irt * irt;
     }
-    return 0.f;
+    return d;
 }
 
 // ------------------------------------------------------------- HCT, FP64
-// Closed forms throughout (FP64 has no cancellation problem at these sizes).
-__device__ __forceinline__ double hct(double r, double rinv, double rt, double irt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s;
-    double L = fmax(rt, fabs(r - s));
-    double iL = 1.0 / L, iU = 1.0 / U;
-    double h = (iL - iU) * (1.0 + (iL + iU) * 0.25 * rinv * (s - r) * (s + r))
-             + 0.5 * rinv * log(L * iU);
-    if (rt < s - r) h += 2.0 * (irt - iL);
+// Closed forms throughout (FP64 has no cancellation problem at these sizes);
+// rc as above (infinity = no cutoff).
+__device__ __forceinline__ double hct(double r, double rinv, double rt, double irt, double s, double rc = INFINITY) {
+    const double U = fmin(r + s, rc), L = fmax(rt, fabs(r - s));
+    double h = 0.0;
+    if (L < U) {
+        double iL = 1.0 / L, iU = 1.0 / U;
+        h = (iL - iU) * (1.0 + (iL + iU) * 0.25 * rinv * (s - r) * (s + r)) + 0.5 * rinv * log(L * iU);
+    }
+    if (rt < s - r) {
+        const double top = fmin(s - r, rc);
+        if (rt < top) h += 2.0 * (irt - 1.0 / top);
+    }
     return h;
 }
 
-__device__ __forceinline__ double hct_dr(double r, double rinv, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s;
-    double L = fmax(rt, fabs(r - s));
-    double iL = 1.0 / L, iU = 1.0 / U;
-    double rinv2 = rinv * rinv;
-    return -0.25 * (iL - iU) * (iL + iU) * (1.0 + s * s * rinv2) - 0.5 * log(L * iU) * rinv2;
+__device__ __forceinline__ double hct_dr(double r, double rinv, double rt, double s, double rc = INFINITY) {
+    const double U = fmin(r + s, rc), L = fmax(rt, fabs(r - s));
+    double d = 0.0;
+    if (L < U) {
+        double iL = 1.0 / L, iU = 1.0 / U;
+        double rinv2 = rinv * rinv;
+        d = -0.25 * (iL - iU) * (iL + iU) * (1.0 + s * s * rinv2) - 0.5 * log(L * iU) * rinv2;
+    }
+    return d;
 }
 
-__device__ __forceinline__ double hct_ds(double r, double rinv, double rt, double s) {
-    if (rt >= r + s) return 0.0;
-    double U = r + s;
-    double L = fmax(rt, fabs(r - s));
-    double iL = 1.0 / L, iU = 1.0 / U;
-    return 0.5 * s * rinv * (iL - iU) * (iL + iU);
+__device__ __forceinline__ double hct_ds(double r, double rinv, double rt, double s, double rc = INFINITY) {
+    const double U = fmin(r + s, rc), L = fmax(rt, fabs(r - s));
+    double d = 0.0;
+    if (L < U) {
+        double iL = 1.0 / L, iU = 1.0 / U;
+        d = 0.5 * s * rinv * (iL - iU) * (iL + iU);
+    }
+    return d;
 }
 
-__device__ __forceinline__ double hct_drt(double r, double rt, double irt, double s) {
-    if (rt >= r + s) return 0.0;
-    if (rt < s - r) return -2.0 * irt * irt;
-    if (rt > fabs(r - s)) {
+__device__ __forceinline__ double hct_drt(double r, double rt, double irt, double s, double rc = INFINITY) {
+    const double U = fmin(r + s, rc), L = fmax(rt, fabs(r - s));
+    if (rt < s - r) return rt < fmin(s - r, rc) ? -2.0 * irt * irt : 0.0;
+    if (rt > fabs(r - s) && L < U) {
         double a = rt - r;
         return (a * a - s * s) * 0.5 / r * irt * irt * irt;
     }

@@ -358,7 +358,7 @@ __global__ void k_site_ref(View V, const double* __restrict__ x0, const int* __r
             double d0 = x0[3 * (P + am)] - x0[3 * (P + an)], d1 = x0[3 * (P + am) + 1] - x0[3 * (P + an) + 1],
                    d2 = x0[3 * (P + am) + 2] - x0[3 * (P + an) + 2];
             const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-            sum += hct(r, 1.0 / r, rt, 1.0 / rt, V.sc[P + an]);
+            sum += hct(r, 1.0 / r, rt, 1.0 / rt, V.sc[P + an], V.rgbmax);
         }
         const double psi = 0.5 * rt * sum;
         const double th = tanh(psi * (V.alpha + psi * (-V.beta + psi * V.gamma)));
@@ -632,8 +632,14 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
 int launch_sym_pair(cph_engine* E, const SymItem* items, int n, bool energy, int pass,
                     cudaStream_t st) {
     if (n <= 0) return CPH_OK;
-    if (pass == 0) k_born_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
-    else if (pass == 2) k_chain_sym<<<n, kSymThreads, 0, st>>>(items, E->V);
+    const bool cut = E->V.rgbmax < INFINITY;
+    if (pass == 0) {
+        if (cut) k_born_sym<true><<<n, kSymThreads, 0, st>>>(items, E->V);
+        else k_born_sym<false><<<n, kSymThreads, 0, st>>>(items, E->V);
+    } else if (pass == 2) {
+        if (cut) k_chain_sym<true><<<n, kSymThreads, 0, st>>>(items, E->V);
+        else k_chain_sym<false><<<n, kSymThreads, 0, st>>>(items, E->V);
+    }
     else if (E->V.kappa > 0) {
         if (energy) k_gb_sym<true, true><<<n, kSymThreads, 0, st>>>(items, E->V);
         else k_gb_sym<false, true><<<n, kSymThreads, 0, st>>>(items, E->V);
@@ -886,6 +892,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         return fail(nullptr, CPH_E_INVALID, "surface term: sa_gamma must be finite, sa_probe finite and >= 0");
     if (!(p->gb.kappa >= 0) || !std::isfinite(p->gb.kappa))
         return fail(nullptr, CPH_E_INVALID, "salt screening kappa must be finite and >= 0");
+    if (!(p->gb.rgbmax >= 0) || !std::isfinite(p->gb.rgbmax))
+        return fail(nullptr, CPH_E_INVALID, "Born-radius cutoff rgbmax must be finite and >= 0 (0 = none)");
     if (!(p->dt > 0) || !(p->gamma_ln >= 0) || !(p->gb.eps_in > 0) || !(p->gb.eps_out > 0))
         return fail(nullptr, CPH_E_INVALID, "dt, gamma_ln, eps_in, eps_out must be positive");
     if (p->mc_ph_every < 0 || p->mc_redox_every < 0 || p->exchange_every < 0)
@@ -1327,6 +1335,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.tau_pair = p->gb.kappa > 0 ? 1.0 : V.tau;
     V.sa_gamma = p->gb.sa_gamma;
     V.sa_probe = p->gb.sa_probe;
+    V.rgbmax = p->gb.rgbmax > 0 ? p->gb.rgbmax : INFINITY;
     V.inv_eps_in = 1.0 / p->gb.eps_in;
     V.sqrt_k = std::sqrt(kCoulomb);
     V.alpha = p->gb.alpha;
@@ -1341,6 +1350,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         for (double v : rt) rtmax = std::max(rtmax, v);
         const double rfar = std::max(smax / (double)kHctXmax, smax + rtmax) * (1.0 + 1e-5);
         V.rfar2 = (float)(rfar * rfar);
+        V.smax32 = (float)smax;
     }
     V.seed = seed;
     Item* di;

@@ -91,6 +91,8 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
         return gfail(CPH_E_INVALID, "cph_gb_energy: bad surface-term parameters");
     if (gb->kappa != 0.0)
         return gfail(CPH_E_INVALID, "cph_gb_energy: salt screening (kappa > 0) is not supported here");
+    if (!(gb->rgbmax >= 0) || !std::isfinite(gb->rgbmax))
+        return gfail(CPH_E_INVALID, "cph_gb_energy: rgbmax must be finite and >= 0 (0 = no cutoff)");
     g = SView{};
     g.n_rep = n_rep;
     g.n = n;
@@ -109,6 +111,7 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     g.offset = gb->offset;
     g.sa_gamma = gb->sa_gamma;
     g.sa_probe = gb->sa_probe;
+    g.rgbmax = gb->rgbmax > 0 ? gb->rgbmax : INFINITY;
     ws_carve_sym(g, ws);
     return CPH_OK;
 }
@@ -122,7 +125,8 @@ int launch_radii(SView& g, cudaStream_t st) {
     const int ba = (int)((na + 255) / 256);
     const int grid = g.n_rep * g.n_itile * g.n_chunk;
     k_gbound<<<ba, 256, 0, st>>>(g);
-    k_gborn_sym<<<grid, kGT, 0, st>>>(g);
+    if (g.rgbmax < INFINITY) k_gborn_sym<true><<<grid, kGT, 0, st>>>(g);
+    else k_gborn_sym<false><<<grid, kGT, 0, st>>>(g);
     k_gfin_born<<<ba, 256, 0, st>>>(g);
     return CPH_OK;
 }
@@ -174,7 +178,8 @@ extern "C" int cph_gb_energy_backward(int n_rep, int n, const float* x, const fl
     const int grid = n_rep * g.n_itile * g.n_chunk;
     k_gpair_sym<true><<<grid, kGT, 0, st>>>(g);
     k_gfin_c<true><<<ba, 256, 0, st>>>(g);
-    k_gchain_sym<<<grid, kGT, 0, st>>>(g);
+    if (g.rgbmax < INFINITY) k_gchain_sym<true><<<grid, kGT, 0, st>>>(g);
+    else k_gchain_sym<false><<<grid, kGT, 0, st>>>(g);
     k_gfin_out<<<ba, 256, 0, st>>>(g);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return gfail(CPH_E_CUDA, std::string("cph_gb_energy_backward: ") + cudaGetErrorString(ce));

@@ -14,7 +14,9 @@
 // Far pairs: a bound kernel takes s_max and rt_max over every replica's atoms;
 // for r >= r_far = max(s_max / 0.35, s_max + rt_max) every descreening
 // integral of the pair, and its r-, rt- and s-derivatives, are in the
-// disjoint-sphere series regime (dH/drt = 0 there).
+// disjoint-sphere series regime (dH/drt = 0 there).  A Born-radius cutoff rc
+// adds the band rc - s_max < r < rc + s_max to the closed forms and zeroes
+// every pair beyond it (see PairBand).
 #pragma once
 #include "cph_device.cuh"
 #include "cph_pair_tiles.cuh"
@@ -34,6 +36,7 @@ struct SView {
     const float *x, *q, *rho, *screen;
     double tau, sqrt_k, alpha, beta, gamma, offset;
     double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
+    double rgbmax;             // Born-radius cutoff, INFINITY = none
     // per replica-atom (index r * n + a); int64 slots alias double slots that
     // are not live at the same time (see ws_carve_sym)
     double *psi, *R, *dEdR, *c, *dq, *gpsi;
@@ -56,10 +59,10 @@ __global__ void k_gbound(SView g) {
     atomicMax(&g.bound[1], __float_as_uint(fmaxf(rt, 0.f)));
 }
 
-__device__ __forceinline__ float gfar2(const SView& g) {
+__device__ __forceinline__ PairBand gband(const SView& g) {
     const float smax = __uint_as_float(g.bound[0]), rtmax = __uint_as_float(g.bound[1]);
     const float rf = fmaxf(smax / kHctXmax, smax + rtmax) * 1.0001f;
-    return rf * rf;
+    return pair_band(rf * rf, smax, (float)g.rgbmax);
 }
 
 struct GItem {
@@ -98,6 +101,7 @@ __device__ __forceinline__ bool gmasked(int jt, int i0, int n) {
 }
 
 // ------------------------------------------------------------ Born radii
+template <bool CUT>
 __global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
     __shared__ BoJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ];
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float off = (float)g.offset, rfar2 = gfar2(g);
+    const float off = (float)g.offset;
+    const PairBand band = gband(g);
     int ii[2];
     bool vi[2];
     BoI2 I[2];
@@ -169,8 +174,8 @@ __global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
                     for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
                 }
             }
-            if (masked) born_tile<true>(sj[pr], lane, I, ah, jh, sk, rfar2);
-            else born_tile<false>(sj[pr], lane, I, ah, jh, sk, rfar2);
+            if (masked) born_tile<true, CUT>(sj[pr], lane, I, ah, jh, sk, band);
+            else born_tile<false, CUT>(sj[pr], lane, I, ah, jh, sk, band);
 #pragma unroll
             for (int u = 0; u < 2; ++u)
                 hx[u] += to_fixed(ah[u].x, (float)kScaleH) + to_fixed(ah[u].y, (float)kScaleH);
@@ -477,26 +482,26 @@ struct GcNear {
     float t, hti, htj, asi, asj;
 };
 
-// Closed forms of one pair inside r_far, out of line (a warp only gets here
-// when one of its lanes has such a pair): the gradient factor t, dH/drt both
-// ways, and the c-weighted dH/ds both ways.
+// Closed forms of one pair inside r_far or in the cutoff band, out of line
+// (a warp only gets here when one of its lanes has such a pair): the gradient
+// factor t, dH/drt both ways, and the c-weighted dH/ds both ways.
 static __device__ __noinline__ GcNear gchain_near(float r2, float rinv, float ci, float rti, float irti, float si,
-                                                  float cj, float sj, float rtj, float irtj) {
+                                                  float cj, float sj, float rtj, float irtj, float rc) {
     const float r = r2 * rinv;
     GcNear o;
-    o.t = (ci * hct_dr(r, rinv, rti, sj) + cj * hct_dr(r, rinv, rtj, si)) * rinv;
-    o.hti = hct_drt(r, rti, irti, sj);
-    o.htj = hct_drt(r, rtj, irtj, si);
-    o.asi = cj * hct_ds(r, rinv, rtj, si);
-    o.asj = ci * hct_ds(r, rinv, rti, sj);
+    o.t = (ci * hct_dr(r, rinv, rti, sj, rc) + cj * hct_dr(r, rinv, rtj, si, rc)) * rinv;
+    o.hti = hct_drt(r, rti, irti, sj, rc);
+    o.htj = hct_drt(r, rtj, irtj, si, rc);
+    o.asi = cj * hct_ds(r, rinv, rtj, si, rc);
+    o.asj = ci * hct_ds(r, rinv, rti, sj, rc);
     return o;
 }
 
-template <bool MASKED>
+template <bool MASKED, bool CUT>
 __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2 (&I)[2], float2 (&ai)[2][5],
-                                            float2 (&aj)[5], const uint32_t (&sk)[2][2], float rfar2) {
+                                            float2 (&aj)[5], const uint32_t (&sk)[2][2], const PairBand& band) {
     const int src = (lane + 1) & 31;
-    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
+    const float skr2 = band.skr2;
     const float2 mone = splat<float2>(-1.f);
 #pragma unroll 2
     for (int k = 0; k < kGJ; ++k) {
@@ -525,28 +530,38 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
             // c_j dH(r; rt_j, s_i)/ds = c_j s_i^2 S_i / r^4, and i <-> j
             asi[u] = __fmul2_rn(__fmul2_rn(cj, I[u].s2), __fmul2_rn(hct_series_ds(yi), rinv4));
             asj[u] = __fmul2_rn(__fmul2_rn(I[u].c, s2j), __fmul2_rn(hct_series_ds(yj), rinv4));
+            if (CUT) { // beyond rc + s_max nothing descreens
+                const bool o0 = r2[u].x >= band.rout2, o1 = r2[u].y >= band.rout2;
+                t[u].x = o0 ? 0.f : t[u].x;
+                t[u].y = o1 ? 0.f : t[u].y;
+                asi[u].x = o0 ? 0.f : asi[u].x;
+                asi[u].y = o1 ? 0.f : asi[u].y;
+                asj[u].x = o0 ? 0.f : asj[u].x;
+                asj[u].y = o1 ? 0.f : asj[u].y;
+            }
         }
-        // closed forms only where some lane has a pair inside r_far (rare; skipped
+        // closed forms only where some lane has such a pair (rare; skipped
         // pairs never get here, and dH/drt is zero in the far regime, so only
         // this branch adds to the rt sums)
-        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        const bool nr = band_near<CUT>(r2[0].x, band) || band_near<CUT>(r2[0].y, band) ||
+                        band_near<CUT>(r2[1].x, band) || band_near<CUT>(r2[1].y, band);
         if (__any_sync(0xffffffffu, nr)) {
             const float4 Nj = sj.n[lane + k];
             const float2 Mj = sj.m[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (r2[u].x < rfar2) {
+                if (band_near<CUT>(r2[u].x, band)) {
                     const GcNear o = gchain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.z, Nj.x,
-                                                 Nj.z, Mj.x);
+                                                 Nj.z, Mj.x, band.rc);
                     t[u].x = o.t;
                     ai[u][3].x += o.hti;
                     aj[3].x += o.htj;
                     asi[u].x = o.asi;
                     asj[u].x = o.asj;
                 }
-                if (r2[u].y < rfar2) {
+                if (band_near<CUT>(r2[u].y, band)) {
                     const GcNear o = gchain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.w, Nj.y,
-                                                 Nj.w, Mj.y);
+                                                 Nj.w, Mj.y, band.rc);
                     t[u].y = o.t;
                     ai[u][3].y += o.hti;
                     aj[3].y += o.htj;
@@ -584,6 +599,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
     }
 }
 
+template <bool CUT>
 __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
     __shared__ GcJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ][5];
@@ -594,7 +610,8 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float off = (float)g.offset, rfar2 = gfar2(g);
+    const float off = (float)g.offset;
+    const PairBand band = gband(g);
     int ii[2];
     bool vi[2];
     GcI2 I[2];
@@ -660,8 +677,8 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
                     for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
                 }
             }
-            if (masked) gchain_tile<true>(sj[pr], lane, I, ai, aj, sk, rfar2);
-            else gchain_tile<false>(sj[pr], lane, I, ai, aj, sk, rfar2);
+            if (masked) gchain_tile<true, CUT>(sj[pr], lane, I, ai, aj, sk, band);
+            else gchain_tile<false, CUT>(sj[pr], lane, I, ai, aj, sk, band);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int row = warp * 64 + u * 32 + lane;

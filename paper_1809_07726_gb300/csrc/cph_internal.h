@@ -88,6 +88,10 @@ struct View {
     double* xprev; // null when SHAKE is off
     double shake_tol;
     float rfar2; // pairs with r^2 >= rfar2 are in the series regime in both directions
+    float smax32; // largest descreening radius s over every system atom
+    // Born-radius cutoff (AMBER's rgbmax): descreening shells beyond it do not
+    // count; INFINITY = none
+    double rgbmax;
     // FP32 pair-kernel operands, staged once per step by one thread per atom
     float4* xs;          // (x, y, z, 0) relative to the walker's first atom
     float4* gq;          // (sqrt(k) q, R, 1/R, log2(e) / (4 R)), after the Born radii and MC

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         rti = Real(V.rt[P + i]);
     }
     const Real irti = Real(1) / rti;
+    const Real rc = Real(V.rgbmax); // Born-radius cutoff (INFINITY = none)
     typename Pr::Acc acc = 0;
     int mp = V.mt_off[it.st];
     const int me = V.mt_off[it.st + 1];
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
                 const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
                 const Real r2 = dx * dx + dy * dy + dz * dz;
                 const Real rinv = Pr::rsqrt(r2);
-                part += hct(r2 * rinv, rinv, rti, irti, b.w);
+                part += hct(r2 * rinv, rinv, rti, irti, b.w, rc);
             }
         } else {
             ++mp;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
                 Real r2 = dx * dx + dy * dy + dz * dz;
                 r2 = self ? Real(1) : r2;
                 const Real rinv = Pr::rsqrt(r2);
-                const Real h = hct(r2 * rinv, rinv, rti, irti, b.w);
+                const Real h = hct(r2 * rinv, rinv, rti, irti, b.w, rc);
                 part += self ? Real(0) : h;
             }
         }
@@ -426,6 +427,7 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
         rti = Real(V.rt[P + i]);
     }
     Acc fx = 0, fy = 0, fz = 0;
+    const Real rc = Real(V.rgbmax); // Born-radius cutoff (INFINITY = none)
     int mp = V.mt_off[it.st];
     const int me = V.mt_off[it.st + 1];
     int next = mp < me ? V.mt_list[mp] : 0x7fffffff;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
                 const Real r2 = dx * dx + dy * dy + dz * dz;
                 const Real rinv = Pr::rsqrt(r2);
                 const Real r = r2 * rinv;
-                const Real g = ci * hct_dr(r, rinv, rti, b.x) + a.w * hct_dr(r, rinv, b.y, si);
+                const Real g = ci * hct_dr(r, rinv, rti, b.x, rc) + a.w * hct_dr(r, rinv, b.y, si, rc);
                 const Real t = -g * rinv;
                 px += t * dx;
                 py += t * dy;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
                 r2 = self ? Real(1) : r2;
                 const Real rinv = Pr::rsqrt(r2);
                 const Real r = r2 * rinv;
-                const Real g = ci * hct_dr(r, rinv, rti, b.x) + a.w * hct_dr(r, rinv, b.y, si);
+                const Real g = ci * hct_dr(r, rinv, rti, b.x, rc) + a.w * hct_dr(r, rinv, b.y, si, rc);
                 const Real t = self ? Real(0) : -g * rinv;
                 px += t * dx;
                 py += t * dy;

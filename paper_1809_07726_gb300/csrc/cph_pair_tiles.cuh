@@ -28,21 +28,56 @@ struct BoJs {
     float4 n[2 * kTileJ]; // (rtA, rtB, 1/rtA, 1/rtB): closed forms
 };
 
-// Closed-form integrals of one pair inside r_far, kept out of line: a warp
-// only gets here when one of its lanes has such a pair, and a single copy of
-// this code keeps the unrolled tile loops small enough for the instruction
-// cache.  Returns (H(r, rt_i, s_j), H(r, rt_j, s_i)).
-static __device__ __noinline__ float2 born_near(float r2, float rinv, float rt_i, float irt_i, float s_i, float s_j,
-                                         float rt_j, float irt_j) {
-    const float r = r2 * rinv;
-    return make_float2(hct(r, rinv, rt_i, irt_i, s_j), hct(r, rinv, rt_j, irt_j, s_i));
+// Which pairs a tile sends to the closed forms.  Without a Born-radius
+// cutoff: those inside r_far.  With a cutoff rc, also the band
+// rc - s_max < r < rc + s_max, where U = min(r + s, rc) may sit at rc; inside
+// the band's lower edge r + s <= rc for every s, so the series still holds
+// there, and beyond its upper edge every integral and derivative of the pair
+// vanishes (L >= r - s_max >= rc >= U), which CUT tiles apply as a select.
+// Skipped pairs take r^2 = skr2, beyond r_far and the band (results zeroed).
+struct PairBand {
+    float rfar2, rin2, rout2, rc, skr2;
+};
+
+// rfar2 and s_max over every atom; rc = INFINITY for no cutoff.  The band's
+// edges are widened by 1e-5 so that rounding can only move a pair towards
+// the closed forms.
+__host__ __device__ inline PairBand pair_band(float rfar2, float smax, float rc) {
+    PairBand b;
+    b.rfar2 = rfar2;
+    b.rc = rc;
+    if (rc < INFINITY) {
+        const float rin = fmaxf(rc - smax, 0.f) * (1.f - 1e-5f), rout = (rc + smax) * (1.f + 1e-5f);
+        b.rin2 = rin * rin;
+        b.rout2 = rout * rout;
+        b.skr2 = 4.f * fmaxf(rfar2, b.rout2) + 1.f;
+    } else {
+        b.rin2 = b.rout2 = INFINITY;
+        b.skr2 = 4.f * rfar2 + 1.f;
+    }
+    return b;
 }
 
-template <bool MASKED>
+template <bool CUT>
+__device__ __forceinline__ bool band_near(float r2, const PairBand& b) {
+    return CUT ? (r2 < b.rfar2 || (r2 > b.rin2 && r2 < b.rout2)) : r2 < b.rfar2;
+}
+
+// Closed-form integrals of one pair inside r_far (or in the cutoff band),
+// kept out of line: a warp only gets here when one of its lanes has such a
+// pair, and a single copy of this code keeps the unrolled tile loops small
+// enough for the instruction cache.  Returns (H(r, rt_i, s_j), H(r, rt_j, s_i)).
+static __device__ __noinline__ float2 born_near(float r2, float rinv, float rt_i, float irt_i, float s_i, float s_j,
+                                         float rt_j, float irt_j, float rc) {
+    const float r = r2 * rinv;
+    return make_float2(hct(r, rinv, rt_i, irt_i, s_j, rc), hct(r, rinv, rt_j, irt_j, s_i, rc));
+}
+
+template <bool MASKED, bool CUT>
 __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (&I)[2], float2 (&ah)[2],
-                                          float2& jh, const uint32_t (&sk)[2][2], float rfar2) {
+                                          float2& jh, const uint32_t (&sk)[2][2], const PairBand& band) {
     const int src = (lane + 1) & 31;
-    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
+    const float skr2 = band.skr2;
 #pragma unroll 2
     for (int k = 0; k < kTileJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
@@ -64,20 +99,30 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
             const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
             hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), __fmul2_rn(s3j, rinv4));
             hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), __fmul2_rn(I[u].s3, rinv4));
+            if (CUT) { // beyond rc + s_max nothing descreens
+                const bool o0 = r2[u].x >= band.rout2, o1 = r2[u].y >= band.rout2;
+                hi[u].x = o0 ? 0.f : hi[u].x;
+                hj[u].x = o0 ? 0.f : hj[u].x;
+                hi[u].y = o1 ? 0.f : hi[u].y;
+                hj[u].y = o1 ? 0.f : hj[u].y;
+            }
         }
-        // closed forms only where some lane has a pair inside r_far (rare)
-        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        // closed forms only where some lane has such a pair (rare)
+        const bool nr = band_near<CUT>(r2[0].x, band) || band_near<CUT>(r2[0].y, band) ||
+                        band_near<CUT>(r2[1].x, band) || band_near<CUT>(r2[1].y, band);
         if (__any_sync(0xffffffffu, nr)) {
             const float4 Nj = sj.n[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (r2[u].x < rfar2) {
-                    const float2 h = born_near(r2[u].x, rinv[u].x, I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z);
+                if (band_near<CUT>(r2[u].x, band)) {
+                    const float2 h = born_near(r2[u].x, rinv[u].x, I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z,
+                                               band.rc);
                     hi[u].x = h.x;
                     hj[u].x = h.y;
                 }
-                if (r2[u].y < rfar2) {
-                    const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w);
+                if (band_near<CUT>(r2[u].y, band)) {
+                    const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w,
+                                               band.rc);
                     hi[u].y = h.x;
                     hj[u].y = h.y;
                 }

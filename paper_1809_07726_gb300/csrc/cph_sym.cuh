@@ -426,20 +426,20 @@ struct ChJs {
     float4 n[2 * kSymJ]; // (sA, sB, rtA, rtB): closed forms
 };
 
-// Closed-form force weight t of one pair inside r_far, out of line for the
-// same reason as born_near.
+// Closed-form force weight t of one pair inside r_far (or in the cutoff
+// band), out of line for the same reason as born_near.
 __device__ __noinline__ float chain_near(float r2, float rinv, float c_i, float rt_i, float s_i, float c_j,
-                                         float s_j, float rt_j) {
+                                         float s_j, float rt_j, float rc) {
     const float r = r2 * rinv;
-    const float g = c_i * hct_dr(r, rinv, rt_i, s_j) + c_j * hct_dr(r, rinv, rt_j, s_i);
+    const float g = c_i * hct_dr(r, rinv, rt_i, s_j, rc) + c_j * hct_dr(r, rinv, rt_j, s_i, rc);
     return -g * rinv;
 }
 
-template <bool MASKED>
+template <bool MASKED, bool CUT>
 __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 (&I)[2], float2 (&a)[2][3],
-                                           float2 (&ja)[3], const uint32_t (&sk)[2][2], float rfar2) {
+                                           float2 (&ja)[3], const uint32_t (&sk)[2][2], const PairBand& band) {
     const int src = (lane + 1) & 31;
-    const float skr2 = 4.f * rfar2 + 1.f; // r^2 of skipped pairs: beyond r_far, results zeroed
+    const float skr2 = band.skr2;
 #pragma unroll 2
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
@@ -463,17 +463,22 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
             const float2 term = __ffma2_rn(__fmul2_rn(I[u].c, s3j), qj, __fmul2_rn(__fmul2_rn(cj, I[u].s3), qi));
             const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
             t[u] = __fmul2_rn(term, __fmul2_rn(rinv4, rinv2));
+            if (CUT) { // beyond rc + s_max nothing descreens
+                t[u].x = r2[u].x >= band.rout2 ? 0.f : t[u].x;
+                t[u].y = r2[u].y >= band.rout2 ? 0.f : t[u].y;
+            }
         }
-        // closed forms only where some lane has a pair inside r_far (rare)
-        const bool nr = r2[0].x < rfar2 || r2[0].y < rfar2 || r2[1].x < rfar2 || r2[1].y < rfar2;
+        // closed forms only where some lane has such a pair (rare)
+        const bool nr = band_near<CUT>(r2[0].x, band) || band_near<CUT>(r2[0].y, band) ||
+                        band_near<CUT>(r2[1].x, band) || band_near<CUT>(r2[1].y, band);
         if (__any_sync(0xffffffffu, nr)) {
             const float4 Nj = sj.n[lane + k];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (r2[u].x < rfar2)
-                    t[u].x = chain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].s, B.z, Nj.x, Nj.z);
-                if (r2[u].y < rfar2)
-                    t[u].y = chain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].s, B.w, Nj.y, Nj.w);
+                if (band_near<CUT>(r2[u].x, band))
+                    t[u].x = chain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].s, B.z, Nj.x, Nj.z, band.rc);
+                if (band_near<CUT>(r2[u].y, band))
+                    t[u].y = chain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].s, B.w, Nj.y, Nj.w, band.rc);
             }
         }
 #pragma unroll
@@ -498,6 +503,7 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
     }
 }
 
+template <bool CUT>
 __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __restrict__ items, View V) {
     __shared__ ChJs sj[kSymG / 2];
     __shared__ __align__(16) float red[kSymG][4][kSymJ][4]; // component 3 unused (vector stores)
@@ -505,7 +511,7 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float rfar2 = V.rfar2;
+    const PairBand band = pair_band(V.rfar2, V.smax32, (float)V.rgbmax);
     int ii[2];
     bool vi[2];
     ChI2 I[2];
@@ -581,8 +587,8 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
                     for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, sk[u][h], nbm);
                 }
             }
-            if (masked) chain_tile<true>(sj[pr], lane, I, acc, ja, sk, rfar2);
-            else chain_tile<false>(sj[pr], lane, I, acc, ja, sk, rfar2);
+            if (masked) chain_tile<true, CUT>(sj[pr], lane, I, acc, ja, sk, band);
+            else chain_tile<false, CUT>(sj[pr], lane, I, acc, ja, sk, band);
             // per-tile conversion (each half is one tile)
 #pragma unroll
             for (int u = 0; u < 2; ++u)
@@ -721,13 +727,14 @@ __global__ void k_final_forces(View V, int a0, int n) {
 
 // ========================================================= Born radii
 // Tile arithmetic (BoI2, BoJs, born_tile) in cph_pair_tiles.cuh.
+template <bool CUT>
 __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __restrict__ items, View V) {
     __shared__ BoJs sj[kSymG / 2];
     __shared__ float red[kSymG][4][kSymJ];
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float rfar2 = V.rfar2;
+    const PairBand band = pair_band(V.rfar2, V.smax32, (float)V.rgbmax);
     int ii[2];
     bool vi[2];
     BoI2 I[2];
@@ -800,8 +807,8 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
                     for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, sk[u][h], nbm);
                 }
             }
-            if (masked) born_tile<true>(sj[pr], lane, I, ah, jh, sk, rfar2);
-            else born_tile<false>(sj[pr], lane, I, ah, jh, sk, rfar2);
+            if (masked) born_tile<true, CUT>(sj[pr], lane, I, ah, jh, sk, band);
+            else born_tile<false, CUT>(sj[pr], lane, I, ah, jh, sk, band);
             // per-tile conversion (each half is one tile)
 #pragma unroll
             for (int u = 0; u < 2; ++u)

@@ -56,7 +56,9 @@ def _descs(systems, grid, keep):
 def _init(L, systems, grid, **kw):
     keep = cphremd._Keep()
     descs, g = _descs(systems, grid, keep)
-    p = cphremd.RunParams(cphremd.default_gb(), kw.get("dt", 0.002), 10.0,
+    gb = cphremd.default_gb()
+    gb.rgbmax = kw.get("rgbmax", 0.0)
+    p = cphremd.RunParams(gb, kw.get("dt", 0.002), 10.0,
                           kw.get("precision", cphremd.PREC_FP32), 10, 10, 100)
     out = C.c_void_p()
     rc = L.cph_init_system(C.cast(descs, C.c_void_p), len(systems), C.byref(g), C.byref(p), 1,
@@ -109,6 +111,13 @@ def test_rejects_bad_precision_and_timestep(L, small):
     assert rc == cphremd.E_INVALID
     rc, _, _ = _init(L, [small], grid, dt=0.0)
     assert rc == cphremd.E_INVALID
+
+
+@pytest.mark.parametrize("rgbmax", [-1.0, float("nan"), float("inf")])
+def test_rejects_bad_born_radius_cutoff(L, small, rgbmax):
+    grid = synth.Grid(np.array([0.0]), np.array([7.0]), np.array([300.0]), np.zeros(1, np.int32))
+    rc, out, msg = _init(L, [small], grid, rgbmax=rgbmax)
+    assert rc == cphremd.E_INVALID and not out.value and "rgbmax" in msg
 
 
 def test_gb_energy_rejects_bad_arguments(L):

@@ -136,20 +136,21 @@ def _band(x, prec):
 
 
 @pytest.mark.parametrize("prec", [cphremd.PREC_FP32, cphremd.PREC_FP64])
-@pytest.mark.parametrize("kappa", [0.0, 0.1])
-def test_mc_sweep_matches_oracle(prec, kappa):
+@pytest.mark.parametrize("kappa,rgbmax", [(0.0, 0.0), (0.1, 0.0), (0.0, 10.0)])
+def test_mc_sweep_matches_oracle(prec, kappa, rgbmax):
     """One protonation + redox sweep on the 2400-atom system with 20 pH sites:
     dU against the oracle's full recomputation, identical decisions; without
-    salt and with Debye-Hueckel screening (kappa = 0.1 / A)."""
+    salt, with Debye-Hueckel screening (kappa = 0.1 / A), and with a 10 A
+    Born-radius cutoff (which the sites' reference compounds see too)."""
     systems, grid = synth.config_c3()
     grid = synth.Grid(grid.E[[0, 3, 5, 7]], grid.pH[[0, 4]], grid.T, np.zeros(8, np.int32),
                       order=("E", "pH"))
-    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, kappa)
+    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, kappa, 0.0, 1.4, rgbmax)
     eng = cphremd.init_system(systems, grid, seed=11, precision=prec, gb=gb)
     eng.set_step(10)
     eng.mc_titrate(cphremd.MC_BOTH)
     recs = eng.mc_records()
-    W = oracle.Walkers(systems, grid, seed=11, gb=oracle.GBParams(kappa=kappa))
+    W = oracle.Walkers(systems, grid, seed=11, gb=oracle.GBParams(kappa=kappa, rgbmax=rgbmax))
     for w in range(grid.n_slots):
         oracle.mc_sweep(W, w, "ph", 10)
         oracle.mc_sweep(W, w, "redox", 10)
@@ -328,14 +329,39 @@ def test_checkpoint_restart_continues_bitwise(ragged_systems):
 
 
 # OBC model II ("igb=5"), model I with other dielectric constants, model I with
-# salt screening, and model II with salt and the surface term: the GB variants
-# are parameter sets of the same kernels
+# salt screening, model II with salt and the surface term, and Born-radius
+# cutoffs (8 A cuts through all three ragged systems, 12 A through the largest
+# with the other variants on): the GB variants are parameter sets of the same
+# kernels (the cutoff selects the band-aware tile variant)
 GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85, kappa=0.0),
                dict(eps_in=2.0, eps_out=80.0, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125, kappa=0.0),
                dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125,
                     kappa=0.1),  # Debye-Hueckel salt screening
                dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85,
-                    kappa=0.05, sa_gamma=0.005, sa_probe=1.4)]  # + ACE surface term
+                    kappa=0.05, sa_gamma=0.005, sa_probe=1.4),  # + ACE surface term
+               dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=0.8, beta=0.0, gamma=2.909125,
+                    kappa=0.0, rgbmax=8.0),  # Born-radius cutoff
+               dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, gamma=4.85,
+                    kappa=0.05, sa_gamma=0.005, sa_probe=1.4, rgbmax=12.0)]
+
+
+def test_cutoff_beyond_every_pair_changes_nothing(ragged_systems):
+    """A Born-radius cutoff farther than every pair separation plus s_max
+    leaves the band-aware FP32 tiles on exactly the arithmetic of the plain
+    ones (bitwise equal results); an 8 A cutoff does change the radii."""
+    grid = _grid_for(ragged_systems)
+    out = []
+    for rc in (0.0, 1000.0, 8.0):
+        gb = cphremd.default_gb()
+        gb.rgbmax = rc
+        eng = cphremd.init_system(ragged_systems, grid, seed=3, gb=gb)
+        eng.evaluate()
+        out.append((eng.born_radii(), eng.forces(), eng.energies()))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    # fewer descreening shells: smaller psi and so smaller radii
+    R0, R8 = out[0][0], out[2][0]
+    assert (R8 <= R0 * (1 + 1e-6)).all() and (R8 < R0 * (1 - 1e-4)).mean() > 0.5
 
 
 @pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
@@ -344,7 +370,8 @@ GB_VARIANTS = [dict(eps_in=1.0, eps_out=78.5, offset=0.09, alpha=1.0, beta=0.8, 
 def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr):
     grid = _grid_for(ragged_systems)
     gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"],
-                          v["kappa"], v.get("sa_gamma", 0.0), v.get("sa_probe", 1.4))
+                          v["kappa"], v.get("sa_gamma", 0.0), v.get("sa_probe", 1.4),
+                          v.get("rgbmax", 0.0))
     eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec, gb=gb)
     eng.evaluate()
     og = oracle.GBParams(**v)

@@ -104,6 +104,32 @@ def test_obc2_energy_and_gradient_match_oracle():
         assert _rel_rms(dr[r], gr) <= 1e-5
 
 
+@pytest.mark.parametrize("rgbmax,n", [(9.0, 300), (14.0, 700)])
+def test_cutoff_energy_and_gradient_match_oracle(rgbmax, n):
+    """A Born-radius cutoff through the differentiable energy: the band-aware
+    tiles' energy and gradient (including the capped-U terms of dH/dr, dH/ds
+    and dH/drt) against the oracle's."""
+    import torch
+    gb = cphremd.default_gb()
+    gb.rgbmax = rgbmax
+    s, x, q, rho = _batch(2, n, 43)
+    xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
+    st = _torch(s.screen, torch.float32)
+    E = cphremd.gb_energy(xt, qt, rt, st, gb=gb).cpu().numpy()
+    dx, dq, dr = (t.cpu().numpy().astype(np.float64) for t in cphremd.gb_energy_backward(
+        xt, qt, rt, st, torch.ones(2, dtype=torch.float64, device="cuda:0"), gb=gb))
+    for r in range(2):
+        xr, qr, rr = (a[r].astype(np.float32).astype(np.float64) for a in (x, q, rho))
+        sc = s.screen.astype(np.float32).astype(np.float64)
+        Eo, gx, gq, gr = oracle.gb_grad(xr, qr, rr, sc, oracle.GBParams(rgbmax=rgbmax))
+        E_full = oracle.gb_grad(xr, qr, rr, sc, oracle.GBParams())[0]
+        assert abs(Eo - E_full) > 1e-4 * abs(E_full)  # the cutoff matters here
+        assert abs(E[r] - Eo) <= 1e-6 * abs(Eo), (E[r], Eo)
+        assert _rel_rms(dx[r], gx) <= 1e-5
+        assert _rel_rms(dq[r], gq) <= 1e-5
+        assert _rel_rms(dr[r], gr) <= 1e-5
+
+
 def test_salt_is_refused_by_the_differentiable_energy():
     import torch
     s, x, q, rho = _batch(1, 40, 3)
