@@ -19,98 +19,116 @@
 namespace cph {
 
 // =====================================================================
-// Monte-Carlo titration sweep (one CTA per walker)
+// Monte-Carlo titration sweep
 // =====================================================================
 // For the visited site with charges q -> q + dq (dq only on the site's atoms),
 //   dU = sum_m dq_m (A q)_m + 1/2 sum_{m,n} dq_m dq_n A_mn,
 // A_ij = k/(eps_in r_ij) [not excluded] - tau k / f_ij (i != j), A_ii = -tau k / R_i,
 // i.e. U_el(q + dq) - U_el(q) for U_el = E_coul + E_GB at fixed Born radii.
-// The linear term runs over all N atoms (threads split j); the Coulomb part of
-// excluded pairs is removed afterwards, and the small quadratic term is summed
-// in FP64.
+//
+// A site's proposal (the state b drawn uniformly among the others, and ln u)
+// depends only on the counter-based stream, never on the other sites'
+// outcomes, and sites share no atoms.  So the sweep runs in two kernels:
+//  - k_mc_site, one CTA per (walker, site): dU0, the change at the charges of
+//    the sweep's start.  The linear term runs over all N atoms (threads split
+//    j); the Coulomb part of excluded pairs is removed afterwards, and the
+//    small quadratic term is summed in FP64 (threads split its pairs).
+//  - k_mc_sweep, one CTA per walker: the sites in index order; the site's dU
+//    is dU0 plus dq^T A dq' for every site of this sweep accepted before it
+//    (dq' its accepted change), then the Metropolis test.
+// Both sums run in fixed orders, so the result does not depend on the launch
+// form.
 constexpr int kMcThreads = 256;
 constexpr int kMaxSiteAtoms = 64;
 
+// A_mn * k (both i != j), without the Coulomb part when `excluded`
 template <class Real>
-__global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, int clear_others,
-                                                   int w_begin) {
+__device__ __forceinline__ Real mc_pair(Real dx, Real dy, Real dz, Real Rm, Real Rn, bool excluded, Real iei,
+                                        Real tau, Real kap, Real ieo, bool salt) {
+    using Pr = Prec<Real>;
+    const Real r2 = dx * dx + dy * dy + dz * dz;
+    const Real rinv = Pr::rsqrt(r2);
+    const Real D = Real(0.25) * r2 / (Rm * Rn);
+    const Real fi = Pr::rsqrt(r2 + Rm * Rn * Pr::expm(D));
+    const Real tf = salt ? iei - ieo * Pr::expm(kap / fi) : tau;
+    return (excluded ? Real(0) : iei * rinv) - tf * fi;
+}
+
+__device__ inline bool mc_excluded(const View& V, int P, int at, int an) {
+    for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e)
+        if (V.excl_j[e] == an) return true;
+    return false;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(kMcThreads) k_mc_site(View V, int kind, int s_off, int w_begin) {
     using Pr = Prec<Real>;
     using Acc = typename Pr::Acc;
-    const int w = w_begin + blockIdx.x;
+    const int w = w_begin + blockIdx.y, k = blockIdx.x;
     const int s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int g0 = V.sys_site_off[s], ns = V.sys_site_off[s + 1] - g0, so = V.w_site_off[w];
+    if (k >= ns || V.site_kind[g0 + k] != kind) return;
+    const int g = g0 + k;
     const uint64_t t = (uint64_t)(*V.step + s_off);
     const int tid = threadIdx.x;
-    const int slot = V.slot_of[w];
-    const int iE = slot % V.nE, ipH = (slot / V.nE) % V.npH, iT = slot / (V.nE * V.npH);
-    const double E = V.gE[iE], pH = V.gpH[ipH], T = V.gT[iT];
-    const double kT = kBoltzmann * T;
     const uint32_t purpose = (kind == CPH_SITE_PH) ? kRngMcPh : kRngMcRedox;
     __shared__ Real mx[kMaxSiteAtoms], my[kMaxSiteAtoms], mz[kMaxSiteAtoms], mR[kMaxSiteAtoms],
         mdq[kMaxSiteAtoms];
     __shared__ int mat[kMaxSiteAtoms];
-    __shared__ int sh_a, sh_b, sh_acc;
-    __shared__ double sh_lnu;
+    __shared__ int sh_b;
     __shared__ long long redl[kMcThreads / 32];
     __shared__ double redd[kMcThreads / 32];
     const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
     const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
     const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
     const bool salt = V.kappa > 0;
-    for (int k = 0; k < ns; ++k) {
-        const int g = g0 + k;
-        if (V.site_kind[g] != kind) {
-            if (clear_others && tid == 0) V.mc_rec[so + k].walker = -1;
-            continue;
-        }
-        const int nat = V.site_nat[g], nst = V.site_nst[g], ao = V.site_aoff[g];
-        const int qo = V.site_qoff[g], no = V.site_noff[g];
-        if (tid == 0) {
-            const U4 u = draw(V.seed, (uint32_t)k, (uint32_t)w, t, purpose);
-            const int a = V.site_state[so + k];
-            const int jj = (int)floor(unit_open(u.a) * (double)(nst - 1));
-            sh_a = a;
-            sh_b = jj < a ? jj : jj + 1;
-            sh_lnu = log(unit_open(u.b));
-        }
-        __syncthreads();
-        const int a = sh_a, b = sh_b;
-        for (int m = tid; m < nat; m += kMcThreads) {
-            const int at = V.site_atoms[ao + m];
-            mat[m] = at;
-            mx[m] = Real(V.x[3 * (A + at)] - cx);
-            my[m] = Real(V.x[3 * (A + at) + 1] - cy);
-            mz[m] = Real(V.x[3 * (A + at) + 2] - cz);
-            mR[m] = Real(V.R[A + at]);
-            mdq[m] = Real((V.site_q[qo + b * nat + m] - V.q[A + at]) * V.sqrt_k);
-        }
-        __syncthreads();
-        Acc lin = 0;
-        for (int j = tid; j < N; j += kMcThreads) {
-            const Real xj = Real(V.x[3 * (A + j)] - cx), yj = Real(V.x[3 * (A + j) + 1] - cy),
-                       zj = Real(V.x[3 * (A + j) + 2] - cz);
-            const Real qj = Real(V.q[A + j]) * sqk;
-            const Real Rj = Real(V.R[A + j]);
-            Real part = 0;
-            for (int m = 0; m < nat; ++m) {
-                if (mat[m] == j) {
-                    const Real ts = salt ? iei - ieo * Pr::expm(kap * mR[m]) : tau;
-                    part += mdq[m] * qj * (-ts / mR[m]);
-                } else {
-                    const Real dx = mx[m] - xj, dy = my[m] - yj, dz = mz[m] - zj;
-                    const Real r2 = dx * dx + dy * dy + dz * dz;
-                    const Real rinv = Pr::rsqrt(r2);
-                    const Real D = Real(0.25) * r2 / (mR[m] * Rj);
-                    const Real fi = Pr::rsqrt(r2 + mR[m] * Rj * Pr::expm(D));
-                    const Real tf = salt ? iei - ieo * Pr::expm(kap / fi) : tau;
-                    part += mdq[m] * qj * (iei * rinv - tf * fi);
-                }
+    const int nat = V.site_nat[g], nst = V.site_nst[g], ao = V.site_aoff[g], qo = V.site_qoff[g];
+    if (tid == 0) {
+        const U4 u = draw(V.seed, (uint32_t)k, (uint32_t)w, t, purpose);
+        const int a = V.site_state[so + k];
+        const int jj = (int)floor(unit_open(u.a) * (double)(nst - 1));
+        const int b = jj < a ? jj : jj + 1;
+        sh_b = b;
+        V.mc_from[so + k] = a;
+        V.mc_to[so + k] = b;
+        V.mc_lnu[so + k] = log(unit_open(u.b));
+    }
+    __syncthreads();
+    const int b = sh_b;
+    for (int m = tid; m < nat; m += kMcThreads) {
+        const int at = V.site_atoms[ao + m];
+        mat[m] = at;
+        mx[m] = Real(V.x[3 * (A + at)] - cx);
+        my[m] = Real(V.x[3 * (A + at) + 1] - cy);
+        mz[m] = Real(V.x[3 * (A + at) + 2] - cz);
+        mR[m] = Real(V.R[A + at]);
+        mdq[m] = Real((V.site_q[qo + b * nat + m] - V.q[A + at]) * V.sqrt_k);
+    }
+    __syncthreads();
+    Acc lin = 0;
+    for (int j = tid; j < N; j += kMcThreads) {
+        const Real xj = Real(V.x[3 * (A + j)] - cx), yj = Real(V.x[3 * (A + j) + 1] - cy),
+                   zj = Real(V.x[3 * (A + j) + 2] - cz);
+        const Real qj = Real(V.q[A + j]) * sqk;
+        const Real Rj = Real(V.R[A + j]);
+        Real part = 0;
+        for (int m = 0; m < nat; ++m) {
+            if (mat[m] == j) {
+                const Real ts = salt ? iei - ieo * Pr::expm(kap * mR[m]) : tau;
+                part += mdq[m] * qj * (-ts / mR[m]);
+            } else {
+                part += mdq[m] * qj * mc_pair<Real>(mx[m] - xj, my[m] - yj, mz[m] - zj, mR[m], Rj, false, iei, tau,
+                                                    kap, ieo, salt);
             }
-            Pr::add(lin, part, Real(kScaleE));
         }
-        double corr = 0.0;
-        for (int m = tid; m < nat; m += kMcThreads) {
-            const int at = mat[m];
+        Pr::add(lin, part, Real(kScaleE));
+    }
+    // FP64: the Coulomb part of excluded pairs (index nat * nat + m) and the
+    // quadratic term's pairs (index m * nat + n)
+    double corr = 0.0;
+    for (int idx = tid; idx < nat * nat + nat; idx += kMcThreads) {
+        if (idx >= nat * nat) {
+            const int m = idx - nat * nat, at = mat[m];
             const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
             const double xm0 = V.x[3 * (A + at)], xm1 = V.x[3 * (A + at) + 1], xm2 = V.x[3 * (A + at) + 2];
             for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e) {
@@ -120,44 +138,126 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
                 const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                 corr -= dqm * V.q[A + j] * kCoulomb * V.inv_eps_in / r;
             }
-            const double Rm = V.R[A + at];
-            for (int n = 0; n < nat; ++n) {
-                const int an = V.site_atoms[ao + n];
-                const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
-                if (n == m) {
-                    corr += 0.5 * dqm * dqn * (-salt_tau(Rm, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / Rm);
-                    continue;
+            continue;
+        }
+        const int m = idx / nat, n = idx % nat, at = mat[m], an = mat[n];
+        const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
+        const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
+        const double Rm = V.R[A + at];
+        if (n == m) {
+            corr += 0.5 * dqm * dqn * (-salt_tau(Rm, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / Rm);
+            continue;
+        }
+        const double d0 = V.x[3 * (A + at)] - V.x[3 * (A + an)], d1 = V.x[3 * (A + at) + 1] - V.x[3 * (A + an) + 1],
+                     d2 = V.x[3 * (A + at) + 2] - V.x[3 * (A + an) + 2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double RR = Rm * V.R[A + an];
+        const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+        double amn = -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / f;
+        if (!mc_excluded(V, P, at, an)) amn += kCoulomb * V.inv_eps_in / sqrt(r2);
+        corr += 0.5 * dqm * dqn * amn;
+    }
+    // block reduction (fixed order)
+    long long lv = 0;
+    double tot_d = corr;
+    if (sizeof(Real) == 4) lv = (long long)lin;
+    else tot_d += (double)lin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lv += __shfl_down_sync(0xffffffffu, lv, o);
+        tot_d += __shfl_down_sync(0xffffffffu, tot_d, o);
+    }
+    if ((tid & 31) == 0) {
+        redl[tid >> 5] = lv;
+        redd[tid >> 5] = tot_d;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long L = 0;
+        double D = 0.0;
+        for (int q = 0; q < kMcThreads / 32; ++q) {
+            L += redl[q];
+            D += redd[q];
+        }
+        V.mc_du0[so + k] = (double)L / kScaleE + D;
+    }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(kMcThreads) k_mc_sweep(View V, int kind, int clear_others, int w_begin) {
+    using Pr = Prec<Real>;
+    using Acc = typename Pr::Acc;
+    const int w = w_begin + blockIdx.x;
+    const int s = V.w_sys[w], A = V.w_off[w], P = V.sys_poff[s];
+    const int g0 = V.sys_site_off[s], ns = V.sys_site_off[s + 1] - g0, so = V.w_site_off[w];
+    const int tid = threadIdx.x;
+    const int slot = V.slot_of[w];
+    const int iE = slot % V.nE, ipH = (slot / V.nE) % V.npH, iT = slot / (V.nE * V.npH);
+    const double E = V.gE[iE], pH = V.gpH[ipH], T = V.gT[iT];
+    const double kT = kBoltzmann * T;
+    __shared__ Real mx[kMaxSiteAtoms], my[kMaxSiteAtoms], mz[kMaxSiteAtoms], mR[kMaxSiteAtoms],
+        mdq[kMaxSiteAtoms];
+    __shared__ int mat[kMaxSiteAtoms];
+    __shared__ int sh_acc;
+    __shared__ long long redl[kMcThreads / 32];
+    __shared__ double redd[kMcThreads / 32];
+    const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
+    const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
+    const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
+    const bool salt = V.kappa > 0;
+    int n_taken = 0; // sites of this sweep accepted so far (uniform across the CTA)
+    for (int k = 0; k < ns; ++k) {
+        const int g = g0 + k;
+        if (V.site_kind[g] != kind) {
+            if (clear_others && tid == 0) V.mc_rec[so + k].walker = -1;
+            continue;
+        }
+        const int nat = V.site_nat[g], ao = V.site_aoff[g], qo = V.site_qoff[g], no = V.site_noff[g];
+        const int a = V.mc_from[so + k], b = V.mc_to[so + k];
+        Acc cross = 0;
+        if (n_taken > 0) {
+            __syncthreads(); // the previous site's staging is no longer read
+            for (int m = tid; m < nat; m += kMcThreads) {
+                const int at = V.site_atoms[ao + m];
+                mat[m] = at;
+                mx[m] = Real(V.x[3 * (A + at)] - cx);
+                my[m] = Real(V.x[3 * (A + at) + 1] - cy);
+                mz[m] = Real(V.x[3 * (A + at) + 2] - cz);
+                mR[m] = Real(V.R[A + at]);
+                mdq[m] = Real((V.site_q[qo + b * nat + m] - V.site_q[qo + a * nat + m]) * V.sqrt_k);
+            }
+            __syncthreads();
+            // dq^T A dq' over the accepted earlier sites k2, pairs (m, n) split over threads
+            for (int k2 = 0; k2 < k; ++k2) {
+                const int g2 = g0 + k2;
+                if (V.site_kind[g2] != kind || !V.mc_take[so + k2]) continue;
+                const int nat2 = V.site_nat[g2], ao2 = V.site_aoff[g2], qo2 = V.site_qoff[g2];
+                const int a2 = V.mc_from[so + k2], b2 = V.mc_to[so + k2];
+                Real part = 0;
+                for (int idx = tid; idx < nat * nat2; idx += kMcThreads) {
+                    const int m = idx / nat2, n = idx % nat2;
+                    const int an = V.site_atoms[ao2 + n];
+                    const Real dqn = Real(V.site_q[qo2 + b2 * nat2 + n] - V.site_q[qo2 + a2 * nat2 + n]) * sqk;
+                    const Real xn = Real(V.x[3 * (A + an)] - cx), yn = Real(V.x[3 * (A + an) + 1] - cy),
+                               zn = Real(V.x[3 * (A + an) + 2] - cz);
+                    part += mdq[m] * dqn * mc_pair<Real>(mx[m] - xn, my[m] - yn, mz[m] - zn, mR[m], Real(V.R[A + an]),
+                                                         mc_excluded(V, P, mat[m], an), iei, tau, kap, ieo, salt);
                 }
-                const double d0 = xm0 - V.x[3 * (A + an)], d1 = xm1 - V.x[3 * (A + an) + 1],
-                             d2 = xm2 - V.x[3 * (A + an) + 2];
-                const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                const double RR = Rm * V.R[A + an];
-                const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
-                double amn = -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / f;
-                bool ex = false;
-                for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e)
-                    if (V.excl_j[e] == an) ex = true;
-                if (!ex) amn += kCoulomb * V.inv_eps_in / sqrt(r2);
-                corr += 0.5 * dqm * dqn * amn;
+                Pr::add(cross, part, Real(kScaleE));
             }
         }
-        // block reduction (fixed order)
         long long lv = 0;
-        double lin_d = 0.0;
-        if (sizeof(Real) == 4) {
-            lv = (long long)lin;
-        } else {
-            lin_d = (double)lin;
-        }
-        double tot_d = lin_d + corr;
+        double dv = 0.0;
+        if (sizeof(Real) == 4) lv = (long long)cross;
+        else dv = (double)cross;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lv += __shfl_down_sync(0xffffffffu, lv, o);
-            tot_d += __shfl_down_sync(0xffffffffu, tot_d, o);
+            dv += __shfl_down_sync(0xffffffffu, dv, o);
         }
         if ((tid & 31) == 0) {
             redl[tid >> 5] = lv;
-            redd[tid >> 5] = tot_d;
+            redd[tid >> 5] = dv;
         }
         __syncthreads();
         if (tid == 0) {
@@ -167,14 +267,15 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
                 L += redl[q];
                 D += redd[q];
             }
-            const double dU = (double)L / kScaleE + D;
+            const double lnu = V.mc_lnu[so + k];
+            const double dU = V.mc_du0[so + k] + ((double)L / kScaleE + D);
             double dG = dU - (V.site_uref[no + b] - V.site_uref[no + a]);
             if (kind == CPH_SITE_PH)
                 dG += kT * kLn10 * (double)(V.site_np[no + b] - V.site_np[no + a]) * (pH - V.site_ref[g]);
             else
                 dG += kFaraday * (double)(V.site_ne[no + b] - V.site_ne[no + a]) * (E - V.site_ref[g]);
             const double x = -dG / kT;
-            const int acc = sh_lnu < x ? 1 : 0;
+            const int acc = lnu < x ? 1 : 0;
             cph_mc_record rec;
             rec.walker = w;
             rec.site = k;
@@ -184,8 +285,9 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
             rec.pad_ = 0;
             rec.dU = dU;
             rec.x = x;
-            rec.lnu = sh_lnu;
+            rec.lnu = lnu;
             V.mc_rec[so + k] = rec;
+            V.mc_take[so + k] = acc;
             if (acc) V.site_state[so + k] = b;
             sh_acc = acc;
             const int base = (kind == CPH_SITE_PH) ? 6 : 8;
@@ -194,9 +296,10 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
         }
         __syncthreads();
         if (sh_acc) {
-            for (int m = tid; m < nat; m += kMcThreads) V.q[A + mat[m]] = V.site_q[qo + b * nat + m];
+            for (int m = tid; m < nat; m += kMcThreads)
+                V.q[A + V.site_atoms[ao + m]] = V.site_q[qo + b * nat + m];
+            ++n_taken;
         }
-        __syncthreads();
     }
 }
 
@@ -206,18 +309,22 @@ __global__ void __launch_bounds__(kMcThreads) k_mc(View V, int kind, int s_off, 
 // (slot, site) row and every (walker, slot) cell has one writer per step:
 // plain read-modify-writes, exact and in a fixed order.
 // =====================================================================
-__global__ void k_observe(View V) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= V.W) return;
+constexpr int kObsThreads = 64;
+
+// one CTA per walker, threads over its sites
+__global__ void __launch_bounds__(kObsThreads) k_observe(View V) {
+    const int w = blockIdx.x;
     const int s = V.slot_of[w];
-    V.visits[(long long)w * V.W + s] += 1;
+    if (threadIdx.x == 0) {
+        V.visits[(long long)w * V.W + s] += 1;
+        if (w == 0) *V.n_obs += 1;
+    }
     // the walker at slot s belongs to the system of the walker that started
     // there, so slot s's rows are laid out like walker s's sites
     const int ws0 = V.w_site_off[w], n = V.w_site_off[w + 1] - ws0;
     const long long row0 = V.w_site_off[s];
-    for (int k = 0; k < n; ++k)
+    for (int k = threadIdx.x; k < n; k += kObsThreads)
         V.occ[(row0 + k) * CPH_MAX_STATES + V.site_state[ws0 + k]] += 1;
-    if (w == 0) *V.n_obs += 1;
 }
 
 // =====================================================================
@@ -448,6 +555,7 @@ struct cph_engine {
     SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
     int n_sym = 0;
     int sym_chunk = kSymChunk;         // j-tiles per symmetric work item (autotuned)
+    int max_sites = 0;                 // largest site count of any system
     int max_terms = 0;                 // largest bonds + angles count of any system
     std::vector<int> sym_w_off, h_sys_sst_off;
     int ex_cap = 0;
@@ -604,19 +712,22 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
     for (int kind : {CPH_SITE_PH, CPH_SITE_REDOX}) {
         const int bit = (kind == CPH_SITE_PH) ? CPH_MC_PH : CPH_MC_REDOX;
         if (!(kinds & bit)) continue;
+        if (E->max_sites <= 0) break;
+        const bool f32 = E->precision == CPH_PREC_FP32;
         if (E->launch_mode == 0) {
-            if (E->precision == CPH_PREC_FP32)
-                k_mc<float><<<W, kMcThreads, 0, st>>>(E->V, kind, s_off, first, 0);
-            else
-                k_mc<double><<<W, kMcThreads, 0, st>>>(E->V, kind, s_off, first, 0);
+            const dim3 g1(E->max_sites, W);
+            if (f32) k_mc_site<float><<<g1, kMcThreads, 0, st>>>(E->V, kind, s_off, 0);
+            else k_mc_site<double><<<g1, kMcThreads, 0, st>>>(E->V, kind, s_off, 0);
+            if (f32) k_mc_sweep<float><<<W, kMcThreads, 0, st>>>(E->V, kind, first, 0);
+            else k_mc_sweep<double><<<W, kMcThreads, 0, st>>>(E->V, kind, first, 0);
         } else {
             TRY(fan_out(E, st));
             for (int w = 0; w < W; ++w) {
                 cudaStream_t s = lane_stream(E, w, st);
-                if (E->precision == CPH_PREC_FP32)
-                    k_mc<float><<<1, kMcThreads, 0, s>>>(E->V, kind, s_off, first, w);
-                else
-                    k_mc<double><<<1, kMcThreads, 0, s>>>(E->V, kind, s_off, first, w);
+                if (f32) k_mc_site<float><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
+                else k_mc_site<double><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
+                if (f32) k_mc_sweep<float><<<1, kMcThreads, 0, s>>>(E->V, kind, first, w);
+                else k_mc_sweep<double><<<1, kMcThreads, 0, s>>>(E->V, kind, first, w);
             }
             TRY(fan_in(E, st));
         }
@@ -762,8 +873,7 @@ int launch_exchange(cph_engine* E, int dim, int s_off, cudaStream_t st) {
 }
 
 int launch_observe(cph_engine* E, cudaStream_t st) {
-    const int bs = 128;
-    k_observe<<<(E->V.W + bs - 1) / bs, bs, 0, st>>>(E->V);
+    k_observe<<<E->V.W, kObsThreads, 0, st>>>(E->V);
     CK(cudaGetLastError());
     return CPH_OK;
 }
@@ -1215,6 +1325,12 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(upload(E, ang_ijk, &d)); V.ang_ijk = d;
     TRY(upload(E, ang_k, &dd)); V.ang_k = dd;
     TRY(upload(E, ang_t0, &dd)); V.ang_t0 = dd;
+    {
+        std::vector<double2> cs0(ang_t0.size());
+        for (size_t a = 0; a < ang_t0.size(); ++a) cs0[a] = make_double2(std::cos(ang_t0[a]), std::sin(ang_t0[a]));
+        double2* dcs;
+        TRY(upload(E, cs0, &dcs)); V.ang_cs0 = dcs;
+    }
     TRY(upload(E, sys_bond_off, &d)); V.sys_bond_off = d;
     TRY(upload(E, sys_ang_off, &d)); V.sys_ang_off = d;
     {
@@ -1227,7 +1343,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         }
         long long* dtf;
         TRY(upload(E, tf_off, &dtf)); V.w_tf_off = dtf;
-        TRY(alloc0(E, (size_t)tf_off[W], &dd)); V.tforce = dd;
+        float* dtfb;
+        TRY(alloc0(E, (size_t)tf_off[W], &dtfb)); V.tforce = dtfb;
     }
     TRY(upload(E, mt_off, &d)); V.mt_off = d;
     TRY(upload(E, mt_list, &d)); V.mt_list = d;
@@ -1287,6 +1404,18 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         dm = (cph_mc_record*)pm;
     }
     V.mc_rec = dm;
+    {
+        // per (walker, site) scratch of the two-kernel MC sweep
+        const size_t nsw = (size_t)w_site_off[W];
+        int* di2;
+        double* dd2;
+        TRY(alloc0(E, nsw, &di2)); V.mc_from = di2;
+        TRY(alloc0(E, nsw, &di2)); V.mc_to = di2;
+        TRY(alloc0(E, nsw, &di2)); V.mc_take = di2;
+        TRY(alloc0(E, nsw, &dd2)); V.mc_lnu = dd2;
+        TRY(alloc0(E, nsw, &dd2)); V.mc_du0 = dd2;
+        for (int s = 0; s < n_sys; ++s) E->max_sites = std::max(E->max_sites, sys_site_off[s + 1] - sys_site_off[s]);
+    }
     E->ex_cap = W; // pairs per attempt <= slots / 2
     {
         void* pe = nullptr;
@@ -1344,6 +1473,19 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.offset = p->gb.offset;
     V.dt = p->dt;
     V.gamma_ln = p->gamma_ln;
+    V.lg_c1 = 1.0 - 0.5 * p->gamma_ln * p->dt;
+    V.lg_c2 = 1.0 / (1.0 + 0.5 * p->gamma_ln * p->dt);
+    {
+        std::vector<double> im(mass.size()), sf(mass.size()), sqT(grid->nT);
+        for (size_t a = 0; a < mass.size(); ++a) {
+            im[a] = p->dt * kAccel / mass[a];
+            sf[a] = std::sqrt(2.0 * p->gamma_ln * kBoltzmann * kAccel * p->dt / mass[a]);
+        }
+        for (int k = 0; k < grid->nT; ++k) sqT[k] = std::sqrt(grid->T[k]);
+        TRY(upload(E, im, &dd)); V.lg_im = dd;
+        TRY(upload(E, sf, &dd)); V.lg_sf = dd;
+        TRY(upload(E, sqT, &dd)); V.lg_sqT = dd;
+    }
     {
         double smax = 0.0, rtmax = 0.0;
         for (double v : sc) smax = std::max(smax, v);

@@ -45,9 +45,10 @@ struct View {
     const double *bond_k, *bond_r0;
     const int *ang_off, *ang_idx, *ang_ijk;
     const int *sys_bond_off, *sys_ang_off; // per-system ranges of the bond / angle arrays
-    const long long* w_tf_off;             // per-walker offset into tforce (doubles)
-    double* tforce;                        // per-term bonded forces: bonds [2][3], angles [3][3]
+    const long long* w_tf_off;             // per-walker offset into tforce (floats)
+    float* tforce;                         // per-term bonded forces: bonds [2][3], angles [3][3]
     const double *ang_k, *ang_t0;
+    const double2* ang_cs0;                // (cos theta0, sin theta0) per angle
     const int *mt_off, *mt_list;
     // sites (global site index g = sys_site_off[s] + k)
     const int *site_kind, *site_nat, *site_aoff, *site_atoms, *site_nst, *site_qoff, *site_noff;
@@ -66,6 +67,10 @@ struct View {
     int* ex_state; // [0] exchange events, [1..3] attempts along E, pH, T
     long long* stats; // [10]
     cph_mc_record* mc_rec;
+    // MC sweep scratch per (walker, site): proposal, ln u, dU at the sweep's
+    // start charges, and whether the sweep accepted it
+    int *mc_from, *mc_to, *mc_take;
+    double *mc_lnu, *mc_du0;
     cph_exchange_record* ex_rec;
     int* ex_n;
     // sampling observables: per (slot, site) state counts, per (walker, slot) visits, samples
@@ -76,6 +81,10 @@ struct View {
     int order[3];
     // parameters
     double tau, inv_eps_in, sqrt_k, alpha, beta, gamma, offset, dt, gamma_ln;
+    // Langevin factors: (1 - g dt/2), 1 / (1 + g dt/2), per system atom
+    // dt A / m and sqrt(2 g kB A dt / m), per temperature sqrt(T)
+    double lg_c1, lg_c2;
+    const double *lg_im, *lg_sf, *lg_sqT;
     // salt screening: kappa (1/A), 1/eps_out, and the factor the finishing
     // kernels apply to pair sums (tau without salt; 1 with salt, whose pair
     // kernels carry tau(f) per pair)

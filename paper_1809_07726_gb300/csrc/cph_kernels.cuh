@@ -559,17 +559,17 @@ __global__ void k_langevin(View V, int s_off, int a0, int n) {
     const int P = V.sys_poff[V.w_sys[w]];
     const uint64_t t = (uint64_t)(*V.step + s_off);
     const int slot = V.slot_of[w];
-    const double T = V.gT[slot / (V.nE * V.npH)];
     Real z[3];
     normals3<Real>(V.seed, (uint32_t)li, (uint32_t)w, t, z);
-    const double m = V.mass[P + li];
-    const double sd = sqrt(2.0 * V.gamma_ln * kBoltzmann * T * kAccel * V.dt / m);
-    const double c1 = 1.0 - 0.5 * V.gamma_ln * V.dt, c2 = 1.0 / (1.0 + 0.5 * V.gamma_ln * V.dt);
+    // per-atom factors dt A / m and sqrt(2 g kB A dt / m), and sqrt(T) per
+    // slot, are set up once: no FP64 division or square root per step
+    const double sd = V.lg_sqT[slot / (V.nE * V.npH)] * V.lg_sf[P + li];
+    const double im = V.lg_im[P + li], c1 = V.lg_c1, c2 = V.lg_c2;
     const double vs = V.vscale[w];
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double vn = (c1 * (V.v[3 * a + c] * vs) + V.dt * kAccel * V.F[3 * a + c] / m + sd * (double)z[c]) * c2;
+        const double vn = (c1 * (V.v[3 * a + c] * vs) + im * V.F[3 * a + c] + sd * (double)z[c]) * c2;
         V.v[3 * a + c] = vn;
         if (V.xprev) V.xprev[3 * a + c] = V.x[3 * a + c]; // SHAKE's reference bond vectors
         const double xn = V.x[3 * a + c] + V.dt * vn;

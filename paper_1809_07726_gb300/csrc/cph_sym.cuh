@@ -632,22 +632,29 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
     const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0;
     const int a0 = V.sys_ang_off[s], na = V.sys_ang_off[s + 1] - a0;
     const int t = blockIdx.x * kBondedThreads + threadIdx.x;
-    double* buf = V.tforce + V.w_tf_off[w];
+    float* buf = V.tforce + V.w_tf_off[w];
     const double* x = V.x;
     double eb = 0.0, ea = 0.0;
+    // FP64 only where a difference of nearly equal numbers decides the result
+    // (r^2 - r0^2; the sine and cosine of theta - theta0); FP32 elsewhere, so
+    // that the few FP64 units of the chip are not the bound.
     if (t < nb) {
         const int b = b0 + t;
         const int i = V.bond_ij[2 * b], j = V.bond_ij[2 * b + 1];
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + i) + c] - x[3 * (A + j) + c];
-        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const double dr = r - V.bond_r0[b];
-        const double g = 2.0 * V.bond_k[b] * dr / r;
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double r0 = V.bond_r0[b];
+        const float r = sqrtf((float)r2);
+        const float dr = (float)(r2 - r0 * r0) / (r + (float)r0); // r - r0 at FP32 relative precision
+        const float kb = (float)V.bond_k[b];
+        const float g = 2.f * kb * dr / r;
         for (int c = 0; c < 3; ++c) {
-            buf[6 * t + c] = -g * d[c];
-            buf[6 * t + 3 + c] = g * d[c];
+            const float f = g * (float)d[c];
+            buf[6 * t + c] = -f;
+            buf[6 * t + 3 + c] = f;
         }
-        eb = V.bond_k[b] * dr * dr;
+        eb = (double)(kb * dr * dr);
     } else if (t < nb + na) {
         const int la = t - nb, a = a0 + la;
         const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
@@ -656,22 +663,38 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
             u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
             v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
         }
-        const double ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        const double rv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (ru * rv);
-        cs = fmin(1.0, fmax(-1.0, cs));
-        const double th = acos(cs);
-        const double dth = th - V.ang_t0[a];
-        const double k = -2.0 * V.ang_k[a] * dth / sqrt(fmax(1e-300, 1.0 - cs * cs)); // dE/dcos
-        double* o = buf + 6 * (size_t)nb + 9 * (size_t)la;
+        // |u||v| cos(theta) and |u||v| sin(theta) in FP64 (the norm of the cross
+        // product by an FP32 reciprocal square root and one Newton step)
+        const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                     cz = u[0] * v[1] - u[1] * v[0];
+        const double w2 = cx * cx + cy * cy + cz * cz;
+        const double y = (double)rsqrtf(fmaxf((float)w2, 1e-30f));
+        double wn = w2 * y;
+        wn += 0.5 * (w2 - wn * wn) * y;
+        // theta - theta0 = atan2(sin(theta - theta0), cos(theta - theta0))
+        const double2 cs0 = V.ang_cs0[a];
+        const float dth = atan2f((float)(wn * cs0.x - uv * cs0.y), (float)(uv * cs0.x + wn * cs0.y));
+        const float ka = (float)V.ang_k[a];
+        float uf[3], vf[3];
         for (int c = 0; c < 3; ++c) {
-            const double gi = k * (v[c] / (ru * rv) - cs * u[c] / (ru * ru));
-            const double gk = k * (u[c] / (ru * rv) - cs * v[c] / (rv * rv));
+            uf[c] = (float)u[c];
+            vf[c] = (float)v[c];
+        }
+        const float ru2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+        const float rv2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+        const float iuv = rsqrtf(ru2 * rv2);                     // 1 / (|u| |v|)
+        const float cs = (float)uv * iuv, sn = fmaxf((float)wn * iuv, 1e-20f);
+        const float k = -2.f * ka * dth / sn;                     // dE/dcos(theta)
+        float* o = buf + 6 * (size_t)nb + 9 * (size_t)la;
+        for (int c = 0; c < 3; ++c) {
+            const float gi = k * (vf[c] * iuv - cs * uf[c] / ru2);
+            const float gk = k * (uf[c] * iuv - cs * vf[c] / rv2);
             o[c] = -gi;
             o[3 + c] = gi + gk;
             o[6 + c] = -gk;
         }
-        ea = V.ang_k[a] * dth * dth;
+        ea = (double)(ka * dth * dth);
     }
     if (ENERGY) {
 #pragma unroll
@@ -705,18 +728,18 @@ __global__ void k_final_forces(View V, int a0, int n) {
     const int A = V.w_off[w], li = a - A, P = V.sys_poff[s];
     double F[3] = {(double)V.Ffix[3 * a] / kScaleE, (double)V.Ffix[3 * a + 1] / kScaleE,
                    (double)V.Ffix[3 * a + 2] / kScaleE};
-    const double* buf = V.tforce + V.w_tf_off[w];
+    const float* buf = V.tforce + V.w_tf_off[w];
     const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0, an0 = V.sys_ang_off[s];
     for (int e = V.bond_off[P + li]; e < V.bond_off[P + li + 1]; ++e) {
         const int b = V.bond_idx[e];
         const int role = (V.bond_ij[2 * b] == li) ? 0 : 1;
-        const double* o = buf + 6 * (b - b0) + 3 * role;
+        const float* o = buf + 6 * (b - b0) + 3 * role;
         for (int c = 0; c < 3; ++c) F[c] += o[c];
     }
     for (int e = V.ang_off[P + li]; e < V.ang_off[P + li + 1]; ++e) {
         const int ag = V.ang_idx[e];
         const int role = (V.ang_ijk[3 * ag] == li) ? 0 : ((V.ang_ijk[3 * ag + 1] == li) ? 1 : 2);
-        const double* o = buf + 6 * (size_t)nb + 9 * (size_t)(ag - an0) + 3 * role;
+        const float* o = buf + 6 * (size_t)nb + 9 * (size_t)(ag - an0) + 3 * role;
         for (int c = 0; c < 3; ++c) F[c] += o[c];
     }
     V.F[3 * a] = F[0];
