@@ -113,6 +113,16 @@ def test_rejects_bad_precision_and_timestep(L, small):
     assert rc == cphremd.E_INVALID
 
 
+def test_rejects_site_beyond_64_atoms(L):
+    s = synth.make_system(200, 43, n_ph=1, ph_atoms=(65, 65), n_redox=0)
+    grid = synth.Grid(np.array([0.0]), np.array([7.0]), np.array([300.0]), np.zeros(1, np.int32))
+    rc, out, msg = _init(L, [s], grid)
+    assert rc == cphremd.E_INVALID and not out.value and "n_atoms must be 1..64" in msg
+    s64 = synth.make_system(200, 43, n_ph=1, ph_atoms=(64, 64), n_redox=0)
+    rc, out, _ = _init(L, [s64], grid)
+    assert rc != cphremd.E_INVALID  # the limit itself is accepted (no GPU here: a CUDA error)
+
+
 @pytest.mark.parametrize("rgbmax", [-1.0, float("nan"), float("inf")])
 def test_rejects_bad_born_radius_cutoff(L, small, rgbmax):
     grid = synth.Grid(np.array([0.0]), np.array([7.0]), np.array([300.0]), np.zeros(1, np.int32))
