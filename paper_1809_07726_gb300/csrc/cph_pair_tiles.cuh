@@ -14,7 +14,8 @@ constexpr int kTileJ = 32; // atoms per j-tile
 // psi_i (i-side sum ah) and H(r, rt_j, s_i) for psi_j (partner sum jh, which
 // moves one lane per step).  In the far regime H = P(y) s^3 / r^4 with
 // y = s^2 / r^2 (P the fitted series), so s^2 and s^3 are staged and 1/r^4
-// serves both directions.  Bit jj of sk[u][h] marks a pair of i atom u and
+// serves both directions as the weight of a fused accumulate (1 for the
+// closed forms, 0 for pairs that are not counted).  Bit jj of sk[u][h] marks a pair of i atom u and
 // partner jj of tile h that is not counted.
 struct BoI2 {
     float2 x, y, z, s2, s3; // the i atom's value in both halves
@@ -82,7 +83,7 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
     for (int k = 0; k < kTileJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 s2j = make_float2(B.z, B.w), s3j = make_float2(C.x, C.y);
-        float2 r2[2], rinv[2], hi[2], hj[2];
+        float2 r2[2], rinv[2], hi[2], hj[2], wt[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
@@ -96,15 +97,12 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
             }
             rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
             const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
-            const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
-            hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), __fmul2_rn(s3j, rinv4));
-            hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), __fmul2_rn(I[u].s3, rinv4));
+            wt[u] = __fmul2_rn(rinv2, rinv2); // r^-4, the weight of both far terms
+            hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), s3j);
+            hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), I[u].s3);
             if (CUT) { // beyond rc + s_max nothing descreens
-                const bool o0 = r2[u].x >= band.rout2, o1 = r2[u].y >= band.rout2;
-                hi[u].x = o0 ? 0.f : hi[u].x;
-                hj[u].x = o0 ? 0.f : hj[u].x;
-                hi[u].y = o1 ? 0.f : hi[u].y;
-                hj[u].y = o1 ? 0.f : hj[u].y;
+                wt[u].x = r2[u].x >= band.rout2 ? 0.f : wt[u].x;
+                wt[u].y = r2[u].y >= band.rout2 ? 0.f : wt[u].y;
             }
         }
         // closed forms only where some lane has such a pair (rare)
@@ -119,12 +117,14 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
                                                band.rc);
                     hi[u].x = h.x;
                     hj[u].x = h.y;
+                    wt[u].x = 1.f;
                 }
                 if (band_near<CUT>(r2[u].y, band)) {
                     const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w,
                                                band.rc);
                     hi[u].y = h.x;
                     hj[u].y = h.y;
+                    wt[u].y = 1.f;
                 }
             }
         }
@@ -132,14 +132,11 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
         for (int u = 0; u < 2; ++u) {
             if (MASKED) {
                 const int jj = (lane + k) & (kTileJ - 1);
-                const bool s0 = (sk[u][0] >> jj) & 1u, s1 = (sk[u][1] >> jj) & 1u;
-                hi[u].x = s0 ? 0.f : hi[u].x;
-                hj[u].x = s0 ? 0.f : hj[u].x;
-                hi[u].y = s1 ? 0.f : hi[u].y;
-                hj[u].y = s1 ? 0.f : hj[u].y;
+                wt[u].x = ((sk[u][0] >> jj) & 1u) ? 0.f : wt[u].x;
+                wt[u].y = ((sk[u][1] >> jj) & 1u) ? 0.f : wt[u].y;
             }
-            ah[u] = __fadd2_rn(ah[u], hi[u]);
-            jh = __fadd2_rn(jh, hj[u]);
+            ah[u] = __ffma2_rn(hi[u], wt[u], ah[u]);
+            jh = __ffma2_rn(hj[u], wt[u], jh);
         }
         jh.x = __shfl_sync(0xffffffffu, jh.x, src);
         jh.y = __shfl_sync(0xffffffffu, jh.y, src);
