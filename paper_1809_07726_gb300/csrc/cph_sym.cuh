@@ -750,11 +750,133 @@ __global__ void k_final_forces(View V, int a0, int n) {
 }
 
 // ========================================================= Born radii
-// Tile arithmetic (BoI2, BoJs, born_tile) in cph_pair_tiles.cuh.
+// Tile arithmetic (BoI2, BoJs, born_tile) in cph_pair_tiles.cuh.  The engine's
+// pass keeps the closed forms out of the tile loop: a pair inside r_far (or
+// in the cutoff band) gets weight 0 there and is queued, per warp, as
+// (tile pair, half, partner, i slot); the warp evaluates its queue 32 pairs
+// at a time with every lane busy (once 64 are pending, and at the end of each
+// staged group), adding both integrals of each queued pair in int64 fixed
+// point to shared sums (order independent).  A flush recomputes r^2 with the
+// tile's own arithmetic, so the near/far decision is the same.
+constexpr int kNearQ = 192; // queue entries per warp: flushed at >= 64; a step adds <= 128
+
+struct BoNear {
+    uint32_t q[kSymThreads / 32][kNearQ]; // lane | u << 5 | partner << 6 | half << 11 | pair << 12
+    float4 ix[kSymThreads / 32][64];      // the warp's i atoms (x, y, z, s), slot u * 32 + lane
+    float2 it[kSymThreads / 32][64];      // (rt, 1/rt)
+    long long ihx[kSymThreads / 32][64];  // i-side sums of queued pairs (2^40 fixed point)
+    long long jhx[kSymG][kSymJ];          // partner-side sums of the staged group
+};
+
+__device__ __noinline__ void born_flush(const BoJs* sj, BoNear& nb, int warp, int lane, int n, PairBand band,
+                                        int* status) {
+    for (int e = lane; e < n; e += 32) {
+        const uint32_t q = nb.q[warp][e];
+        const int l = q & 31u, u = (q >> 5) & 1u, jj = (q >> 6) & 31u, h = (q >> 11) & 1u, pr = q >> 12;
+        const int slot = u * 32 + l;
+        const float4 xi = nb.ix[warp][slot];
+        const float2 ti = nb.it[warp][slot];
+        const BoJs& S = sj[pr];
+        const float4 A = S.a[jj], B = S.b[jj], C = S.c[jj], Nj = S.n[jj];
+        const float dx = xi.x + (h ? A.y : A.x), dy = xi.y + (h ? A.w : A.z), dz = xi.z + (h ? B.y : B.x);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float2 hv = born_near(r2, rsqrt_ftz(r2), ti.x, ti.y, xi.w, h ? C.w : C.z, h ? Nj.y : Nj.x,
+                                    h ? Nj.w : Nj.z, band.rc);
+        if (!(fabsf(hv.x) < 1e20f && fabsf(hv.y) < 1e20f)) atomicOr(status, 4);
+        atomicAdd((unsigned long long*)&nb.ihx[warp][slot], (unsigned long long)to_fixed(hv.x, (float)kScaleH));
+        atomicAdd((unsigned long long*)&nb.jhx[2 * pr + h][jj], (unsigned long long)to_fixed(hv.y, (float)kScaleH));
+    }
+    __syncwarp();
+}
+
+// born_tile with the closed forms queued (weight 0 in the loop)
+template <bool MASKED, bool CUT>
+__device__ __forceinline__ void born_tile_q(const BoJs* sjg, int pr, int lane, int warp, const BoI2 (&I)[2],
+                                            float2 (&ah)[2], float2& jh, const uint32_t (&sk)[2][2],
+                                            const PairBand& band, BoNear& nb, int& nq, int* status) {
+    const BoJs& sj = sjg[pr];
+    const int src = (lane + 1) & 31;
+    const float skr2 = band.skr2;
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll 2
+    for (int k = 0; k < kTileJ; ++k) {
+        const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
+        const float2 s2j = make_float2(B.z, B.w), s3j = make_float2(C.x, C.y);
+        float2 r2[2], hi[2], hj[2], wt[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            if (MASKED) { // skipped pairs stay off the closed-form queue
+                const int jj = (lane + k) & (kTileJ - 1);
+                r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
+                r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
+            }
+            const float2 rinv = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+            wt[u] = __fmul2_rn(rinv2, rinv2); // r^-4, the weight of both far terms
+            hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), s3j);
+            hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), I[u].s3);
+            if (CUT) { // beyond rc + s_max nothing descreens
+                wt[u].x = r2[u].x >= band.rout2 ? 0.f : wt[u].x;
+                wt[u].y = r2[u].y >= band.rout2 ? 0.f : wt[u].y;
+            }
+        }
+        const uint32_t nm = (band_near<CUT>(r2[0].x, band) ? 1u : 0u) | (band_near<CUT>(r2[0].y, band) ? 2u : 0u) |
+                            (band_near<CUT>(r2[1].x, band) ? 4u : 0u) | (band_near<CUT>(r2[1].y, band) ? 8u : 0u);
+        if (__any_sync(0xffffffffu, nm != 0u)) {
+            const uint32_t jj = (uint32_t)((lane + k) & (kTileJ - 1));
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool f = (nm >> b) & 1u;
+                const uint32_t bal = __ballot_sync(0xffffffffu, f);
+                if (f)
+                    nb.q[warp][nq + __popc(bal & lt)] =
+                        (uint32_t)lane | ((uint32_t)(b >> 1) << 5) | (jj << 6) | ((uint32_t)(b & 1) << 11) |
+                        ((uint32_t)pr << 12);
+                nq += __popc(bal);
+            }
+            // queued pairs leave the loop's sums (values too: a far form at
+            // tiny r may overflow, and inf * 0 would not vanish)
+            wt[0].x = (nm & 1u) ? 0.f : wt[0].x;
+            wt[0].y = (nm & 2u) ? 0.f : wt[0].y;
+            wt[1].x = (nm & 4u) ? 0.f : wt[1].x;
+            wt[1].y = (nm & 8u) ? 0.f : wt[1].y;
+            hi[0].x = (nm & 1u) ? 0.f : hi[0].x;
+            hi[0].y = (nm & 2u) ? 0.f : hi[0].y;
+            hi[1].x = (nm & 4u) ? 0.f : hi[1].x;
+            hi[1].y = (nm & 8u) ? 0.f : hi[1].y;
+            hj[0].x = (nm & 1u) ? 0.f : hj[0].x;
+            hj[0].y = (nm & 2u) ? 0.f : hj[0].y;
+            hj[1].x = (nm & 4u) ? 0.f : hj[1].x;
+            hj[1].y = (nm & 8u) ? 0.f : hj[1].y;
+            if (nq >= 64) {
+                __syncwarp();
+                born_flush(sjg, nb, warp, lane, nq, band, status);
+                nq = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (MASKED) {
+                const int jj = (lane + k) & (kTileJ - 1);
+                wt[u].x = ((sk[u][0] >> jj) & 1u) ? 0.f : wt[u].x;
+                wt[u].y = ((sk[u][1] >> jj) & 1u) ? 0.f : wt[u].y;
+            }
+            ah[u] = __ffma2_rn(hi[u], wt[u], ah[u]);
+            jh = __ffma2_rn(hj[u], wt[u], jh);
+        }
+        jh.x = __shfl_sync(0xffffffffu, jh.x, src);
+        jh.y = __shfl_sync(0xffffffffu, jh.y, src);
+    }
+}
 template <bool CUT>
-__global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __restrict__ items, View V) {
+__global__ void __launch_bounds__(kSymThreads, 5) k_born_sym(const SymItem* __restrict__ items, View V) {
     __shared__ BoJs sj[kSymG / 2];
     __shared__ float red[kSymG][4][kSymJ];
+    __shared__ BoNear nb;
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -777,7 +899,12 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
         I[u].s = si;
         I[u].rt = vi[u] ? pi.y : 1.f;
         I[u].irt = vi[u] ? pi.z : 1.f;
+        nb.ix[warp][u * 32 + lane] = make_float4(I[u].x.x, I[u].y.x, I[u].z.x, si);
+        nb.it[warp][u * 32 + lane] = make_float2(I[u].rt, I[u].irt);
+        nb.ihx[warp][u * 32 + lane] = 0;
     }
+    for (int q = tid; q < kSymG * kSymJ; q += kSymThreads) nb.jhx[q / kSymJ][q % kSymJ] = 0;
+    int nq = 0; // this warp's queued pairs (warp-uniform)
     long long hx[2] = {0, 0}; // i-side fixed-point sums
     int mp = V.smt_off[it.st];
     const int me = V.smt_off[it.st + 1];
@@ -831,8 +958,8 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
                     for (int u = 0; u < 2; ++u) sym_masks(V, P, ii[u], vi[u], jt * kSymJ, N, sk[u][h], nbm);
                 }
             }
-            if (masked) born_tile<true, CUT>(sj[pr], lane, I, ah, jh, sk, band);
-            else born_tile<false, CUT>(sj[pr], lane, I, ah, jh, sk, band);
+            if (masked) born_tile_q<true, CUT>(sj, pr, lane, warp, I, ah, jh, sk, band, nb, nq, V.status);
+            else born_tile_q<false, CUT>(sj, pr, lane, warp, I, ah, jh, sk, band, nb, nq, V.status);
             // per-tile conversion (each half is one tile)
 #pragma unroll
             for (int u = 0; u < 2; ++u)
@@ -840,17 +967,26 @@ __global__ void __launch_bounds__(kSymThreads, 6) k_born_sym(const SymItem* __re
             red[2 * pr][warp][lane] = jh.x;
             red[2 * pr + 1][warp][lane] = jh.y;
         }
+        if (nq > 0) { // the group's staged rows are about to be replaced
+            born_flush(sj, nb, warp, lane, nq, band, V.status);
+            nq = 0;
+        }
         __syncthreads();
         for (int q = tid; q < ng * kSymJ; q += kSymThreads) {
             const int g = q / kSymJ, j = q % kSymJ;
             const float v = red[g][0][j] + red[g][1][j] + red[g][2][j] + red[g][3][j];
             const int jg = g0 * kSymJ + q;
-            if (jg < N) red_add_h(&V.Hfix[A + jg], v, V.status);
+            if (jg < N) {
+                red_add_h(&V.Hfix[A + jg], v, V.status);
+                if (nb.jhx[g][j] != 0) fix_add(&V.Hfix[A + jg], nb.jhx[g][j]);
+            }
+            nb.jhx[g][j] = 0;
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-        if (vi[u]) fix_add(&V.Hfix[A + ii[u]], hx[u]);
+        if (vi[u]) fix_add(&V.Hfix[A + ii[u]], hx[u] + nb.ihx[warp][u * 32 + lane]);
 }
 
 // psi, R, dR/dpsi from the descreening sums (FP64); resets the accumulators
