@@ -39,14 +39,14 @@ WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-a
 # the method evaluates for a far pair (r >= r_far: the HCT series; over 99 % of
 # the pairs here): FP32 lane operations (an FMA counts once) and MUFU
 # operations (rsqrt, ex2).  born: distance 6, powers of 1/r 2, two series
-# terms 16, sums 2; gb: distance 6, GB kernel and dE/dR 18, LJ 9, Coulomb 2,
+# terms (y, P, s^3) 14, r^-4-weighted fused sums 2; gb: distance 6, GB kernel and dE/dR 18, LJ 9, Coulomb 2,
 # force and partner force 6 (minus fused products), 3 MUFU; chain: distance 6,
 # powers 3, two dH/dr series 12, weights 5, forces 6.
-PASS_COST = {"born": (26, 1), "gb": (40, 3), "chain": (32, 1)}
-# GB-energy backward (Born radii recomputed): born 26/1 + GB adjoint (energy,
+PASS_COST = {"born": (24, 1), "gb": (40, 3), "chain": (32, 1)}
+# GB-energy backward (Born radii recomputed): born 24/1 + GB adjoint (energy,
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
 # dH/drt = 0 far) 48/1
-BACKWARD_COST = (106, 4)
+BACKWARD_COST = (104, 4)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
