@@ -43,6 +43,11 @@ WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-a
 # force and partner force 6 (minus fused products), 3 MUFU; chain: distance 6,
 # powers 3, two dH/dr series 12, weights 5, forces 6.
 PASS_COST = {"born": (24, 1), "gb": (40, 3), "chain": (32, 1)}
+# A GB pair with D = r^2 / (4 R_i R_j) >= 18 needs no exponential and no second
+# square root (1/f = 1/r and e^-D to FP32 precision): distance 6, D 2, LJ 9,
+# charges and eps 3, combined GB + Coulomb force factor 3, forces 6, 1 MUFU.
+GB_FAR_COST = (29, 1)
+GB_FAR_D = 18.0
 # GB-energy backward (Born radii recomputed): born 24/1 + GB adjoint (energy,
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
 # dH/drt = 0 far) 48/1
@@ -124,6 +129,40 @@ class ClockSampler:
 def workload():
     from paper_1809_07726_gb300 import synth
     return synth.config_c4()
+
+
+def gb_far_fraction(eng, systems, grid, samples=200000, seed=0):
+    """Fraction of the workload's unordered pairs with D >= GB_FAR_D, from the
+    engine's current positions and Born radii (one walker per system, random
+    pairs), weighted by each system's pair count over the grid."""
+    rng = np.random.default_rng(seed)
+    x_all, r_all = eng.positions(), eng.born_radii()
+    sos = np.asarray(grid.system_of_slot)
+    num = den = 0.0
+    for s in np.unique(sos):
+        w = int(np.nonzero(sos == s)[0][0])  # the walker that starts in system s's first slot
+        sl = eng.walker_slice(w)
+        x, R = x_all[sl], r_all[sl]
+        n = len(R)
+        if n < 2:
+            continue
+        i = rng.integers(0, n, samples)
+        j = rng.integers(0, n, samples)
+        keep = i != j
+        i, j = i[keep], j[keep]
+        D = ((x[i] - x[j]) ** 2).sum(1) / (4.0 * R[i] * R[j])
+        pairs = n * (n - 1) / 2 * np.count_nonzero(sos == s)
+        num += pairs * float((D >= GB_FAR_D).mean())
+        den += pairs
+    return num / den if den else 0.0
+
+
+def pass_clk(name, gb_far=0.0):
+    """SM clocks per unordered pair of a pass at its algorithmic cost; the GB
+    pass mixes the far form (fraction gb_far of the pairs) with the full one."""
+    if name == "gb":
+        return gb_far * clk_per_pair_per_sm(*GB_FAR_COST) + (1.0 - gb_far) * clk_per_pair_per_sm(*PASS_COST["gb"])
+    return clk_per_pair_per_sm(*PASS_COST[name])
 
 
 def pair_count(systems, grid):
@@ -315,10 +354,10 @@ def run_gpu(args):
     names = ["born", "gb", "chain"]
     dom = int(np.argmax(pass_ms))
     f_mhz = clocks["sm_mhz"] or 2070.0
-    fp, mu = PASS_COST[names[dom]]
-    peak = N_SM * f_mhz * 1e6 * pairs_per_clk_per_sm(fp, mu) / 1e9
+    gb_far = gb_far_fraction(eng, systems, grid)
+    peak = N_SM * f_mhz * 1e6 / pass_clk(names[dom], gb_far) / 1e9
     achieved = total_pairs / (pass_ms[dom] / 1e3) / 1e9
-    step_peak = N_SM * f_mhz * 1e6 / sum(clk_per_pair_per_sm(*v) for v in PASS_COST.values()) / 1e9
+    step_peak = N_SM * f_mhz * 1e6 / sum(pass_clk(n, gb_far) for n in names) / 1e9
 
     if args.quick:
         if rank == 0:
@@ -422,8 +461,12 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
                      "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": PASS_DRAM_BYTES.get(names[dom]),
                      "traffic_basis": "DRAM read + write bytes per launch of the pass's pair kernel (ncu)",
-                     "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) x "
-                                   f"1/max({fp}/128, {mu}/16) pairs/clk/SM (FP32 lanes, MUFU)",
+                     "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) / "
+                                   f"{pass_clk(names[dom], gb_far):.4f} SM clocks per pair, a pair's form "
+                                   "costing max(fp32/128, mufu/16) clocks (FP32 lanes, MUFU)",
+                     "algorithmic_cost": {n: list(PASS_COST[n]) for n in names} | {
+                         "gb_far": list(GB_FAR_COST), "gb_far_fraction": gb_far,
+                         "gb_far_rule": f"D = r^2/(4 R_i R_j) >= {GB_FAR_D:g}"},
                      "step_frac": (total_pairs / (sum(pass_ms) / 1e3) / 1e9) / step_peak},
         "e2e": {"value": e2e_value, "unit": "replica-steps/s",
                 "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e},

@@ -143,6 +143,15 @@ struct GbMask {
 // SALT: Debye-Hueckel screening; the GB terms then carry tau(f) (energy) and
 // taud(f) (derivatives) per pair, f = 1 / fi, and the finishing kernels
 // apply 1 instead of tau to the pair sums.
+// Far GB pairs: with D = r^2 / (4 R_i R_j) >= 18, e^-D <= 1.6e-8, so
+// 1/f = 1/r to 1e-10 relative, the GB force factor (1 - e^-D / 4) is 1 to
+// 4e-9, and the pair's dE/dR term (~ e^-D (1 + D)) is below 3e-7 of its
+// q_i q_j / r^3 (and far below the self and near-pair terms of dE/dR).  A step
+// in which every lane's four pairs are that far (about half the steps of an
+// 8000-atom system) takes 1/f = 1/r, no exponential and no dE/dR term; GB and
+// Coulomb then combine into q_i q_j / (eps_out r) (kappa = 0).
+constexpr float kGbFarD2 = 18.f * kLog2e; // the threshold on D log2(e)
+
 template <bool MASKED, bool ENERGY, bool SALT>
 __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I)[2], float2 (&a)[2][4],
                                         float2 (&ja)[4], const GbMask& m, float tau, float iei, float kappa,
@@ -157,75 +166,118 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k], D = sj.d[lane + k];
         const float2 qj = make_float2(B.z, B.w), Rj = make_float2(C.x, C.y);
+        float2 dx[2], dy[2], dz[2], r2[2], D2[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
-            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
-            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
-            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            float2 qq = __fmul2_rn(I[u].q, qj);
-            float2 ep4 = __fmul2_rn(I[u].se4, make_float2(D.z, D.w));
+            dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            dy[u] = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            dz[u] = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx[u], dx[u], __ffma2_rn(dy[u], dy[u], __fmul2_rn(dz[u], dz[u])));
             if (MASKED) {
                 const int jj = (lane + k) & (kSymJ - 1);
-                const bool s0 = (m.sk[u][0] >> jj) & 1u, s1 = (m.sk[u][1] >> jj) & 1u;
-                const bool b0 = (m.nb[u][0] >> jj) & 1u, b1 = (m.nb[u][1] >> jj) & 1u;
-                r2.x = s0 ? 1.f : r2.x;
-                r2.y = s1 ? 1.f : r2.y;
-                qq.x = s0 ? 0.f : qq.x;
-                qq.y = s1 ? 0.f : qq.y;
-                ep4.x = b0 ? 0.f : ep4.x;
-                ep4.y = b1 ? 0.f : ep4.y;
+                r2[u].x = ((m.sk[u][0] >> jj) & 1u) ? 1.f : r2[u].x;
+                r2[u].y = ((m.sk[u][1] >> jj) & 1u) ? 1.f : r2[u].y;
             }
-            float2 cq = __fmul2_rn(qq, ie); // sqrt(k) q_i sqrt(k) q_j / eps_in
-            if (MASKED) {
-                const int jj = (lane + k) & (kSymJ - 1);
-                cq.x = ((m.nb[u][0] >> jj) & 1u) ? 0.f : cq.x;
-                cq.y = ((m.nb[u][1] >> jj) & 1u) ? 0.f : cq.y;
+            D2[u] = __fmul2_rn(r2[u], __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
+        }
+        const bool far = !MASKED && !SALT &&
+                         __all_sync(0xffffffffu, fminf(fminf(D2[0].x, D2[0].y), fminf(D2[1].x, D2[1].y)) >= kGbFarD2);
+        if (far) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float2 qq = __fmul2_rn(I[u].q, qj);
+                const float2 ep4 = __fmul2_rn(I[u].se4, make_float2(D.z, D.w));
+                const float2 rinv = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+                const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
+                const float2 sr2 = __fmul2_rn(__fmul2_rn(sig, sig), rinv2);
+                const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+                const float2 l6 = __fmul2_rn(ep4, sr6);
+                const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
+                // (Coulomb - tau GB) q_i q_j / r^3 = q_i q_j / (eps_out r^3)
+                const float2 fs = __ffma2_rn(__fmul2_rn(__fmul2_rn(qq, ieo2), rinv), rinv2, __fmul2_rn(lj, rinv2));
+                a[u][0] = __ffma2_rn(fs, dx[u], a[u][0]);
+                a[u][1] = __ffma2_rn(fs, dy[u], a[u][1]);
+                a[u][2] = __ffma2_rn(fs, dz[u], a[u][2]);
+                ja[0] = __ffma2_rn(fs, dx[u], ja[0]); // the partner's force is minus this sum
+                ja[1] = __ffma2_rn(fs, dy[u], ja[1]);
+                ja[2] = __ffma2_rn(fs, dz[u], ja[2]);
+                if (ENERGY) {
+                    const float2 eg = __fmul2_rn(qq, rinv);
+                    const float2 eco = __fmul2_rn(__fmul2_rn(qq, ie), rinv);
+                    const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
+                    egb.add(eg.x);
+                    egb.add(eg.y);
+                    ec.add(eco.x);
+                    ec.add(eco.y);
+                    elj.add(el.x);
+                    elj.add(el.y);
+                }
             }
-            const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-            const float2 rinv2 = __fmul2_rn(rinv, rinv);
-            const float2 D2 = __fmul2_rn(r2, __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
-            const float2 e = make_float2(exp2_ftz(-D2.x), exp2_ftz(-D2.y));
-            const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2);
-            const float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
-            const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
-            const float2 qfe = __fmul2_rn(qf3, e);
-            float2 tf = one, td = one;
-            if (SALT) {
-                const float2 f = __fmul2_rn(fa, fi); // effective distance
-                const float2 es = __fmul2_rn(ieo2, make_float2(exp2_ftz(-kl * f.x), exp2_ftz(-kl * f.y)));
-                tf = __ffma2_rn(es, mone, ie);                                 // tau(f)
-                td = __ffma2_rn(__fmul2_rn(kap2, f), __fmul2_rn(es, mone), tf); // taud(f)
-            }
-            float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
-            if (SALT) t = __fmul2_rn(t, td);
-            a[u][3] = __ffma2_rn(t, Rj, a[u][3]);
-            ja[3] = __ffma2_rn(t, I[u].R, ja[3]);
-            const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
-            const float2 sr2 = __fmul2_rn(__fmul2_rn(sig, sig), rinv2);
-            const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
-            const float2 l6 = __fmul2_rn(ep4, sr6);
-            const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
-            // -tau qf3 (1 - e/4); with salt taud(f) in place of tau
-            const float2 w = SALT ? __fmul2_rn(td, __ffma2_rn(q25, qfe, __fmul2_rn(mone, qf3)))
-                                  : __ffma2_rn(qtau4, qfe, __fmul2_rn(mtau, qf3));
-            const float2 fs = __ffma2_rn(__ffma2_rn(cq, rinv, lj), rinv2, w);
-            a[u][0] = __ffma2_rn(fs, dx, a[u][0]);
-            a[u][1] = __ffma2_rn(fs, dy, a[u][1]);
-            a[u][2] = __ffma2_rn(fs, dz, a[u][2]);
-            ja[0] = __ffma2_rn(fs, dx, ja[0]); // the partner's force is minus this sum
-            ja[1] = __ffma2_rn(fs, dy, ja[1]);
-            ja[2] = __ffma2_rn(fs, dz, ja[2]);
-            if (ENERGY) {
-                const float2 eg = SALT ? __fmul2_rn(tf, __fmul2_rn(qq, fi)) : __fmul2_rn(qq, fi);
-                const float2 eco = __fmul2_rn(cq, rinv);
-                const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
-                egb.add(eg.x);
-                egb.add(eg.y);
-                ec.add(eco.x);
-                ec.add(eco.y);
-                elj.add(el.x);
-                elj.add(el.y);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                float2 qq = __fmul2_rn(I[u].q, qj);
+                float2 ep4 = __fmul2_rn(I[u].se4, make_float2(D.z, D.w));
+                if (MASKED) {
+                    const int jj = (lane + k) & (kSymJ - 1);
+                    const bool s0 = (m.sk[u][0] >> jj) & 1u, s1 = (m.sk[u][1] >> jj) & 1u;
+                    const bool b0 = (m.nb[u][0] >> jj) & 1u, b1 = (m.nb[u][1] >> jj) & 1u;
+                    qq.x = s0 ? 0.f : qq.x;
+                    qq.y = s1 ? 0.f : qq.y;
+                    ep4.x = b0 ? 0.f : ep4.x;
+                    ep4.y = b1 ? 0.f : ep4.y;
+                }
+                float2 cq = __fmul2_rn(qq, ie); // sqrt(k) q_i sqrt(k) q_j / eps_in
+                if (MASKED) {
+                    const int jj = (lane + k) & (kSymJ - 1);
+                    cq.x = ((m.nb[u][0] >> jj) & 1u) ? 0.f : cq.x;
+                    cq.y = ((m.nb[u][1] >> jj) & 1u) ? 0.f : cq.y;
+                }
+                const float2 rinv = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+                const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                const float2 e = make_float2(exp2_ftz(-D2[u].x), exp2_ftz(-D2[u].y));
+                const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2[u]);
+                const float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
+                const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
+                const float2 qfe = __fmul2_rn(qf3, e);
+                float2 tf = one, td = one;
+                if (SALT) {
+                    const float2 f = __fmul2_rn(fa, fi); // effective distance
+                    const float2 es = __fmul2_rn(ieo2, make_float2(exp2_ftz(-kl * f.x), exp2_ftz(-kl * f.y)));
+                    tf = __ffma2_rn(es, mone, ie);                                 // tau(f)
+                    td = __ffma2_rn(__fmul2_rn(kap2, f), __fmul2_rn(es, mone), tf); // taud(f)
+                }
+                float2 t = __fmul2_rn(qfe, __ffma2_rn(D2[u], ln2, one));
+                if (SALT) t = __fmul2_rn(t, td);
+                a[u][3] = __ffma2_rn(t, Rj, a[u][3]);
+                ja[3] = __ffma2_rn(t, I[u].R, ja[3]);
+                const float2 sig = __fadd2_rn(I[u].sg, make_float2(D.x, D.y));
+                const float2 sr2 = __fmul2_rn(__fmul2_rn(sig, sig), rinv2);
+                const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+                const float2 l6 = __fmul2_rn(ep4, sr6);
+                const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
+                // -tau qf3 (1 - e/4); with salt taud(f) in place of tau
+                const float2 w = SALT ? __fmul2_rn(td, __ffma2_rn(q25, qfe, __fmul2_rn(mone, qf3)))
+                                      : __ffma2_rn(qtau4, qfe, __fmul2_rn(mtau, qf3));
+                const float2 fs = __ffma2_rn(__ffma2_rn(cq, rinv, lj), rinv2, w);
+                a[u][0] = __ffma2_rn(fs, dx[u], a[u][0]);
+                a[u][1] = __ffma2_rn(fs, dy[u], a[u][1]);
+                a[u][2] = __ffma2_rn(fs, dz[u], a[u][2]);
+                ja[0] = __ffma2_rn(fs, dx[u], ja[0]); // the partner's force is minus this sum
+                ja[1] = __ffma2_rn(fs, dy[u], ja[1]);
+                ja[2] = __ffma2_rn(fs, dz[u], ja[2]);
+                if (ENERGY) {
+                    const float2 eg = SALT ? __fmul2_rn(tf, __fmul2_rn(qq, fi)) : __fmul2_rn(qq, fi);
+                    const float2 eco = __fmul2_rn(cq, rinv);
+                    const float2 el = __fmul2_rn(l6, __fadd2_rn(sr6, splat<float2>(-1.f)));
+                    egb.add(eg.x);
+                    egb.add(eg.y);
+                    ec.add(eco.x);
+                    ec.add(eco.y);
+                    elj.add(el.x);
+                    elj.add(el.y);
+                }
             }
         }
 #pragma unroll
