@@ -52,6 +52,9 @@ GB_FAR_D = 18.0
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
 # dH/drt = 0 far) 48/1
 BACKWARD_COST = (104, 4)
+# the same with the GB adjoint in its far form (1/f = 1/r: no exponential, no
+# dE/dR term; 22 FP32 lane operations and 1 MUFU) for a pair with D >= 18
+BACKWARD_FAR_COST = (94, 3)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
@@ -273,12 +276,25 @@ def backward_leg(dev, stream, barrier, sm_mhz, n_eval=5):
     bw_ms = b0.elapsed_time(b1) / n_eval
     bw_pairs = q5.shape[0] * q5.shape[1] * (q5.shape[1] - 1) // 2
     bw_achieved = bw_pairs / (bw_ms / 1e3) / 1e9
-    bw_peak = N_SM * (sm_mhz or 2070.0) * 1e6 * pairs_per_clk_per_sm(*BACKWARD_COST) / 1e9
+    # far-form share of the pairs, from the engine's Born radii of replica 0
+    import copy
+    s0 = copy.deepcopy(s5)
+    s0.x = np.ascontiguousarray(x5[0], dtype=np.float64).reshape(-1, 3)
+    s0.rho = np.asarray(rho5[0], dtype=np.float64)
+    s0.q = np.asarray(q5[0], dtype=np.float64)
+    g0 = synth.Grid(np.array([0.0]), np.array([7.0]), np.array([300.0]), np.zeros(1, np.int32))
+    e0 = cphremd.init_system([s0], g0, seed=1)
+    e0.evaluate()
+    far = gb_far_fraction(e0, [s0], g0)
+    clk = far * clk_per_pair_per_sm(*BACKWARD_FAR_COST) + (1.0 - far) * clk_per_pair_per_sm(*BACKWARD_COST)
+    bw_peak = N_SM * (sm_mhz or 2070.0) * 1e6 / clk / 1e9
     return {"workload": "GB energy backward w.r.t. x, q, rho: 128 replicas x 8000 atoms",
             "ms_per_eval": bw_ms, "evals_per_s": q5.shape[0] / (bw_ms / 1e3),
             "pair_evals_per_s": bw_pairs / (bw_ms / 1e3),
             "roofline": {"bound": "alu", "achieved": bw_achieved, "peak": bw_peak,
-                         "unit": "Gpair/s", "frac": bw_achieved / bw_peak}}
+                         "unit": "Gpair/s", "frac": bw_achieved / bw_peak,
+                         "algorithmic_cost": {"full": list(BACKWARD_COST), "gb_far": list(BACKWARD_FAR_COST),
+                                              "gb_far_fraction": far}}}
 
 
 def run_gpu(args):

@@ -241,46 +241,74 @@ __device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 
     for (int k = 0; k < kGJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 qj = make_float2(B.z, B.w), Rj = make_float2(C.x, C.y);
+        float2 dx[2], dy[2], dz[2], r2[2], D2[2];
+        bool s0[2] = {false, false}, s1[2] = {false, false};
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
-            const float2 dy = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
-            const float2 dz = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
-            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            bool s0 = false, s1 = false;
+            dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
+            dy[u] = __fadd2_rn(I[u].y, make_float2(A.z, A.w));
+            dz[u] = __fadd2_rn(I[u].z, make_float2(B.x, B.y));
+            r2[u] = __ffma2_rn(dx[u], dx[u], __ffma2_rn(dy[u], dy[u], __fmul2_rn(dz[u], dz[u])));
             if (MASKED) {
                 const int jj = (lane + k) & (kGJ - 1);
-                s0 = (sk[u][0] >> jj) & 1u;
-                s1 = (sk[u][1] >> jj) & 1u;
-                r2.x = s0 ? 1.f : r2.x;
-                r2.y = s1 ? 1.f : r2.y;
+                s0[u] = (sk[u][0] >> jj) & 1u;
+                s1[u] = (sk[u][1] >> jj) & 1u;
+                r2[u].x = s0[u] ? 1.f : r2[u].x;
+                r2[u].y = s1[u] ? 1.f : r2[u].y;
             }
-            const float2 D2 = __fmul2_rn(r2, __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
-            const float2 e = make_float2(exp2_ftz(-D2.x), exp2_ftz(-D2.y));
-            const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2);
-            float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
-            if (MASKED) {
-                fi.x = s0 ? 0.f : fi.x;
-                fi.y = s1 ? 0.f : fi.y;
+            D2[u] = __fmul2_rn(r2[u], __fmul2_rn(I[u].dk, make_float2(C.z, C.w))); // D log2(e)
+        }
+        // a step whose pairs all have D >= 18: 1/f = 1/r, no exponential, no
+        // dE/dR term (see kGbFarD2)
+        const bool far = !MASKED &&
+                         __all_sync(0xffffffffu, fminf(fminf(D2[0].x, D2[0].y), fminf(D2[1].x, D2[1].y)) >= kGbFarD2);
+        if (far) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float2 fi = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
+                const float2 qq = __fmul2_rn(I[u].q, qj);
+                ei[u] = __ffma2_rn(qq, fi, ei[u]);
+                if (BACKWARD) {
+                    ai[u][1] = __ffma2_rn(qj, fi, ai[u][1]);
+                    aj[1] = __ffma2_rn(I[u].q, fi, aj[1]);
+                    const float2 g2 = __fmul2_rn(tau2, __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi)));
+                    ai[u][2] = __ffma2_rn(g2, dx[u], ai[u][2]);
+                    ai[u][3] = __ffma2_rn(g2, dy[u], ai[u][3]);
+                    ai[u][4] = __ffma2_rn(g2, dz[u], ai[u][4]);
+                    aj[2] = __ffma2_rn(g2, dx[u], aj[2]); // the partner's gradient is minus this sum
+                    aj[3] = __ffma2_rn(g2, dy[u], aj[3]);
+                    aj[4] = __ffma2_rn(g2, dz[u], aj[4]);
+                }
             }
-            const float2 qq = __fmul2_rn(I[u].q, qj);
-            ei[u] = __ffma2_rn(qq, fi, ei[u]);
-            if (BACKWARD) {
-                const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
-                const float2 qfe = __fmul2_rn(qf3, e);
-                const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2, ln2, one));
-                ai[u][0] = __ffma2_rn(t, Rj, ai[u][0]);
-                aj[0] = __ffma2_rn(t, I[u].R, aj[0]);
-                ai[u][1] = __ffma2_rn(qj, fi, ai[u][1]);
-                aj[1] = __ffma2_rn(I[u].q, fi, aj[1]);
-                // tau qf3 (1 - e/4)
-                const float2 g2 = __ffma2_rn(mtau4, qfe, __fmul2_rn(tau2, qf3));
-                ai[u][2] = __ffma2_rn(g2, dx, ai[u][2]);
-                ai[u][3] = __ffma2_rn(g2, dy, ai[u][3]);
-                ai[u][4] = __ffma2_rn(g2, dz, ai[u][4]);
-                aj[2] = __ffma2_rn(g2, dx, aj[2]); // the partner's gradient is minus this sum
-                aj[3] = __ffma2_rn(g2, dy, aj[3]);
-                aj[4] = __ffma2_rn(g2, dz, aj[4]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float2 e = make_float2(exp2_ftz(-D2[u].x), exp2_ftz(-D2[u].y));
+                const float2 fa = __ffma2_rn(__fmul2_rn(I[u].R, Rj), e, r2[u]);
+                float2 fi = make_float2(rsqrt_ftz(fa.x), rsqrt_ftz(fa.y));
+                if (MASKED) {
+                    fi.x = s0[u] ? 0.f : fi.x;
+                    fi.y = s1[u] ? 0.f : fi.y;
+                }
+                const float2 qq = __fmul2_rn(I[u].q, qj);
+                ei[u] = __ffma2_rn(qq, fi, ei[u]);
+                if (BACKWARD) {
+                    const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
+                    const float2 qfe = __fmul2_rn(qf3, e);
+                    const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2[u], ln2, one));
+                    ai[u][0] = __ffma2_rn(t, Rj, ai[u][0]);
+                    aj[0] = __ffma2_rn(t, I[u].R, aj[0]);
+                    ai[u][1] = __ffma2_rn(qj, fi, ai[u][1]);
+                    aj[1] = __ffma2_rn(I[u].q, fi, aj[1]);
+                    // tau qf3 (1 - e/4)
+                    const float2 g2 = __ffma2_rn(mtau4, qfe, __fmul2_rn(tau2, qf3));
+                    ai[u][2] = __ffma2_rn(g2, dx[u], ai[u][2]);
+                    ai[u][3] = __ffma2_rn(g2, dy[u], ai[u][3]);
+                    ai[u][4] = __ffma2_rn(g2, dz[u], ai[u][4]);
+                    aj[2] = __ffma2_rn(g2, dx[u], aj[2]); // the partner's gradient is minus this sum
+                    aj[3] = __ffma2_rn(g2, dy[u], aj[3]);
+                    aj[4] = __ffma2_rn(g2, dz[u], aj[4]);
+                }
             }
         }
         if (BACKWARD) {

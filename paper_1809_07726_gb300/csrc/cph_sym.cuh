@@ -143,14 +143,10 @@ struct GbMask {
 // SALT: Debye-Hueckel screening; the GB terms then carry tau(f) (energy) and
 // taud(f) (derivatives) per pair, f = 1 / fi, and the finishing kernels
 // apply 1 instead of tau to the pair sums.
-// Far GB pairs: with D = r^2 / (4 R_i R_j) >= 18, e^-D <= 1.6e-8, so
-// 1/f = 1/r to 1e-10 relative, the GB force factor (1 - e^-D / 4) is 1 to
-// 4e-9, and the pair's dE/dR term (~ e^-D (1 + D)) is below 3e-7 of its
-// q_i q_j / r^3 (and far below the self and near-pair terms of dE/dR).  A step
-// in which every lane's four pairs are that far (about half the steps of an
-// 8000-atom system) takes 1/f = 1/r, no exponential and no dE/dR term; GB and
-// Coulomb then combine into q_i q_j / (eps_out r) (kappa = 0).
-constexpr float kGbFarD2 = 18.f * kLog2e; // the threshold on D log2(e)
+// Far GB pairs (kGbFarD2, cph_pair_tiles.cuh): a step in which every lane's
+// four pairs are that far (about half the steps of an 8000-atom system) takes
+// 1/f = 1/r, no exponential and no dE/dR term; GB and Coulomb then combine
+// into q_i q_j / (eps_out r) (kappa = 0).
 
 template <bool MASKED, bool ENERGY, bool SALT>
 __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I)[2], float2 (&a)[2][4],
