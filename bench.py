@@ -58,7 +58,7 @@ BACKWARD_FAR_COST = (94, 3)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
-PASS_DRAM_BYTES = {"born": 33.41e6, "gb": 89.65e6 + 3.79e6, "chain": 60.35e6}
+PASS_DRAM_BYTES = {"born": 33.38e6, "gb": 89.60e6 + 3.68e6, "chain": 60.35e6}
 FP32_LANES = 128   # FP32 lane operations per clock per SM
 MUFU_LANES = 16    # MUFU operations per clock per SM
 
