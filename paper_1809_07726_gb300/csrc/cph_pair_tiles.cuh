@@ -22,8 +22,8 @@ constexpr float kGbFarD2 = 18.f * kLog2e; // the threshold on D log2(e)
 // moves one lane per step).  In the far regime H = P(y) s^3 / r^4 with
 // y = s^2 / r^2 (P the fitted series), so s^2 and s^3 are staged and 1/r^4
 // serves both directions as the weight of a fused accumulate (1 for the
-// closed forms, 0 for pairs that are not counted).  Bit jj of sk[u][h] marks a pair of i atom u and
-// partner jj of tile h that is not counted.
+// closed forms, 0 for pairs that are not counted).  Bit jj of sk[u][h]
+// marks a pair of i atom u and partner jj of tile h that is not counted.
 struct BoI2 {
     float2 x, y, z, s2, s3; // the i atom's value in both halves
     float s, rt, irt;       // closed-form operands

@@ -23,7 +23,10 @@
 // Far pairs.  At set-up r_far = max(s_max / 0.35, s_max + rt_max) over every
 // atom (times 1 + 1e-5), so for r >= r_far every descreening integral of the
 // pair is in its disjoint-sphere series regime; one comparison of r^2 then
-// selects the series for both directions.
+// selects the series for both directions.  Pairs inside r_far take closed
+// forms: queued per warp in the Born pass (born_tile_q), in line behind a warp
+// vote in the chain-rule pass.  In the GB pass a step whose pairs all have
+// D = r^2 / (4 R_i R_j) >= 18 takes the far GB form (kGbFarD2).
 #pragma once
 #include "cph_device.cuh"
 #include "cph_internal.h"
