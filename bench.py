@@ -50,11 +50,11 @@ GB_FAR_COST = (29, 1)
 GB_FAR_D = 18.0
 # GB-energy backward (Born radii recomputed): born 24/1 + GB adjoint (energy,
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
-# dH/drt = 0 far) 48/1
-BACKWARD_COST = (104, 4)
+# dH/drt = 0 far, r^-4-weighted fused s sums) 46/1
+BACKWARD_COST = (102, 4)
 # the same with the GB adjoint in its far form (1/f = 1/r: no exponential, no
 # dE/dR term; 22 FP32 lane operations and 1 MUFU) for a pair with D >= 18
-BACKWARD_FAR_COST = (94, 3)
+BACKWARD_FAR_COST = (92, 3)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)

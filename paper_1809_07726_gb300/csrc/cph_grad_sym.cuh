@@ -535,7 +535,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
     for (int k = 0; k < kGJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 cj = make_float2(B.z, B.w), s2j = make_float2(C.x, C.y), s3j = make_float2(C.z, C.w);
-        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2], asi[2], asj[2];
+        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2], asi[2], asj[2], wt[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
@@ -555,17 +555,17 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
             // t = (c_i dH_i/dr + c_j dH_j/dr) / r = -(c_i s_j^3 Q_j + c_j s_i^3 Q_i) / r^6
             const float2 term = __ffma2_rn(__fmul2_rn(I[u].c, s3j), qj, __fmul2_rn(__fmul2_rn(cj, I[u].s3), qi));
             t[u] = __fmul2_rn(term, __fmul2_rn(__fmul2_rn(rinv4, rinv2), mone));
-            // c_j dH(r; rt_j, s_i)/ds = c_j s_i^2 S_i / r^4, and i <-> j
-            asi[u] = __fmul2_rn(__fmul2_rn(cj, I[u].s2), __fmul2_rn(hct_series_ds(yi), rinv4));
-            asj[u] = __fmul2_rn(__fmul2_rn(I[u].c, s2j), __fmul2_rn(hct_series_ds(yj), rinv4));
+            // c_j dH(r; rt_j, s_i)/ds = c_j s_i^2 S_i / r^4, and i <-> j, with r^-4 the
+            // weight of their fused accumulate (1 for closed forms, 0 if not counted)
+            asi[u] = __fmul2_rn(__fmul2_rn(cj, I[u].s2), hct_series_ds(yi));
+            asj[u] = __fmul2_rn(__fmul2_rn(I[u].c, s2j), hct_series_ds(yj));
+            wt[u] = rinv4;
             if (CUT) { // beyond rc + s_max nothing descreens
                 const bool o0 = r2[u].x >= band.rout2, o1 = r2[u].y >= band.rout2;
                 t[u].x = o0 ? 0.f : t[u].x;
                 t[u].y = o1 ? 0.f : t[u].y;
-                asi[u].x = o0 ? 0.f : asi[u].x;
-                asi[u].y = o1 ? 0.f : asi[u].y;
-                asj[u].x = o0 ? 0.f : asj[u].x;
-                asj[u].y = o1 ? 0.f : asj[u].y;
+                wt[u].x = o0 ? 0.f : wt[u].x;
+                wt[u].y = o1 ? 0.f : wt[u].y;
             }
         }
         // closed forms only where some lane has such a pair (rare; skipped
@@ -586,6 +586,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                     aj[3].x += o.htj;
                     asi[u].x = o.asi;
                     asj[u].x = o.asj;
+                    wt[u].x = 1.f;
                 }
                 if (band_near<CUT>(r2[u].y, band)) {
                     const GcNear o = gchain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.w, Nj.y,
@@ -595,6 +596,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                     aj[3].y += o.htj;
                     asi[u].y = o.asi;
                     asj[u].y = o.asj;
+                    wt[u].y = 1.f;
                 }
             }
         }
@@ -605,10 +607,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                 const bool s0 = (sk[u][0] >> jj) & 1u, s1 = (sk[u][1] >> jj) & 1u;
                 t[u].x = s0 ? 0.f : t[u].x;
                 t[u].y = s1 ? 0.f : t[u].y;
-                asi[u].x = s0 ? 0.f : asi[u].x;
-                asi[u].y = s1 ? 0.f : asi[u].y;
-                asj[u].x = s0 ? 0.f : asj[u].x;
-                asj[u].y = s1 ? 0.f : asj[u].y;
+                wt[u].x = s0 ? 0.f : wt[u].x;
+                wt[u].y = s1 ? 0.f : wt[u].y;
             }
             ai[u][0] = __ffma2_rn(t[u], dx[u], ai[u][0]);
             ai[u][1] = __ffma2_rn(t[u], dy[u], ai[u][1]);
@@ -616,8 +616,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
             aj[0] = __ffma2_rn(t[u], dx[u], aj[0]); // the partner's gradient is minus this sum
             aj[1] = __ffma2_rn(t[u], dy[u], aj[1]);
             aj[2] = __ffma2_rn(t[u], dz[u], aj[2]);
-            ai[u][4] = __fadd2_rn(ai[u][4], asi[u]);
-            aj[4] = __fadd2_rn(aj[4], asj[u]);
+            ai[u][4] = __ffma2_rn(asi[u], wt[u], ai[u][4]);
+            aj[4] = __ffma2_rn(asj[u], wt[u], aj[4]);
         }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
