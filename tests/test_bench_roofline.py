@@ -1,0 +1,30 @@
+"""The roofline accounting of bench.py on CPU: a pass's SM clocks per pair are
+max(fp32 / 128, mufu / 16) of its form, and the GB pass mixes its far and
+full forms by the share of pairs with D >= 18."""
+import pytest
+
+import bench
+
+
+def test_single_form_clocks():
+    assert bench.clk_per_pair_per_sm(24, 1) == pytest.approx(24 / 128)
+    assert bench.clk_per_pair_per_sm(8, 4) == pytest.approx(4 / 16)  # MUFU-bound form
+    for name in ("born", "chain"):
+        assert bench.pass_clk(name, 0.7) == bench.clk_per_pair_per_sm(*bench.PASS_COST[name])
+
+
+def test_gb_mix_interpolates_its_two_forms():
+    full = bench.clk_per_pair_per_sm(*bench.PASS_COST["gb"])
+    far = bench.clk_per_pair_per_sm(*bench.GB_FAR_COST)
+    assert far < full
+    assert bench.pass_clk("gb", 0.0) == pytest.approx(full)
+    assert bench.pass_clk("gb", 1.0) == pytest.approx(far)
+    assert bench.pass_clk("gb", 0.25) == pytest.approx(0.25 * far + 0.75 * full)
+
+
+def test_far_forms_cost_less_in_both_directions():
+    assert all(a <= b for a, b in zip(bench.GB_FAR_COST, bench.PASS_COST["gb"]))
+    assert all(a <= b for a, b in zip(bench.BACKWARD_FAR_COST, bench.BACKWARD_COST))
+    # the backward totals are the sums of their three passes' forms
+    assert bench.BACKWARD_COST[0] == bench.PASS_COST["born"][0] + 32 + 46
+    assert bench.BACKWARD_FAR_COST[0] == bench.PASS_COST["born"][0] + 22 + 46
