@@ -380,6 +380,34 @@ int cph_reset_observables(cph_engine* e, void* stream);
 int cph_fit_hill(int kind, int n_pts, const double* x, const double* f, double T, double v,
                  double* x0, double* n_hill, double* rss);
 
+/* Predictions of eqs (6)-(8) (host only, no GPU needed).  The "Temperature
+ * dependence in predicting E0 vs pH and pKa vs redox potential" section draws
+ * Figure 6's solid lines from eqs (7) and (8) with parameters taken from the
+ * simulation, without fitting.  A redox-active group (v electrons) couples to
+ * n_sites pH-active groups: pka_red[i] / pka_oxi[i] (host [n_sites]) are site
+ * i's pKa with the redox group reduced / oxidised; e0_prot / e0_deprot (V) are
+ * the redox group's E0 with every pH site protonated / deprotonated; T in K.
+ *   eq (6): *delta_e0 = E0_prot - E0_deprot
+ *                     = kB T ln10 sum_i (pka_red[i] - pka_oxi[i]) / (v F)
+ *   eq (7): e0[k] = E0_prot + kB T / (v F) sum_i ln((10^-pka_red[i] + 10^-pH[k])
+ *                                                   / (10^-pka_oxi[i] + 10^-pH[k]))
+ *   eq (8): sum_pka[k] = sum_i pka_red[i] + log10((exp(-v F e0_prot / kB T)
+ *                        + exp(-F E[k] / kB T)) / (exp(-v F e0_deprot / kB T)
+ *                        + exp(-F E[k] / kB T)))
+ * The logarithm of eq (8) is read as base 10, and v multiplies only the E0
+ * terms, as printed.  pH[n_pts], E[n_pts] (V) host inputs; e0[n_pts],
+ * sum_pka[n_pts] host outputs.  CPH_E_INVALID for negative counts, NULL
+ * arrays of positive length, T <= 0, v <= 0 or non-finite inputs; nothing is
+ * written then. */
+int cph_predict_delta_e0(int n_sites, const double* pka_red, const double* pka_oxi, double T,
+                         double v, double* delta_e0);
+int cph_predict_e0(int n_pts, const double* pH, double e0_prot, int n_sites,
+                   const double* pka_red, const double* pka_oxi, double T, double v,
+                   double* e0);
+int cph_predict_sum_pka(int n_pts, const double* E, double e0_prot, double e0_deprot,
+                        int n_sites, const double* pka_red, double T, double v,
+                        double* sum_pka);
+
 /* ---- differentiable GB energy (device buffers, caller-owned) */
 
 /* E_GB of n_rep independent configurations of one n-atom system (no Coulomb,

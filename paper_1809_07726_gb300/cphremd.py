@@ -134,6 +134,9 @@ def lib():
             "cph_reset_observables": ([vp, vp], i),
             "cph_fit_hill": ([i, i, vp, vp, C.c_double, C.c_double, C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(C.c_double)], i),
+            "cph_predict_delta_e0": ([i, vp, vp, d, d, C.POINTER(C.c_double)], i),
+            "cph_predict_e0": ([i, vp, d, i, vp, vp, d, d, vp], i),
+            "cph_predict_sum_pka": ([i, vp, d, d, i, vp, d, d, vp], i),
             "cph_get_reference_energies": ([vp, vp], i),
             "cph_get_mc_records": ([vp, vp, i, vp, vp], i),
             "cph_get_exchange_records": ([vp, vp, i, vp, vp], i),
@@ -423,6 +426,38 @@ def fit_hill(kind, x, f, T=300.0, v=1.0):
     _check(lib().cph_fit_hill(kind, x.size, _p(x), _p(f), float(T), float(v), C.byref(x0),
                               C.byref(n), C.byref(rss)))
     return x0.value, n.value, rss.value
+
+
+def predict_delta_e0(pka_red, pka_oxi, T, v=1.0):
+    """Eq (6): E0_prot - E0_deprot (V) from the per-site pKa_red, pKa_oxi."""
+    a, b = _f64(pka_red).reshape(-1), _f64(pka_oxi).reshape(-1)
+    if a.size != b.size:
+        raise ValueError("pka_red and pka_oxi differ in length")
+    out = C.c_double()
+    _check(lib().cph_predict_delta_e0(a.size, _p(a), _p(b), float(T), float(v), C.byref(out)))
+    return out.value
+
+
+def predict_e0(pH, e0_prot, pka_red, pka_oxi, T, v=1.0):
+    """Eq (7): the pH-dependent E0 (V) at every pH."""
+    x = _f64(pH).reshape(-1)
+    a, b = _f64(pka_red).reshape(-1), _f64(pka_oxi).reshape(-1)
+    if a.size != b.size:
+        raise ValueError("pka_red and pka_oxi differ in length")
+    out = np.zeros(x.size)
+    _check(lib().cph_predict_e0(x.size, _p(x), float(e0_prot), a.size, _p(a), _p(b), float(T),
+                                float(v), _p(out)))
+    return out
+
+
+def predict_sum_pka(E, e0_prot, e0_deprot, pka_red, T, v=1.0):
+    """Eq (8): the sum of the pH sites' pKa values at every redox potential E (V)."""
+    x = _f64(E).reshape(-1)
+    a = _f64(pka_red).reshape(-1)
+    out = np.zeros(x.size)
+    _check(lib().cph_predict_sum_pka(x.size, _p(x), float(e0_prot), float(e0_deprot), a.size,
+                                     _p(a), float(T), float(v), _p(out)))
+    return out
 
 
 def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.0,

@@ -155,3 +155,89 @@ extern "C" int cph_fit_hill(int kind, int n_pts, const double* x, const double* 
     if (rss_out) *rss_out = S;
     return CPH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Predictions of eqs (6)-(8) ("Temperature dependence in predicting E0 vs pH
+// and pKa vs redox potential": Figure 6's solid lines come from eqs (7) and (8)
+// with parameters taken from the simulation).  A redox-active group couples to
+// n_sites pH-active groups; pKa_red / pKa_oxi of site i are its pKa with the
+// redox group reduced / oxidised, E0_prot / E0_deprot the redox group's E0
+// with every pH site protonated / deprotonated.
+//   eq (6): v F (E0_prot - E0_deprot) = kB T ln 10 sum_i (pKa_red,i - pKa_oxi,i)
+//   eq (7): E0(pH) = E0_prot + kB T / (v F) sum_i ln((10^-pKa_red,i + 10^-pH)
+//                                                    / (10^-pKa_oxi,i + 10^-pH))
+//   eq (8): sum_i pKa_i(E) = sum_i pKa_red,i + log10((e^(-v F E0_prot / kB T)
+//                    + e^(-F E / kB T)) / (e^(-v F E0_deprot / kB T) + e^(-F E / kB T)))
+// The logarithm in eq (8) is read as base 10 (it adds to a sum of pKa values);
+// v multiplies the E0 terms and not the E term, as printed.  Sums of
+// exponentials are taken in log space (log(a + b) = max + log1p(exp(-|d|)))
+// so no term under- or overflows.
+namespace {
+
+inline double log_add(double a, double b) { // ln(e^a + e^b)
+    const double m = std::fmax(a, b);
+    return m + std::log1p(std::exp(-std::fabs(a - b)));
+}
+
+bool finite_all(const double* p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+} // namespace
+
+extern "C" int cph_predict_delta_e0(int n_sites, const double* pka_red, const double* pka_oxi,
+                                    double T, double v, double* delta_e0) {
+    if (n_sites < 0 || (n_sites > 0 && (!pka_red || !pka_oxi)) || !delta_e0)
+        return afail("cph_predict_delta_e0: bad arguments");
+    if (!(T > 0.0) || !(v > 0.0) || !std::isfinite(T) || !std::isfinite(v))
+        return afail("cph_predict_delta_e0: needs T > 0 and v > 0");
+    if (!finite_all(pka_red, n_sites) || !finite_all(pka_oxi, n_sites))
+        return afail("cph_predict_delta_e0: non-finite pKa");
+    double s = 0.0;
+    for (int i = 0; i < n_sites; ++i) s += pka_red[i] - pka_oxi[i];
+    *delta_e0 = cph::kBoltzmann * T * cph::kLn10 * s / (v * cph::kFaraday);
+    return CPH_OK;
+}
+
+extern "C" int cph_predict_e0(int n_pts, const double* pH, double e0_prot, int n_sites,
+                              const double* pka_red, const double* pka_oxi, double T, double v,
+                              double* e0) {
+    if (n_pts < 0 || (n_pts > 0 && (!pH || !e0)) || n_sites < 0 ||
+        (n_sites > 0 && (!pka_red || !pka_oxi)))
+        return afail("cph_predict_e0: bad arguments");
+    if (!(T > 0.0) || !(v > 0.0) || !std::isfinite(T) || !std::isfinite(v) || !std::isfinite(e0_prot))
+        return afail("cph_predict_e0: needs T > 0, v > 0 and a finite E0_prot");
+    if (!finite_all(pH, n_pts) || !finite_all(pka_red, n_sites) || !finite_all(pka_oxi, n_sites))
+        return afail("cph_predict_e0: non-finite pH or pKa");
+    const double scale = cph::kBoltzmann * T / (v * cph::kFaraday);
+    for (int k = 0; k < n_pts; ++k) {
+        const double lp = -cph::kLn10 * pH[k];
+        double s = 0.0;
+        for (int i = 0; i < n_sites; ++i)
+            s += log_add(-cph::kLn10 * pka_red[i], lp) - log_add(-cph::kLn10 * pka_oxi[i], lp);
+        e0[k] = e0_prot + scale * s;
+    }
+    return CPH_OK;
+}
+
+extern "C" int cph_predict_sum_pka(int n_pts, const double* E, double e0_prot, double e0_deprot,
+                                   int n_sites, const double* pka_red, double T, double v,
+                                   double* sum_pka) {
+    if (n_pts < 0 || (n_pts > 0 && (!E || !sum_pka)) || n_sites < 0 || (n_sites > 0 && !pka_red))
+        return afail("cph_predict_sum_pka: bad arguments");
+    if (!(T > 0.0) || !(v > 0.0) || !std::isfinite(T) || !std::isfinite(v) ||
+        !std::isfinite(e0_prot) || !std::isfinite(e0_deprot))
+        return afail("cph_predict_sum_pka: needs T > 0, v > 0 and finite E0 values");
+    if (!finite_all(E, n_pts) || !finite_all(pka_red, n_sites))
+        return afail("cph_predict_sum_pka: non-finite E or pKa");
+    const double b = cph::kFaraday / (cph::kBoltzmann * T);
+    double base = 0.0;
+    for (int i = 0; i < n_sites; ++i) base += pka_red[i];
+    for (int k = 0; k < n_pts; ++k) {
+        const double le = -b * E[k];
+        sum_pka[k] = base + (log_add(-v * b * e0_prot, le) - log_add(-v * b * e0_deprot, le)) / cph::kLn10;
+    }
+    return CPH_OK;
+}
