@@ -178,7 +178,20 @@ typedef struct cph_run_params {
      * constraints. */
     int shake;
     double shake_tol;               /* > 0 when shake = 1, e.g. 1e-8 */
+    /* Energy eps of the T exchange, eq (5) ("the energy of the system"):
+     * CPH_TEX_POTENTIAL (0, default): the total potential energy U.
+     * CPH_TEX_SEMIGRAND (1): U - sum_k U_ref,k(s_k)
+     *   + sum_{redox k} F N_e,k(s_k) (E - E0_ref,k), the part of the C(pH,E)MD
+     *   weight exp(-G/kT) that scales with 1/kT (G the state free energy of the
+     *   MC moves with U_el completed to U; the pH term does not scale with T).
+     *   With it one T attempt is in detailed balance with the C(pH,E)MD
+     *   ensemble of each walker's states; the two differ only when the pair's
+     *   site states differ.  Other values: CPH_E_INVALID. */
+    int t_exchange_energy;
 } cph_run_params;
+
+#define CPH_TEX_POTENTIAL 0
+#define CPH_TEX_SEMIGRAND 1
 
 typedef struct cph_engine cph_engine; /* opaque */
 

@@ -372,5 +372,5 @@ def fit_hill(kind, x, f, T=300.0, v=1.0):
     return float(res.x[0]), float(res.x[1]), float(np.sum(res.fun ** 2))
 
 
-from .run import (Walkers, exchange_attempt, exchange_exponent, mc_sweep,  # noqa: E402,F401
-                  reference_energies, run_schedule)
+from .run import (Walkers, exchange_attempt, exchange_energy, exchange_exponent,  # noqa: E402,F401
+                  mc_sweep, reference_energies, run_schedule)

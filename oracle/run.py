@@ -62,6 +62,10 @@ class Walkers:
     t: int = 0
     shake: bool = False
     shake_tol: float = 1e-10
+    # energy of eq (5): "potential" = U (total potential energy); "semigrand" =
+    # U - sum_k U_ref,k(s_k) + sum_redox F N_e,k(s_k) (E - E0_ref,k), the part of
+    # the C(pH,E)MD weight that scales with 1/kT
+    t_energy: str = "potential"
 
     def __post_init__(self):
         if self.shake:
@@ -194,6 +198,31 @@ def _line_slots(W: Walkers, dim: str):
     return lines
 
 
+def exchange_energy(W: Walkers, w: int) -> float:
+    """The energy eq (5) uses for walker w at its current condition.  The paper
+    calls it "the energy of the system" (T-REMD section); "potential" takes
+    the total potential energy U.  In C(pH,E)MD the sampled weight of a
+    walker is exp(-(U - sum_k U_ref,k + F sum_redox N_e,k (E - E0_ref,k)) / kT)
+    times 10^-(N_H (pH - pKa_ref)) (the state free energy G of the MC moves
+    with U_el completed to U), so the part that scales with 1/kT is
+    U - sum_k U_ref,k(s_k) + sum_redox F N_e,k(s_k) (E - E0_ref,k): "semigrand"
+    takes that one.  The two differ when the pair's site states differ."""
+    if W.t_energy == "potential":
+        return float(W.U[w])
+    if W.t_energy != "semigrand":
+        raise ValueError(f"unknown T-exchange energy {W.t_energy!r}")
+    sysd = W.systems[W.sys_of[w]]
+    ur = W.uref[W.sys_of[w]]
+    E = W.cond(w)[0]
+    e = float(W.U[w])
+    for k, st in enumerate(sysd.sites):
+        b = int(W.state[w][k])
+        e -= ur[k][b]
+        if st.kind == "redox":
+            e += FARADAY * st.n_elec[b] * (E - st.ref)
+    return e
+
+
 def exchange_exponent(dim, ci, cj, Ui, Uj, NHi, NHj, Nei, Nej):
     """Exponent x of min{1, e^x} for swapping walkers i and j with conditions
     ci, cj = (E, pH, T): eq (3) for pH, eq (4) for E, eq (5) for T."""
@@ -213,7 +242,8 @@ def exchange_attempt(W: Walkers, dim: str, t: int):
     Exponents (i = walker at slot m, j = walker at slot m+1):
       pH, eq (3): ln10 (pH_i - pH_j)(N_H,i - N_H,j)
       E,  eq (4): F/(kT) (E_i - E_j)(N_e,i - N_e,j)
-      T,  eq (5): (1/kT_i - 1/kT_j)(U_i - U_j), U = total potential energy
+      T,  eq (5): (1/kT_i - 1/kT_j)(U_i - U_j), U = exchange_energy (the
+                  total potential energy by default)
     Accept iff ln u < x with u = Philox(slot m, dim, t, exchange).  On a T swap
     each walker's velocities are scaled by sqrt(T_new / T_old)."""
     par = W.n_attempts[dim] % 2
@@ -227,7 +257,9 @@ def exchange_attempt(W: Walkers, dim: str, t: int):
                 continue
             Ei, pHi, Ti = W.cond(wi)
             Ej, pHj, Tj = W.cond(wj)
-            x = exchange_exponent(dim, (Ei, pHi, Ti), (Ej, pHj, Tj), W.U[wi], W.U[wj],
+            Ui = exchange_energy(W, wi) if dim == "T" else 0.0
+            Uj = exchange_energy(W, wj) if dim == "T" else 0.0
+            x = exchange_exponent(dim, (Ei, pHi, Ti), (Ej, pHj, Tj), Ui, Uj,
                                   W.n_prot(wi), W.n_prot(wj), W.n_elec(wi), W.n_elec(wj))
             u = uniforms(W.seed, s1, di, t, PURPOSE_EXCHANGE)
             lnu = math.log(u[0])

@@ -21,6 +21,7 @@ DIM_E, DIM_PH, DIM_T, DIM_NEXT = 0, 1, 2, -1
 MC_PH, MC_REDOX, MC_BOTH = 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_REPLICA = 0, 1
+TEX_POTENTIAL, TEX_SEMIGRAND = 0, 1
 NTERMS = 6
 MAX_STATES = 8
 FIT_PH, FIT_REDOX = 1, 2
@@ -66,7 +67,8 @@ class GBParams(C.Structure):
 class RunParams(C.Structure):
     _fields_ = [("gb", GBParams), ("dt", C.c_double), ("gamma_ln", C.c_double),
                 ("precision", C.c_int), ("mc_ph_every", C.c_int), ("mc_redox_every", C.c_int),
-                ("exchange_every", C.c_int), ("shake", C.c_int), ("shake_tol", C.c_double)]
+                ("exchange_every", C.c_int), ("shake", C.c_int), ("shake_tol", C.c_double),
+                ("t_exchange_energy", C.c_int)]
 
 
 class MCRecord(C.Structure):
@@ -462,7 +464,8 @@ def predict_sum_pka(E, e0_prot, e0_deprot, pka_red, T, v=1.0):
 
 def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.0,
                 mc_ph_every=10, mc_redox_every=10, exchange_every=100, gb=None,
-                velocities=None, shake=False, shake_tol=1e-10) -> Engine:
+                velocities=None, shake=False, shake_tol=1e-10,
+                t_exchange_energy=TEX_POTENTIAL) -> Engine:
     """cph_init_system for a list of ``synth.System`` and a ``synth.Grid``."""
     keep = _Keep()
     descs = (SystemDesc * len(systems))()
@@ -476,7 +479,7 @@ def init_system(systems, grid, seed, precision=PREC_FP32, dt=0.002, gamma_ln=10.
     for k, name in enumerate(grid.order):
         g.order[k] = DIM_NAMES[name]
     p = RunParams(gb or default_gb(), dt, gamma_ln, precision, mc_ph_every, mc_redox_every,
-                  exchange_every, 1 if shake else 0, shake_tol)
+                  exchange_every, 1 if shake else 0, shake_tol, int(t_exchange_energy))
     out = C.c_void_p()
     rc = lib().cph_init_system(C.cast(descs, C.c_void_p), len(systems), C.byref(g), C.byref(p),
                                C.c_uint64(seed), C.byref(out))

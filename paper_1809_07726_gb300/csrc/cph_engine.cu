@@ -352,6 +352,19 @@ __device__ inline double walker_energy(const View& V, int w) {
     return (double)e / kScaleE;
 }
 
+// Semi-grand exchange energy of walker w at redox potential E (T exchange with
+// CPH_TEX_SEMIGRAND): U - sum_k U_ref,k(s_k) + sum_redox F N_e,k(s_k) (E - E0_ref,k).
+__device__ inline double walker_semigrand_energy(const View& V, int w, double E) {
+    double e = walker_energy(V, w);
+    const int s = V.w_sys[w];
+    for (int g = V.sys_site_off[s], k = 0; g < V.sys_site_off[s + 1]; ++g, ++k) {
+        const int b = V.site_state[V.w_site_off[w] + k], no = V.site_noff[g];
+        e -= V.site_uref[no + b];
+        if (V.site_kind[g] == CPH_SITE_REDOX) e += kFaraday * (double)V.site_ne[no + b] * (E - V.site_ref[g]);
+    }
+    return e;
+}
+
 constexpr int kExThreads = 256;
 
 __global__ void __launch_bounds__(kExThreads) k_exchange(View V, int dim_req, int s_off) {
@@ -416,7 +429,16 @@ __global__ void __launch_bounds__(kExThreads) k_exchange(View V, int dim_req, in
             const double e1 = V.gE[s1 % V.nE], e2 = V.gE[s2 % V.nE];
             x = kFaraday / (kBoltzmann * T1) * (e1 - e2) * (double)(walker_nelec(V, w1) - walker_nelec(V, w2));
         } else {
-            x = (1.0 / (kBoltzmann * T1) - 1.0 / (kBoltzmann * T2)) * (walker_energy(V, w1) - walker_energy(V, w2));
+            double u1, u2;
+            if (V.tex_semigrand) { // a T line shares E: s1 and s2 have the same E index
+                const double e = V.gE[s1 % V.nE];
+                u1 = walker_semigrand_energy(V, w1, e);
+                u2 = walker_semigrand_energy(V, w2, e);
+            } else {
+                u1 = walker_energy(V, w1);
+                u2 = walker_energy(V, w2);
+            }
+            x = (1.0 / (kBoltzmann * T1) - 1.0 / (kBoltzmann * T2)) * (u1 - u2);
         }
         const U4 u = draw(V.seed, (uint32_t)s1, (uint32_t)dim, t, kRngExchange);
         const double lnu = log(unit_open(u.a));
@@ -1008,6 +1030,8 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         return fail(nullptr, CPH_E_INVALID, "dt, gamma_ln, eps_in, eps_out must be positive");
     if (p->mc_ph_every < 0 || p->mc_redox_every < 0 || p->exchange_every < 0)
         return fail(nullptr, CPH_E_INVALID, "negative interval");
+    if (p->t_exchange_energy != CPH_TEX_POTENTIAL && p->t_exchange_energy != CPH_TEX_SEMIGRAND)
+        return fail(nullptr, CPH_E_INVALID, "unknown T-exchange energy %d", p->t_exchange_energy);
     if (grid->nE < 1 || grid->npH < 1 || grid->nT < 1 || !grid->E || !grid->pH || !grid->T ||
         !grid->system_of_slot)
         return fail(nullptr, CPH_E_INVALID, "bad grid");
@@ -1495,6 +1519,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         V.smax32 = (float)smax;
     }
     V.seed = seed;
+    V.tex_semigrand = p->t_exchange_energy == CPH_TEX_SEMIGRAND ? 1 : 0;
     Item* di;
     TRY(upload(E, items, &di)); E->d_items = di;
     TRY(upload(E, items_by_w, &di)); E->d_items_by_w = di;

@@ -108,6 +108,7 @@ struct View {
     const float4* pb32;  // per system atom, static: (s, rt, 1/rt, 0)
     const float2* plj32; // per system atom, static: (sigma/2, sqrt(eps))
     unsigned long long seed;
+    int tex_semigrand; // T exchange on U - sum U_ref + sum_redox F N_e (E - E0_ref) instead of U
 };
 
 } // namespace cph

@@ -4,6 +4,7 @@ differences in test_oracle_physics.py)."""
 import numpy as np
 import pytest
 
+import errlog
 import oracle
 from paper_1809_07726_gb300 import build, cphremd, synth
 
@@ -75,6 +76,9 @@ def test_full_size_batch_sampled_replica():
     r = 77
     xr, qr, rr = (a[r].astype(np.float32).astype(np.float64) for a in (x, q, rho))
     Eo, gx, gq, gr = oracle.gb_grad(xr, qr, rr, s.screen.astype(np.float32).astype(np.float64))
+    errlog.record("GB energy and gradient, 128 x 8000 (FP32)", replica=r, energy_rel=abs(E[r] - Eo) / abs(Eo),
+                  dx_rms_rel=_rel_rms(dx[r], gx), dq_rms_rel=_rel_rms(dq[r], gq),
+                  drho_rms_rel=_rel_rms(dr[r], gr))
     assert abs(E[r] - Eo) <= 1e-6 * abs(Eo)
     assert _rel_rms(dx[r], gx) <= 1e-5
     assert _rel_rms(dq[r], gq) <= 1e-5

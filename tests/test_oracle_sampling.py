@@ -318,3 +318,73 @@ def test_exchange_acceptance_rate_matches_min_one_exp():
     x = (1 / (KB * 300.0) - 1 / (KB * 310.0)) * (-100.0 + 99.0)
     p = min(1.0, math.exp(x))
     assert abs(acc / n - p) < 4 * math.sqrt(p * (1 - p) / n)
+
+
+def _t_line_matrix(conds, eps, parity):
+    """Exact transition matrix of one T attempt on one line, walker w carrying
+    the exchange energy eps[w]."""
+    nslot = len(conds)
+    perms = list(itertools.permutations(range(nslot)))
+    idx = {p: i for i, p in enumerate(perms)}
+    P = np.zeros((len(perms), len(perms)))
+    pairs = [(m, m + 1) for m in range(parity, nslot - 1, 2)]
+    for p in perms:
+        for choice in itertools.product([0, 1], repeat=len(pairs)):
+            prob = 1.0
+            q = list(p)
+            for (a, b), c in zip(pairs, choice):
+                x = oracle.exchange_exponent("T", conds[a], conds[b], eps[p[a]], eps[p[b]], 0, 0, 0, 0)
+                acc = min(1.0, math.exp(x))
+                prob *= acc if c else 1 - acc
+                if c:
+                    q[a], q[b] = q[b], q[a]
+            P[idx[p], idx[tuple(q)]] += prob
+    return perms, P
+
+
+@pytest.mark.parametrize("choice", ["potential", "semigrand"])
+def test_t_exchange_energy_choices_detailed_balance(choice):
+    """Walkers in different redox states and with different site reference
+    energies along a T line at E != E0_ref.  The C(pH,E)MD weight of walker w
+    at temperature T is exp(-(U - U_ref + F N_e (E - E0_ref)) / kT) (the pH
+    factor is the same at every slot of a T line).  With the semi-grand
+    exchange energy one attempt is in detailed balance with that weight; with
+    the potential energy it is in detailed balance with exp(-U / kT) only, and
+    not with the C(pH,E)MD weight."""
+    rng = np.random.default_rng(11)
+    E, e0_ref, n = -0.15, -0.2, 4
+    conds = [(E, 7.0, t) for t in 300.0 * 1.06 ** np.arange(n)]
+    U = rng.normal(-500.0, 1.5, n)
+    uref = rng.normal(-40.0, 1.0, n)
+    Ne = np.array([0, 1, 1, 0])
+    full = U - uref + FARADAY * Ne * (E - e0_ref)
+    eps = full if choice == "semigrand" else U
+
+    def lw(perm, energy):
+        return sum(-energy[w] / (KB * conds[slot][2]) for slot, w in enumerate(perm))
+
+    for parity in (0, 1):
+        perms, P = _t_line_matrix(conds, eps, parity)
+        for energy, should_hold in ((full, choice == "semigrand"), (U, choice == "potential")):
+            w = np.array([lw(p, energy) for p in perms])
+            pi = np.exp(w - w.max())
+            pi /= pi.sum()
+            dev = np.abs(pi @ P - pi).max() / pi.max()
+            assert (dev < 1e-10) == should_hold, (choice, parity, dev)
+
+
+def test_semigrand_exchange_energy_of_a_walker():
+    """exchange_energy: the potential energy, less the sites' reference
+    energies, plus F N_e (E - E0_ref) per redox site."""
+    s = synth.make_system(40, 12, n_ph=2, ph_atoms=(6, 6), redox_atoms=8)
+    grid = synth.Grid(np.array([-0.1]), np.array([6.0]), np.array([300.0]), np.zeros(1, np.int32))
+    W = oracle.Walkers([s], grid, seed=1, t_energy="semigrand")
+    W.state[0][:] = [1, 0, 1]
+    W.U[0] = -321.5
+    ur = W.uref[0]
+    red = [k for k, st in enumerate(s.sites) if st.kind == "redox"][0]
+    want = -321.5 - sum(ur[k][W.state[0][k]] for k in range(len(s.sites))) \
+        + FARADAY * s.sites[red].n_elec[W.state[0][red]] * (-0.1 - s.sites[red].ref)
+    assert oracle.exchange_energy(W, 0) == pytest.approx(want, rel=1e-14)
+    W.t_energy = "potential"
+    assert oracle.exchange_energy(W, 0) == -321.5
