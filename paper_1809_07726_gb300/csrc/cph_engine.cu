@@ -969,6 +969,10 @@ namespace {
 // Replaces the current item arrays and drops captured graphs (they hold the
 // old item pointers).
 int build_sym_items(cph_engine* E, int chunk) {
+    // the pair passes sum i-side partials per aligned group of kSymG j-tiles:
+    // items must start and end on group boundaries (or at the row's end)
+    if (chunk < kSymG || chunk % kSymG != 0 || kSymI % (kSymG * kSymJ) != 0)
+        return fail(E, CPH_E_INVALID, "work-item size %d is not a multiple of %d j-tiles", chunk, kSymG);
     const int W = E->V.W;
     std::vector<SymItem> sym, by_w;
     std::vector<int> w_off(W + 1, 0);

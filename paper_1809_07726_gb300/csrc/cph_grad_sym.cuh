@@ -379,12 +379,16 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
             S.c[r] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
         }
         __syncthreads();
-        for (int pr = 0; pr < npair; ++pr) {
-            float2 ai[2][5], aj[5], ei[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        // i-side partials of the staged group in FP32 (tile pairs in turn, halves
+        // = even / odd tiles), one fixed-point conversion per group; groups are
+        // aligned runs of kGG j-tiles, whatever the item's chunk
+        float2 ai[2][5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                ai[0][c] = ai[1][c] = aj[c] = make_float2(0.f, 0.f);
-            }
+        for (int c = 0; c < 5; ++c) ai[0][c] = ai[1][c] = make_float2(0.f, 0.f);
+        for (int pr = 0; pr < npair; ++pr) {
+            float2 aj[5], ei[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+            for (int c = 0; c < 5; ++c) aj[c] = make_float2(0.f, 0.f);
             uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
             bool masked = false;
 #pragma unroll
@@ -406,13 +410,6 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
             }
             if (BACKWARD) {
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int row = warp * 64 + u * 32 + lane;
-#pragma unroll
-                    for (int c = 0; c < 5; ++c)
-                        sfx[c][row] += to_fixed(ai[u][c].x, (float)kScaleE) + to_fixed(ai[u][c].y, (float)kScaleE);
-                }
-#pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     const float sgn = c >= 2 ? -1.f : 1.f;
                     red[2 * pr][warp][lane][c] = sgn * aj[c].x;
@@ -421,6 +418,12 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
             }
         }
         if (BACKWARD) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int row = warp * 64 + u * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) sfx[c][row] += to_fixed(ai[u][c].x + ai[u][c].y, (float)kScaleE);
+            }
             __syncthreads();
             for (int v = tid; v < ng * kGJ * 5; v += kGT) {
                 const int gt = v / (kGJ * 5), rem = v % (kGJ * 5), j = rem / 5, c = rem % 5;
@@ -690,10 +693,14 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
             S.m[r] = make_float2(v[0][6], v[1][6]);
         }
         __syncthreads();
-        for (int pr = 0; pr < npair; ++pr) {
-            float2 ai[2][5], aj[5];
+        // i-side partials of the staged group in FP32, one conversion per group
+        float2 ai[2][5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) ai[0][c] = ai[1][c] = aj[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 5; ++c) ai[0][c] = ai[1][c] = make_float2(0.f, 0.f);
+        for (int pr = 0; pr < npair; ++pr) {
+            float2 aj[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) aj[c] = make_float2(0.f, 0.f);
             uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
             bool masked = false;
 #pragma unroll
@@ -708,18 +715,17 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
             if (masked) gchain_tile<true, CUT>(sj[pr], lane, I, ai, aj, sk, band);
             else gchain_tile<false, CUT>(sj[pr], lane, I, ai, aj, sk, band);
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int row = warp * 64 + u * 32 + lane;
-#pragma unroll
-                for (int c = 0; c < 5; ++c)
-                    sfx[c][row] += to_fixed(ai[u][c].x, (float)kScaleE) + to_fixed(ai[u][c].y, (float)kScaleE);
-            }
-#pragma unroll
             for (int c = 0; c < 5; ++c) {
                 const float sgn = c < 3 ? -1.f : 1.f;
                 red[2 * pr][warp][lane][c] = sgn * aj[c].x;
                 red[2 * pr + 1][warp][lane][c] = sgn * aj[c].y;
             }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int row = warp * 64 + u * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) sfx[c][row] += to_fixed(ai[u][c].x + ai[u][c].y, (float)kScaleE);
         }
         __syncthreads();
         for (int v = tid; v < ng * kGJ * 5; v += kGT) {

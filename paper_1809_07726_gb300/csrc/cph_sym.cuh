@@ -356,11 +356,16 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
             }
         }
         __syncthreads();
+        // i-side partials of the whole staged group, summed in FP32 in a fixed
+        // order (tile pairs in turn, halves = even / odd tiles) and converted to
+        // fixed point once per group: groups are the aligned runs of kSymG
+        // j-tiles (items start at a multiple of kSymG tiles and span a multiple
+        // of it), so the sums do not depend on the item's chunking
+        float2 acc[2][4] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}},
+                            {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
         for (int pr = 0; pr < npair; ++pr) {
             const int jtA = g0 + 2 * pr; // tile B (jtA + 1) may lie past the item: padding
             float2 ja[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            float2 acc[2][4] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}},
-                                {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
             GbMask m = {};
             bool masked = false;
 #pragma unroll
@@ -376,17 +381,15 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
             }
             if (masked) gb_tile<true, ENERGY, SALT>(sj[pr], lane, I, acc, ja, m, tau, iei, kappa, ieo, egb, ec, elj);
             else gb_tile<false, ENERGY, SALT>(sj[pr], lane, I, acc, ja, m, tau, iei, kappa, ieo, egb, ec, elj);
-            // per-tile conversion (each half is one tile): independent of the item's chunking
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    sfx[c][warp * 64 + u * 32 + lane] +=
-                        to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
             // lane l now holds the partials of partner l of both tiles
             *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(-ja[0].x, -ja[1].x, -ja[2].x, ja[3].x);
             *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(-ja[0].y, -ja[1].y, -ja[2].y, ja[3].y);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                sfx[c][warp * 64 + u * 32 + lane] += to_fixed(acc[u][c].x + acc[u][c].y, (float)kScaleE);
         __syncthreads();
         // add the four warps' partials of every staged partner and send them
         for (int v = tid; v < ng * kSymJ * 4; v += kSymThreads) {
@@ -621,10 +624,12 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
             }
         }
         __syncthreads();
+        // i-side partials of the staged group in FP32, one conversion per group
+        // (aligned runs of kSymG j-tiles: independent of the item's chunking)
+        float2 acc[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
         for (int pr = 0; pr < npair; ++pr) {
             const int jtA = g0 + 2 * pr;
             float2 ja[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            float2 acc[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
             uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
             bool masked = false;
 #pragma unroll
@@ -641,16 +646,14 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_chain_sym(const SymItem* __r
             }
             if (masked) chain_tile<true, CUT>(sj[pr], lane, I, acc, ja, sk, band);
             else chain_tile<false, CUT>(sj[pr], lane, I, acc, ja, sk, band);
-            // per-tile conversion (each half is one tile)
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    sfx[c][warp * 64 + u * 32 + lane] +=
-                        to_fixed(acc[u][c].x, (float)kScaleE) + to_fixed(acc[u][c].y, (float)kScaleE);
             *reinterpret_cast<float4*>(red[2 * pr][warp][lane]) = make_float4(-ja[0].x, -ja[1].x, -ja[2].x, 0.f);
             *reinterpret_cast<float4*>(red[2 * pr + 1][warp][lane]) = make_float4(-ja[0].y, -ja[1].y, -ja[2].y, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                sfx[c][warp * 64 + u * 32 + lane] += to_fixed(acc[u][c].x + acc[u][c].y, (float)kScaleE);
         __syncthreads();
         for (int v = tid; v < ng * kSymJ * 3; v += kSymThreads) {
             const int g = v / (kSymJ * 3), rem = v % (kSymJ * 3), j = rem / 3, c = rem % 3;

@@ -28,3 +28,18 @@ def test_far_forms_cost_less_in_both_directions():
     # the backward totals are the sums of their three passes' forms
     assert bench.BACKWARD_COST[0] == bench.PASS_COST["born"][0] + 32 + 46
     assert bench.BACKWARD_FAR_COST[0] == bench.PASS_COST["born"][0] + 22 + 46
+
+
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (100, 5), (200, 3), (7, 3), (199, 5), (150, 10)])
+def test_timed_window_holds_the_schedule_events(steps, warmup):
+    """The window leaves room for the warm-up steps after step 0, holds an
+    exchange step, and holds MC steps in their proportion (one per 10 steps,
+    give or take the ends); whole periods when K is a multiple of 100."""
+    first = bench.window_start(steps, warmup)
+    assert first - warmup >= 1
+    ev = bench.schedule_events(first, steps)
+    assert ev["last_step"] - ev["first_step"] + 1 == steps
+    assert ev["exchange_steps"] >= 1
+    assert abs(ev["mc_ph_steps"] - steps / 10) <= 1
+    if steps % 100 == 0:
+        assert ev["exchange_steps"] == steps // 100 and ev["mc_ph_steps"] == steps // 10

@@ -195,9 +195,9 @@ def test_mc_sweep_matches_oracle(prec, kappa, rgbmax):
 def test_exchange_attempts_match_oracle(prec, tex):
     """pH and E exchanges (integer counts: exact exponents) and T exchanges
     (energies from the engine vs the oracle) on an 4 x 2 x 3 grid, in both
-    precision modes.  In FP32 mode the T exponent (1/kT_i - 1/kT_j)(U_i - U_j)
-    carries the energy bar: |dx| <= |1/kT_i - 1/kT_j| ENERGY_REL (S_i + S_j),
-    S = sum of the magnitudes of a walker's energy terms; a decision inside
+    precision modes.  The T exponent (1/kT_i - 1/kT_j)(U_i - U_j) carries the
+    mode's energy bar: |dx| <= |1/kT_i - 1/kT_j| e (S_i + S_j), e = 1e-6 (FP32)
+    or 1e-10 (FP64), S = sum of the magnitudes of a walker's energy terms; a decision inside
     that band (or the MC band 2e-4 max(1,|x|), whichever is wider) is counted,
     and the oracle then follows the engine's condition map.  "semigrand" runs
     eq (5) on U - sum U_ref + sum_redox F N_e (E - E0_ref) (CPH_TEX_SEMIGRAND)
@@ -248,10 +248,11 @@ def test_exchange_attempts_match_oracle(prec, tex):
             assert (r.walker_lo, r.walker_hi) == (e[3], e[4])
             assert r.lnu == e[6]
             tol = 1e-9 * max(1.0, abs(e[5]))
-            if dim == "T" and prec == cphremd.PREC_FP32:
+            if dim == "T":  # the energy bar of the mode, carried through eq (5)
                 Ti, Tj = W.grid.T[r.slot_lo // 8], W.grid.T[r.slot_hi // 8]
                 dbeta = abs(1.0 / (oracle.KB * Ti) - 1.0 / (oracle.KB * Tj))
-                tol = max(tol, dbeta * ENERGY_REL * (scale[e[3]] + scale[e[4]]))
+                ebar = ENERGY_REL if prec == cphremd.PREC_FP32 else 1e-10
+                tol = max(tol, dbeta * ebar * (scale[e[3]] + scale[e[4]]))
             assert abs(r.x - e[5]) <= tol, (dim, r.x, e[5], tol)
             worst = max(worst, abs(r.x - e[5]))
             seen += 1
