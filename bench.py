@@ -51,8 +51,9 @@ WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-a
 PASS_COST = {"born": (24, 1), "gb": (40, 3), "chain": (32, 1)}
 # A GB pair with D = r^2 / (4 R_i R_j) >= 18 needs no exponential and no second
 # square root (1/f = 1/r and e^-D to FP32 precision): distance 6, D 2, LJ 9,
-# charges and eps 3, combined GB + Coulomb force factor 3, forces 6, 1 MUFU.
-GB_FAR_COST = (29, 1)
+# charges and eps 2, combined GB + Coulomb force factor ((q_i q_j / r) / eps_out
+# + LJ) / r^2 2, forces 6, 1 MUFU.
+GB_FAR_COST = (27, 1)
 GB_FAR_D = 18.0
 # GB-energy backward (Born radii recomputed): born 24/1 + GB adjoint (energy,
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,

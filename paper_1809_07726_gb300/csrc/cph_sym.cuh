@@ -194,7 +194,7 @@ __device__ __forceinline__ void gb_tile(const GbJs& sj, int lane, const GbI2 (&I
                 const float2 l6 = __fmul2_rn(ep4, sr6);
                 const float2 lj = __fmul2_rn(l6, __ffma2_rn(c12, sr6, cm6));
                 // (Coulomb - tau GB) q_i q_j / r^3 = q_i q_j / (eps_out r^3)
-                const float2 fs = __ffma2_rn(__fmul2_rn(__fmul2_rn(qq, ieo2), rinv), rinv2, __fmul2_rn(lj, rinv2));
+                const float2 fs = __fmul2_rn(__ffma2_rn(__fmul2_rn(qq, rinv), ieo2, lj), rinv2);
                 a[u][0] = __ffma2_rn(fs, dx[u], a[u][0]);
                 a[u][1] = __ffma2_rn(fs, dy[u], a[u][1]);
                 a[u][2] = __ffma2_rn(fs, dz[u], a[u][2]);
