@@ -1280,7 +1280,10 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     std::vector<int> item_w_off(W + 1, 0);
     for (int w = 0; w < W; ++w) {
         const int s = w_sys[w], N = sys_n[s];
-        for (int it = 0; it * kTile < N; ++it) items_by_w.push_back(Item{w, it * kTile, sys_st_off[s] + it, 0});
+        // ordered passes: kWarpAtoms atoms i per CTA (one warp each); the masked
+        // j-tiles are those of the 128-atom i-tile the group lies in
+        for (int i0 = 0; i0 < N; i0 += kWarpAtoms)
+            items_by_w.push_back(Item{w, i0, sys_st_off[s] + i0 / kTile, 0});
         item_w_off[w + 1] = (int)items_by_w.size();
     }
     items = items_by_w;

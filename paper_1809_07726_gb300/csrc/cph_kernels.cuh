@@ -2,17 +2,20 @@
 // grid, bonded terms, Langevin integration, Monte-Carlo titration sweeps and
 // replica exchanges.  Host code lives in cph_engine.cu.
 //
-// Work decomposition of the three pair passes.  Every walker's atoms are cut
-// into i-tiles of kTile atoms; one CTA of kTile threads owns one i-tile, one
-// thread one atom i.  The CTA sweeps all j of its walker in tiles of kTile
-// staged in shared memory and read back as broadcasts, so every ordered pair
-// (i, j) is evaluated by the owner of i: no atomics, no cross-thread
-// reductions, and the result of an atom does not depend on the launch shape
-// (batched and per-replica launches agree bit for bit).  Positions are made
-// relative to the i-tile's first atom in FP64 before rounding to FP32, so
-// close pairs keep full FP32 precision in their separation.  In FP32 mode a
-// j-tile's partial sums are FP32 and are added into int64 fixed-point
-// accumulators (scales 2^32 and 2^40); in FP64 mode everything is FP64.
+// Work decomposition of the three ordered pair passes (FP64 mode).  One CTA of
+// kTile threads owns kWarpAtoms consecutive atoms i, one warp each; the CTA
+// sweeps all j of its walker in tiles of kTile staged in shared memory, lane l
+// of a warp taking entries l, l + 32, l + 64, l + 96 of every tile, so every
+// ordered pair (i, j) is evaluated by the warp of i.  A lane's partial sums
+// are added per tile into its accumulator; the warp's accumulators are
+// reduced by a fixed shuffle tree at the end, so the result of an atom does
+// not depend on the launch shape (batched and per-replica launches agree bit
+// for bit) and no atomics are needed.  A warp per atom spreads even a
+// 160-atom walker over 40 CTAs (FP64 arithmetic is a small fraction of the
+// chip's, so it must run on every SM).  Positions are made relative to the
+// group's first atom in FP64 before any rounding.  With Real = float the
+// per-tile partials go into int64 fixed-point accumulators (scales 2^32 and
+// 2^40); with double everything is FP64.
 //
 // Tiles in which some atom i of the CTA meets itself or an excluded partner
 // are listed per (system, i-tile) at set-up; only those run the masked loop.
@@ -23,7 +26,17 @@
 namespace cph {
 
 constexpr int kTile = 128;
+constexpr int kWarpAtoms = kTile / 32; // atoms i per CTA of the ordered passes
 constexpr float kFarF = 1.0e4f;
+
+// Sum of a lane accumulator over the warp by a fixed shuffle tree; lane 0
+// receives the total (the same order every time: deterministic).
+template <class T>
+__device__ __forceinline__ T warp_total(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 
 template <class Real>
 struct alignas(sizeof(Real) * 4) J4 {
@@ -79,8 +92,8 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
     __shared__ J4<Real> sj[kTile];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x;
-    const int i = it.i0 + tid;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = it.i0 + (tid >> 5);
     const bool vi = i < N;
     if (it.i0 == 0) {
         if (zero_energy && tid < kEAcc) V.eacc[w * kEAcc + tid] = 0;
@@ -120,8 +133,8 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         __syncthreads();
         Real part = 0;
         if (jt != next) {
-#pragma unroll 4
-            for (int k = 0; k < kTile; ++k) {
+#pragma unroll
+            for (int k = lane; k < kTile; k += 32) {
                 const J4<Real> b = sj[k];
                 const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
                 const Real r2 = dx * dx + dy * dy + dz * dz;
@@ -132,7 +145,8 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
             ++mp;
             next = mp < me ? V.mt_list[mp] : 0x7fffffff;
             const int dself = i - j0;
-            for (int k = 0; k < kTile; ++k) {
+#pragma unroll
+            for (int k = lane; k < kTile; k += 32) {
                 const J4<Real> b = sj[k];
                 const bool self = (k == dself);
                 const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
@@ -145,7 +159,8 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         }
         Pr::add(acc, part, Real(kScaleH));
     }
-    if (vi) {
+    acc = warp_total(acc);
+    if (vi && lane == 0) {
         const double sumH = Pr::value(acc, kScaleH);
         const double rt = V.rt[P + i], rho = V.rho[P + i];
         const double psi = 0.5 * rt * sumH;
@@ -173,8 +188,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
     __shared__ long long red[4];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x;
-    const int i = it.i0 + tid;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = it.i0 + (tid >> 5);
     const bool vi = i < N;
     const Real sqk = Real(V.sqrt_k);
     const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
@@ -225,8 +240,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         Real px = 0, py = 0, pz = 0, pdr = 0;
         KSum<Real> pgb, pc, plj;
         if (jt != next) {
-#pragma unroll 2
-            for (int k = 0; k < kTile; ++k) {
+#pragma unroll
+            for (int k = lane; k < kTile; k += 32) {
                 const J4<Real> a = sa[k];
                 const J4<Real> b = sb[k];
                 const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
@@ -268,7 +283,8 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {
                 const uint32_t me_ = mex[q4], ms_ = mself[q4];
-                for (int kk = 0; kk < 32; ++kk) {
+                {
+                    const int kk = lane;
                     const int k = q4 * 32 + kk;
                     const bool self = (ms_ >> kk) & 1u;
                     const bool ex = (me_ >> kk) & 1u;
@@ -321,7 +337,16 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
             Pr::add(elj, plj.value(), Real(kScaleE));
         }
     }
-    if (vi) {
+    fx = warp_total(fx);
+    fy = warp_total(fy);
+    fz = warp_total(fz);
+    adr = warp_total(adr);
+    if (ENERGY) {
+        egb = warp_total(egb);
+        ec = warp_total(ec);
+        elj = warp_total(elj);
+    }
+    if (vi && lane == 0) {
         const double q = V.q[A + i] * V.sqrt_k;
         const double R = V.R[A + i];
         const double dEdR = 0.5 * (V.tau_pair * Pr::value(adr, kScaleE)
@@ -334,7 +359,7 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
     }
     if (ENERGY) {
         long long e0 = 0, e1 = 0, e2 = 0;
-        if (vi) {
+        if (vi && lane == 0) {
             const double q = V.q[A + i] * V.sqrt_k;
             const double R = V.R[A + i];
             e0 = __double2ll_rn((-0.5 * (V.tau_pair * Pr::value(egb, kScaleE)
@@ -412,8 +437,8 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
     __shared__ long long red[4];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x;
-    const int i = it.i0 + tid;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = it.i0 + (tid >> 5);
     const bool vi = i < N;
     const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
                  cz = V.x[3 * (A + it.i0) + 2];
@@ -456,8 +481,8 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
         __syncthreads();
         Real px = 0, py = 0, pz = 0;
         if (jt != next) {
-#pragma unroll 4
-            for (int k = 0; k < kTile; ++k) {
+#pragma unroll
+            for (int k = lane; k < kTile; k += 32) {
                 const J4<Real> a = sa[k];
                 const J2<Real> b = sb[k];
                 const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
@@ -474,7 +499,8 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
             ++mp;
             next = mp < me ? V.mt_list[mp] : 0x7fffffff;
             const int dself = i - j0;
-            for (int k = 0; k < kTile; ++k) {
+#pragma unroll
+            for (int k = lane; k < kTile; k += 32) {
                 const J4<Real> a = sa[k];
                 const J2<Real> b = sb[k];
                 const bool self = (k == dself);
@@ -494,8 +520,11 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
         Pr::add(fy, py, Real(kScaleE));
         Pr::add(fz, pz, Real(kScaleE));
     }
+    fx = warp_total(fx);
+    fy = warp_total(fy);
+    fz = warp_total(fz);
     double eb = 0.0, ea = 0.0;
-    if (vi) {
+    if (vi && lane == 0) {
         double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE),
                        V.Fd[3 * (A + i) + 1] + Pr::value(fy, kScaleE),
                        V.Fd[3 * (A + i) + 2] + Pr::value(fz, kScaleE)};
