@@ -272,6 +272,24 @@ int cph_attempt_exchanges(cph_engine* e, int dim, void* stream);
  * Whole periods of the schedule replay a captured CUDA graph. */
 int cph_run(cph_engine* e, int64_t n_steps, void* stream);
 
+/* Tile shape of a system's pair passes in FP32 mode (FP64 mode always runs
+ * the ordered form):
+ *   CPH_SHAPE_SYMMETRIC (default): every unordered pair once, a CTA of 128
+ *     threads owning a 256-atom i-tile against chunks of 32-atom j-tiles, both
+ *     atoms' sums in int64 fixed point (best for large systems);
+ *   CPH_SHAPE_WARP_PER_ATOM: every ordered pair, one warp per atom i with its
+ *     lanes over j and a fixed-order warp reduction; twice the pair arithmetic
+ *     but 64 times more CTAs, for systems too small to fill the GPU with
+ *     256-atom tiles.
+ * Both forms meet the same accuracy bars; their results differ in the last
+ * bits (different summation order), so a run is bitwise reproducible only
+ * with the same shapes.  Batched and per-replica launches agree bitwise for
+ * any shapes.  CPH_E_INVALID for a bad system index or shape. */
+#define CPH_SHAPE_SYMMETRIC 0
+#define CPH_SHAPE_WARP_PER_ATOM 1
+int cph_set_tile_shape(cph_engine* e, int system, int shape);
+int cph_get_tile_shapes(const cph_engine* e, int* shapes /* host [n_sys] */);
+
 /* Diagnostic timing of the three pair passes at the current state, with CUDA
  * events recorded on `stream` around each launch (batched or per-replica, per
  * the launch mode): ms[0] Born radii, ms[1] GB + Coulomb + LJ, ms[2] chain
@@ -289,12 +307,18 @@ int cph_time_passes(cph_engine* e, int reps, double* ms /* host [3] */, void* st
  * roofline uses.  Allocates nothing; synchronises `stream`. */
 int cph_probe_pipe_rates(double* fp32_ops_per_s, double* mufu_ops_per_s, void* stream);
 
-/* Tile-shape autotuner: times the three pair passes at the current state for
- * each candidate work-item size (j-tiles of 32 atoms per CTA: 8..128) and
- * keeps the fastest; *chosen (may be NULL) receives it.  Derived per-atom
- * quantities are rewritten as by cph_time_passes; results of later steps are
- * bitwise the same whatever size is chosen (fixed-point sums).  FP64 mode has
- * nothing to tune (*chosen = 0).  Synchronises `stream`. */
+/* Tile-shape autotuner (FP32 mode): times the three pair passes at the
+ * current state for each candidate and keeps the fastest.  First the
+ * symmetric work-item size (j-tiles of 32 atoms per CTA: 8..128; results of
+ * later steps are bitwise the same whatever size is chosen, fixed-point
+ * sums); then the per-system tile shape: systems of at most n atoms run
+ * CPH_SHAPE_WARP_PER_ATOM, the others CPH_SHAPE_SYMMETRIC, for n over the
+ * distinct system sizes and 0 (every system symmetric).  *chosen (may be
+ * NULL) receives the work-item size; cph_get_tile_shapes reports the shapes.
+ * A change of shape changes later results in the last bits (see
+ * cph_set_tile_shape).  Derived per-atom quantities are rewritten as by
+ * cph_time_passes.  FP64 mode has nothing to tune (*chosen = 0).
+ * Synchronises `stream`. */
 int cph_autotune(cph_engine* e, void* stream, int* chosen);
 
 /* ---- getters and setters (host buffers; getters synchronise `stream`) */

@@ -22,6 +22,7 @@ MC_PH, MC_REDOX, MC_BOTH = 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_REPLICA = 0, 1
 TEX_POTENTIAL, TEX_SEMIGRAND = 0, 1
+SHAPE_SYMMETRIC, SHAPE_WARP_PER_ATOM = 0, 1
 NTERMS = 6
 MAX_STATES = 8
 FIT_PH, FIT_REDOX = 1, 2
@@ -150,6 +151,8 @@ def lib():
             "cph_status": ([vp, vp], i),
             "cph_time_passes": ([vp, i, vp, vp], i),
             "cph_autotune": ([vp, vp, C.POINTER(C.c_int)], i),
+            "cph_set_tile_shape": ([vp, i, i], i),
+            "cph_get_tile_shapes": ([vp, vp], i),
             "cph_probe_pipe_rates": ([C.POINTER(C.c_double), C.POINTER(C.c_double), vp], i),
             "cph_gb_workspace_bytes": ([i, i], C.c_size_t),
             "cph_gb_energy": ([i, i, vp, vp, vp, vp, C.POINTER(GBParams), vp, vp, C.c_size_t,
@@ -403,6 +406,14 @@ class Engine:
         c = C.c_int(0)
         self._c(lib().cph_autotune(self.ptr, _stream(stream), C.byref(c)))
         return c.value
+
+    def set_tile_shape(self, system, shape):
+        self._c(lib().cph_set_tile_shape(self.ptr, int(system), int(shape)))
+
+    def tile_shapes(self):
+        out = np.zeros(len(self.systems), np.int32)
+        self._c(lib().cph_get_tile_shapes(self.ptr, _p(out)))
+        return out
 
     def status(self, stream=None):
         self._c(lib().cph_status(self.ptr, _stream(stream)))

@@ -569,17 +569,21 @@ struct cph_engine {
     std::vector<int> h_sys_n, h_w_sys, h_w_off, h_w_site_off, h_sys_site_off;
     std::vector<int> h_site_nst, h_site_kind, h_site_noff, h_site_np, h_site_ne;
     int n_site_states = 0;
+    // ordered (one warp per atom) items: every walker in FP64 mode, the walkers
+    // of the systems whose tile shape is CPH_SHAPE_WARP_PER_ATOM in FP32 mode
     Item* d_items = nullptr;
     int n_items = 0;
     std::vector<int> item_w_off; // per-walker item ranges (items grouped by walker, per-replica mode)
     Item* d_items_by_w = nullptr;
+    std::vector<int> h_sys_shape;  // CPH_SHAPE_* per system (FP32 mode)
+    int* d_sys_ordered = nullptr;  // 1 where a system runs the ordered passes
     SymItem* d_sym = nullptr;          // symmetric FP32 items, largest system first
     SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
     int n_sym = 0;
     int sym_chunk = kSymChunk;         // j-tiles per symmetric work item (autotuned)
     int max_sites = 0;                 // largest site count of any system
     int max_terms = 0;                 // largest bonds + angles count of any system
-    std::vector<int> sym_w_off, h_sys_sst_off;
+    std::vector<int> sym_w_off, h_sys_sst_off, h_sys_st_off;
     int ex_cap = 0;
     int mc_kinds_last = 0;
     cudaStream_t cap_stream = nullptr;
@@ -594,6 +598,8 @@ struct cph_engine {
             if (g) cudaGraphExecDestroy(g);
         if (d_sym) cudaFree(d_sym);
         if (d_sym_by_w) cudaFree(d_sym_by_w);
+        if (d_items) cudaFree(d_items);
+        if (d_items_by_w) cudaFree(d_items_by_w);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (int k = 0; k < 32; ++k) {
             if (rs[k]) cudaStreamDestroy(rs[k]);
@@ -662,6 +668,12 @@ bool finite_all(const double* p, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
     return true;
+}
+
+// Whether walkers of system s run the ordered passes (one warp per atom i):
+// always in FP64 mode, by the system's tile shape in FP32 mode.
+bool sys_ordered(const cph_engine* E, int s) {
+    return E->precision == CPH_PREC_FP64 || E->h_sys_shape[s] == CPH_SHAPE_WARP_PER_ATOM;
 }
 
 // ---- launch helpers
@@ -828,17 +840,25 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
             return pass == 1 ? launch_gb(E, E->d_items, E->n_items, energy, st)
                              : launch_chain(E, E->d_items, E->n_items, energy, st);
         }
-        TRY(launch_stage(E, pass, 0, E->V.total_atoms, st));
-        TRY(launch_sym_pair(E, E->d_sym, E->n_sym, energy, pass, st));
-        if (pass == 2) TRY(launch_bonded(E, energy, 0, E->V.W, st));
-        return launch_atoms(E, fin, energy, 0, E->V.total_atoms, st);
+        if (E->n_sym > 0) {
+            TRY(launch_stage(E, pass, 0, E->V.total_atoms, st));
+            TRY(launch_sym_pair(E, E->d_sym, E->n_sym, energy, pass, st));
+            if (pass == 2) TRY(launch_bonded(E, energy, 0, E->V.W, st));
+            TRY(launch_atoms(E, fin, energy, 0, E->V.total_atoms, st));
+        }
+        if (E->n_items > 0) { // systems on the ordered passes (bonded terms in k_chain)
+            if (pass == 0) TRY(launch_born(E, E->d_items, E->n_items, energy, st));
+            else TRY(pass == 1 ? launch_gb(E, E->d_items, E->n_items, energy, st)
+                               : launch_chain(E, E->d_items, E->n_items, energy, st));
+        }
+        return CPH_OK;
     }
     TRY(fan_out(E, st));
     for (int w = 0; w < W; ++w) {
         const Item* it = E->d_items_by_w + E->item_w_off[w];
         const int ni = E->item_w_off[w + 1] - E->item_w_off[w];
         cudaStream_t s = lane_stream(E, w, st);
-        if (!fp32) {
+        if (!fp32 || sys_ordered(E, E->h_w_sys[w])) {
             if (pass == 0) TRY(launch_born(E, it, ni, energy, s));
             else TRY(pass == 1 ? launch_gb(E, it, ni, energy, s) : launch_chain(E, it, ni, energy, s));
         } else {
@@ -964,20 +984,43 @@ int get_graph(cph_engine* E, cudaGraphExec_t* out) {
 
 namespace {
 
-// Symmetric work items for j-tile chunks of `chunk` tiles: every walker's
-// 256-atom i-tiles against the 32-atom j-tiles from their first atom on.
-// Replaces the current item arrays and drops captured graphs (they hold the
-// old item pointers).
-int build_sym_items(cph_engine* E, int chunk) {
+// Work items of the pair passes.  Ordered items: groups of kWarpAtoms atoms i
+// (one warp each) of the walkers whose system runs the ordered passes.
+// Symmetric items (FP32), for the other walkers: j-tile chunks of `chunk`
+// tiles, every 256-atom i-tile against the 32-atom j-tiles from its first
+// atom on.  Replaces the current item arrays and the device copy of the
+// per-system shape flags, and drops captured graphs (they hold the old item
+// pointers).
+int build_items(cph_engine* E, int chunk) {
     // the pair passes sum i-side partials per aligned group of kSymG j-tiles:
     // items must start and end on group boundaries (or at the row's end)
     if (chunk < kSymG || chunk % kSymG != 0 || kSymI % (kSymG * kSymJ) != 0)
         return fail(E, CPH_E_INVALID, "work-item size %d is not a multiple of %d j-tiles", chunk, kSymG);
     const int W = E->V.W;
+    std::vector<Item> oitems, o_by_w;
+    std::vector<int> o_off(W + 1, 0);
+    std::vector<int> ordered(E->n_sys);
+    for (int s = 0; s < E->n_sys; ++s) ordered[s] = sys_ordered(E, s) ? 1 : 0;
+    for (int w = 0; w < W; ++w) {
+        const int s = E->h_w_sys[w], N = E->h_sys_n[s];
+        // the masked j-tiles of a group are those of the 128-atom i-tile it lies in
+        if (ordered[s])
+            for (int i0 = 0; i0 < N; i0 += kWarpAtoms)
+                o_by_w.push_back(Item{w, i0, E->h_sys_st_off[s] + i0 / kTile, 0});
+        o_off[w + 1] = (int)o_by_w.size();
+    }
+    oitems = o_by_w;
+    std::stable_sort(oitems.begin(), oitems.end(), [&](const Item& a, const Item& b) {
+        return E->h_sys_n[E->h_w_sys[a.w]] > E->h_sys_n[E->h_w_sys[b.w]];
+    });
     std::vector<SymItem> sym, by_w;
     std::vector<int> w_off(W + 1, 0);
     for (int w = 0; w < W; ++w) {
         const int s = E->h_w_sys[w], N = E->h_sys_n[s];
+        if (ordered[s]) {
+            w_off[w + 1] = (int)by_w.size();
+            continue;
+        }
         const int njt = (N + kSymJ - 1) / kSymJ;
         for (int it = 0; it * kSymI < N; ++it) {
             const int i0 = it * kSymI;
@@ -1005,6 +1048,16 @@ int build_sym_items(cph_engine* E, int chunk) {
     E->n_sym = (int)sym.size();
     E->sym_w_off = w_off;
     E->sym_chunk = chunk;
+    if (E->d_items) cudaFree(E->d_items);
+    if (E->d_items_by_w) cudaFree(E->d_items_by_w);
+    E->d_items = E->d_items_by_w = nullptr;
+    CK(cudaMalloc(&E->d_items, sizeof(Item) * std::max<size_t>(1, oitems.size())));
+    CK(cudaMalloc(&E->d_items_by_w, sizeof(Item) * std::max<size_t>(1, o_by_w.size())));
+    CK(cudaMemcpy(E->d_items, oitems.data(), sizeof(Item) * oitems.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E->d_items_by_w, o_by_w.data(), sizeof(Item) * o_by_w.size(), cudaMemcpyHostToDevice));
+    E->n_items = (int)oitems.size();
+    E->item_w_off = o_off;
+    CK(cudaMemcpy(E->d_sys_ordered, ordered.data(), sizeof(int) * ordered.size(), cudaMemcpyHostToDevice));
     return CPH_OK;
 }
 
@@ -1275,22 +1328,6 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
             for (int m = 0; m < sd.n_atoms; ++m) hq[w_off[w] + sd.atoms[m]] = sd.q[sd.init_state * sd.n_atoms + m];
         }
     }
-    // work items, largest systems first
-    std::vector<Item> items, items_by_w;
-    std::vector<int> item_w_off(W + 1, 0);
-    for (int w = 0; w < W; ++w) {
-        const int s = w_sys[w], N = sys_n[s];
-        // ordered passes: kWarpAtoms atoms i per CTA (one warp each); the masked
-        // j-tiles are those of the 128-atom i-tile the group lies in
-        for (int i0 = 0; i0 < N; i0 += kWarpAtoms)
-            items_by_w.push_back(Item{w, i0, sys_st_off[s] + i0 / kTile, 0});
-        item_w_off[w + 1] = (int)items_by_w.size();
-    }
-    items = items_by_w;
-    std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
-        return sys_n[w_sys[a.w]] > sys_n[w_sys[b.w]];
-    });
-
     cph_engine* E = new cph_engine();
     std::unique_ptr<cph_engine> guard(E);
     E->precision = p->precision;
@@ -1309,9 +1346,9 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     E->h_site_np = site_np;
     E->h_site_ne = site_ne;
     E->n_site_states = (int)site_np.size();
-    E->item_w_off = item_w_off;
-    E->n_items = (int)items.size();
     E->h_sys_sst_off = sys_sst_off;
+    E->h_sys_st_off = sys_st_off;
+    E->h_sys_shape.assign(n_sys, CPH_SHAPE_SYMMETRIC);
     E->graph_period = schedule_period(E);
     View& V = E->V;
     V.W = W;
@@ -1527,10 +1564,13 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     }
     V.seed = seed;
     V.tex_semigrand = p->t_exchange_energy == CPH_TEX_SEMIGRAND ? 1 : 0;
-    Item* di;
-    TRY(upload(E, items, &di)); E->d_items = di;
-    TRY(upload(E, items_by_w, &di)); E->d_items_by_w = di;
-    TRY(build_sym_items(E, kSymChunk));
+    {
+        int* dso;
+        TRY(alloc0(E, (size_t)n_sys, &dso));
+        E->d_sys_ordered = dso;
+        V.sys_ordered = dso;
+    }
+    TRY(build_items(E, kSymChunk));
 
     // reference energies of every (site, state)
     if (!site_np.empty()) {
@@ -1635,23 +1675,67 @@ int cph_autotune(cph_engine* e, void* stream, int* chosen) {
         return CPH_OK; // the FP64 passes have no tunable shape
     }
     cph_engine* E = e;
+    auto timed = [&](double* t) -> int {
+        double ms[3];
+        TRY(cph_time_passes(e, 1, ms, stream)); // warm-up
+        TRY(cph_time_passes(e, 2, ms, stream));
+        *t = ms[0] + ms[1] + ms[2];
+        return CPH_OK;
+    };
+    // 1. work-item size of the symmetric tiles, every system symmetric
+    const std::vector<int> shapes0 = e->h_sys_shape;
+    e->h_sys_shape.assign(e->n_sys, CPH_SHAPE_SYMMETRIC);
     const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128};
     double best = 1e300;
     int best_c = e->sym_chunk;
     for (int c : cand) {
-        TRY(build_sym_items(e, c));
-        double ms[3];
-        TRY(cph_time_passes(e, 1, ms, stream)); // warm-up
-        TRY(cph_time_passes(e, 2, ms, stream));
-        const double t = ms[0] + ms[1] + ms[2];
+        TRY(build_items(e, c));
+        double t;
+        TRY(timed(&t));
         if (t < best) {
             best = t;
             best_c = c;
         }
     }
-    TRY(build_sym_items(e, best_c));
+    // 2. systems of at most n atoms on one warp per atom, n over the sizes
+    std::vector<int> sizes(e->h_sys_n.begin(), e->h_sys_n.end());
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    int best_n = 0;
+    for (int n : sizes) {
+        for (int s = 0; s < e->n_sys; ++s)
+            e->h_sys_shape[s] = e->h_sys_n[s] <= n ? CPH_SHAPE_WARP_PER_ATOM : CPH_SHAPE_SYMMETRIC;
+        TRY(build_items(e, best_c));
+        double t;
+        TRY(timed(&t));
+        if (t < best) {
+            best = t;
+            best_n = n;
+        }
+    }
+    for (int s = 0; s < e->n_sys; ++s)
+        e->h_sys_shape[s] = e->h_sys_n[s] <= best_n ? CPH_SHAPE_WARP_PER_ATOM : CPH_SHAPE_SYMMETRIC;
+    (void)shapes0;
+    TRY(build_items(e, best_c));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     if (chosen) *chosen = best_c;
+    return CPH_OK;
+}
+
+int cph_set_tile_shape(cph_engine* e, int system, int shape) {
+    if (!e) return fail(nullptr, CPH_E_INVALID, "NULL engine");
+    if (system < 0 || system >= e->n_sys) return fail(e, CPH_E_INVALID, "system %d out of range", system);
+    if (shape != CPH_SHAPE_SYMMETRIC && shape != CPH_SHAPE_WARP_PER_ATOM)
+        return fail(e, CPH_E_INVALID, "unknown tile shape %d", shape);
+    if (e->h_sys_shape[system] == shape) return CPH_OK;
+    e->h_sys_shape[system] = shape;
+    return build_items(e, e->sym_chunk);
+}
+
+int cph_get_tile_shapes(const cph_engine* e, int* shapes) {
+    if (!e || !shapes) return fail(nullptr, CPH_E_INVALID, "bad arguments");
+    for (int s = 0; s < e->n_sys; ++s)
+        shapes[s] = e->precision == CPH_PREC_FP64 ? CPH_SHAPE_WARP_PER_ATOM : e->h_sys_shape[s];
     return CPH_OK;
 }
 

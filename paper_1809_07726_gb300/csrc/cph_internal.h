@@ -109,6 +109,7 @@ struct View {
     const float2* plj32; // per system atom, static: (sigma/2, sqrt(eps))
     unsigned long long seed;
     int tex_semigrand; // T exchange on U - sum U_ref + sum_redox F N_e (E - E0_ref) instead of U
+    const int* sys_ordered; // per system: 1 = ordered passes (one warp per atom), 0 = symmetric tiles
 };
 
 } // namespace cph

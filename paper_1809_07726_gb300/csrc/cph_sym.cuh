@@ -447,6 +447,7 @@ __global__ void k_fin_c(View V, int a0, int n) {
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
+    if (V.sys_ordered[V.w_sys[w]]) return; // the ordered passes finish these atoms themselves
     const int P = V.sys_poff[V.w_sys[w]] + (a - V.w_off[w]);
     const double q = V.q[a] * V.sqrt_k, R = V.R[a];
     const double esa = sa_ace(V.sa_gamma, V.sa_probe, V.rho[P], R);
@@ -684,6 +685,7 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
     __shared__ double re[kBondedThreads / 32][2];
     const int w = w0 + blockIdx.y;
     const int s = V.w_sys[w], A = V.w_off[w];
+    if (V.sys_ordered[s]) return; // bonded terms of the ordered passes are in k_chain
     const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0;
     const int a0 = V.sys_ang_off[s], na = V.sys_ang_off[s + 1] - a0;
     const int t = blockIdx.x * kBondedThreads + threadIdx.x;
@@ -780,6 +782,7 @@ __global__ void k_final_forces(View V, int a0, int n) {
     const int a = a0 + l;
     const int w = V.a_walker[a];
     const int s = V.w_sys[w];
+    if (V.sys_ordered[s]) return;
     const int A = V.w_off[w], li = a - A, P = V.sys_poff[s];
     double F[3] = {(double)V.Ffix[3 * a] / kScaleE, (double)V.Ffix[3 * a + 1] / kScaleE,
                    (double)V.Ffix[3 * a + 2] / kScaleE};
@@ -1051,6 +1054,7 @@ __global__ void k_fin_born(View V, int a0, int n, int zero_energy) {
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
+    if (V.sys_ordered[V.w_sys[w]]) return;
     const int li = a - V.w_off[w];
     const int P = V.sys_poff[V.w_sys[w]] + li;
     const double rt = V.rt[P], rho = V.rho[P];

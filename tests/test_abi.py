@@ -140,3 +140,9 @@ def test_gb_energy_rejects_bad_arguments(L):
                          C.byref(g), C.c_void_p(16), C.c_void_p(8), 1 << 20, None)
     assert rc == cphremd.E_INVALID
     assert "aligned" in L.cph_last_error(None).decode()
+
+
+def test_tile_shape_calls_refuse_a_missing_engine(L):
+    assert L.cph_set_tile_shape(None, 0, cphremd.SHAPE_SYMMETRIC) == cphremd.E_INVALID
+    shapes = np.zeros(1, np.int32)
+    assert L.cph_get_tile_shapes(None, shapes.ctypes.data) == cphremd.E_INVALID

@@ -68,18 +68,26 @@ def ragged_systems():
             synth.make_system(40, 23, n_ph=1, redox_atoms=8)]
 
 
-@pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
-                                           (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11)])
-def test_evaluate_matches_oracle_ragged_batch(ragged_systems, prec, tf, te, tr):
+@pytest.mark.parametrize("prec,tf,te,tr,shapes", [
+    (cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, None),
+    (cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, (0, 1, 1)),  # mixed tile shapes in one launch
+    (cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, (1, 1, 1)),
+    (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11, None)])
+def test_evaluate_matches_oracle_ragged_batch(ragged_systems, prec, tf, te, tr, shapes):
     grid = _grid_for(ragged_systems)
     eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec)
+    for k, sh in enumerate(shapes or ()):
+        eng.set_tile_shape(k, sh)
+    if shapes:
+        np.testing.assert_array_equal(eng.tile_shapes(), shapes)
     eng.evaluate()
     for w in range(grid.n_slots):
         s = ragged_systems[grid.system_of_slot[w]]
         _compare_walker(eng, w, s, s.x, s.q, tf, te, tr)
 
 
-def test_batched_equals_per_replica_bitwise(ragged_systems):
+@pytest.mark.parametrize("shapes", [(0, 0, 0), (1, 0, 1)])
+def test_batched_equals_per_replica_bitwise(ragged_systems, shapes):
     grid = _grid_for(ragged_systems)
     a = cphremd.init_system(ragged_systems, grid, seed=3)
     b = cphremd.init_system(ragged_systems, grid, seed=3)
@@ -87,6 +95,9 @@ def test_batched_equals_per_replica_bitwise(ragged_systems):
     c = cphremd.init_system(ragged_systems, grid, seed=3)
     c.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
     c.set_replica_streams(4)  # walkers on four streams, forked and joined per sequence
+    for e in (a, b, c):
+        for k, sh in enumerate(shapes):
+            e.set_tile_shape(k, sh)
     a.run(25)
     b.run(25)
     c.run(25)
@@ -121,16 +132,20 @@ def test_graph_replay_equals_direct_steps(ragged_systems):
         np.testing.assert_array_equal(getattr(a, get)(), getattr(b, get)())
 
 
-def test_full_3d_grid_sampled_walkers():
+@pytest.mark.parametrize("shapes", [None, (1, 0, 0)])
+def test_full_3d_grid_sampled_walkers(shapes):
     """The 384-walker E x T x pH grid over 500/2000/8000-atom systems in one
-    batched launch: one walker of each system against the oracle."""
+    batched launch: one walker of each system against the oracle (all
+    systems on symmetric tiles, and the 500-atom one on one warp per atom)."""
     systems, grid = synth.config_c4()
     eng = cphremd.init_system(systems, grid, seed=4)
+    for k, sh in enumerate(shapes or ()):
+        eng.set_tile_shape(k, sh)
     eng.evaluate()
     for w in (0, 2 * 64 + 5, 5 * 64 + 63):
         s = systems[grid.system_of_slot[w]]
         _compare_walker(eng, w, s, s.x, s.q, FORCE_RMS, ENERGY_REL, R_REL,
-                        case="3D grid, 384 walkers (FP32)")
+                        case="3D grid, 384 walkers (FP32" + (", shapes %s)" % (shapes,) if shapes else ")"))
 
 
 def test_reference_energies_match_oracle(ragged_systems):
@@ -335,18 +350,38 @@ def test_nonfinite_state_is_reported_not_hidden():
     assert ei.value.code == cphremd.E_NONFINITE
 
 
-def test_autotuned_tile_shape_changes_nothing_but_speed(ragged_systems):
-    """The autotuner only changes the work-item size; fixed-point sums make the
-    trajectory bitwise identical to the default shape."""
+def test_autotuned_work_item_size_changes_nothing_but_speed(ragged_systems):
+    """The symmetric tiles' work-item size only changes speed: fixed-point sums
+    make the trajectory bitwise identical to the default size (the shapes held
+    at symmetric after tuning)."""
     grid = _grid_for(ragged_systems)
     a = cphremd.init_system(ragged_systems, grid, seed=21)
     b = cphremd.init_system(ragged_systems, grid, seed=21)
     chunk = a.autotune()
     assert chunk in (8, 16, 24, 32, 48, 64, 96, 128)
+    for k in range(len(ragged_systems)):
+        a.set_tile_shape(k, cphremd.SHAPE_SYMMETRIC)
     a.run(20)
     b.run(20)
     np.testing.assert_array_equal(a.positions(), b.positions())
     np.testing.assert_array_equal(a.forces(), b.forces())
+
+
+def test_autotuned_tile_shapes_meet_the_bars(ragged_systems):
+    """Whatever per-system shapes the autotuner picks (smallest systems on one
+    warp per atom up to a tuned size), the results meet the FP32 bars; the
+    shapes it reports follow its size rule."""
+    grid = _grid_for(ragged_systems)
+    eng = cphremd.init_system(ragged_systems, grid, seed=3)
+    eng.autotune()
+    sh = eng.tile_shapes()
+    sizes = np.array([s.n for s in ragged_systems])
+    if sh.any():
+        assert sizes[sh == 1].max() < sizes[sh == 0].min() if (sh == 0).any() else True
+    eng.evaluate()
+    for w in range(grid.n_slots):
+        s = ragged_systems[grid.system_of_slot[w]]
+        _compare_walker(eng, w, s, s.x, s.q, FORCE_RMS, ENERGY_REL, R_REL)
 
 
 def test_checkpoint_restart_continues_bitwise(ragged_systems):
