@@ -18,9 +18,12 @@ on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank runs its own independent 384-replica
-ensemble (own seed) on its own GPU: no data-path collective; the value is the
-sum over ranks of replica-steps divided by the max-over-ranks time.
+Under torchrun (N > 1) the ranks share the one 384-replica grid: each
+advances a load-balanced part of its walkers on its own GPU, and at every
+exchange step the 40-byte per-walker exchange rows are all-gathered over NCCL
+and every rank runs the same exchange attempt (paper_1809_07726_gb300/shard.py).
+The value is the grid's replica-steps over the max-over-ranks time (strong
+scaling: the total work is fixed).
 """
 from __future__ import annotations
 
@@ -191,9 +194,10 @@ def aggregate_max(t_local, world, device=None):
     return float(tt.item())
 
 
-def whole_job_value(world, walkers, steps, t_max):
-    """Replica-steps of all ranks over the slowest rank's time."""
-    return world * walkers * steps / t_max
+def whole_job_value(grid_walkers, steps, t_max):
+    """Replica-steps of the whole grid (every rank's share of it) over the
+    slowest rank's time."""
+    return grid_walkers * steps / t_max
 
 
 def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
@@ -380,6 +384,7 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     eng = cphremd.init_system(systems, grid, seed=7, precision=precision)
+    eng.autotune()
     eng.run(n_steps)
     x = eng.positions()
     e = eng.energies()
@@ -408,7 +413,8 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
            "pair_evals_per_s": pairs_step * n_steps / (ms / 1e3),
            "e2e": {"value": W * n_steps / e2e_s, "unit": "replica-steps/s", "seconds": e2e_s,
                    "h2d_bytes": h2d, "d2h_bytes": d2h,
-                   "includes": "init_system from host buffers, run, read back positions and energies"}}
+                   "includes": "init_system from host buffers, autotune, run, read back positions "
+                               "and energies"}}
     if precision == cphremd.PREC_FP32:
         far = gb_far_fraction(eng2, systems, grid)
         step_peak = N_SM * (sm_mhz or 2070.0) * 1e6 / sum(pass_clk(n, far) for n in ("born", "gb", "chain"))
@@ -438,7 +444,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1809_07726_gb300 import build, cphremd, synth
+    from paper_1809_07726_gb300 import build, cphremd, shard, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -452,8 +458,22 @@ def run_gpu(args):
     systems, grid = workload()
     total_pairs = pair_count(systems, grid)
     W = grid.n_slots
-    seed = 4 + 1000 * rank
-    eng = cphremd.init_system(systems, grid, seed=seed)
+    seed = 4
+    sharded = world > 1
+    parts = shard.partition([s.n for s in systems], grid.system_of_slot, world)
+    mine = parts[rank]
+    local_pairs = sum(systems[grid.system_of_slot[w]].n * (systems[grid.system_of_slot[w]].n - 1) // 2
+                      for w in mine)
+
+    def make_engine():
+        e = cphremd.init_system(systems, grid, seed=seed)
+        if not sharded:
+            return e, e.run
+        e.set_local_walkers(mine)
+        drv = shard.ShardedRun(e, shard.torch_allgather(), 10, 10, 100)
+        return e, drv.run
+
+    eng, advance = make_engine()
     # L2 flush buffer (256 MB > 129 MB L2), written before every timed step
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -465,10 +485,10 @@ def run_gpu(args):
     chunk = eng.autotune()  # tile shape for this workload (outside the timed region)
     first = window_start(args.steps, args.warmup)
     events = schedule_events(first, args.steps)
-    eng.run(1)  # step 0
-    eng.run(first - args.warmup - 1)  # to the warm-up steps (window_start leaves room)
+    advance(1)  # step 0
+    advance(first - args.warmup - 1)  # to the warm-up steps (window_start leaves room)
     ck = eng.get_state()  # the per-replica runs restart from here: same steps, same work
-    eng.run(args.warmup)
+    advance(args.warmup)
     barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -481,7 +501,7 @@ def run_gpu(args):
         for k in range(args.steps):
             flush.fill_(float(k))
             starts[k].record(stream)
-            eng.run(1)
+            advance(1)
             ends[k].record(stream)
             launches += schedule_launches(t_first + k)
         barrier()
@@ -490,21 +510,24 @@ def run_gpu(args):
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_local = sum(ms) / 1e3
     t_max = aggregate_max(t_local, world, dev)
-    value = whole_job_value(world, W, args.steps, t_max)
+    value = whole_job_value(W, args.steps, t_max)
     clocks = clk.summary()
     ms_step = 1e3 * t_max / args.steps
 
-    # graph replay of whole schedule periods (no flush between steps)
+    # graph replay of whole schedule periods (no flush between steps); a
+    # sharded engine leaves its exchange steps to the host driver
     period = 100
-    while eng.get_step() % period != 1:
-        eng.run(1)
-    barrier()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    eng.run(period)
-    g1.record(stream)
-    barrier()
-    graph_ms = g0.elapsed_time(g1) / period
+    graph_ms = None
+    if not sharded:
+        while eng.get_step() % period != 1:
+            eng.run(1)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        eng.run(period)
+        g1.record(stream)
+        barrier()
+        graph_ms = g0.elapsed_time(g1) / period
 
     # dominant pair pass: CUDA events around each pass on the launching stream
     pass_ms = eng.time_passes(reps=3)
@@ -515,7 +538,7 @@ def run_gpu(args):
     f_mhz = clocks["sm_mhz"] or 2070.0
     gb_far = gb_far_fraction(eng, systems, grid)
     peak = N_SM * f_mhz * 1e6 / pass_clk(names[dom], gb_far) / 1e9
-    achieved = total_pairs / (pass_ms[dom] / 1e3) / 1e9
+    achieved = local_pairs / (pass_ms[dom] / 1e3) / 1e9
     step_peak = N_SM * f_mhz * 1e6 / sum(pass_clk(n, gb_far) for n in names) / 1e9
 
     if args.quick:
@@ -525,39 +548,43 @@ def run_gpu(args):
                               "clocks": clocks}), flush=True)
         return
     # the same steps as per-replica launches: restart from the checkpoint, same window
-    eng.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
-    eng.autotune()
-    eng.set_state(ck)
-    barrier()
-    pr_ms = sum(timed_window(eng, stream, flush, first, args.steps, args.warmup)) / args.steps
-    pr_pass_ms = eng.time_passes(reps=1)
-    # and spread over 8 streams (as 8 processes per GPU would overlap)
-    eng.set_replica_streams(8)
-    eng.set_state(ck)
-    barrier()
-    pr8_ms = sum(timed_window(eng, stream, flush, first, args.steps, args.warmup)) / args.steps
+    pr_ms = pr8_ms = None
+    pr_pass_ms = []
+    if not sharded:
+        eng.set_launch_mode(cphremd.LAUNCH_PER_REPLICA)
+        eng.autotune()
+        eng.set_state(ck)
+        barrier()
+        pr_ms = sum(timed_window(eng, stream, flush, first, args.steps, args.warmup)) / args.steps
+        pr_pass_ms = eng.time_passes(reps=1)
+        # and spread over 8 streams (as 8 processes per GPU would overlap)
+        eng.set_replica_streams(8)
+        eng.set_state(ck)
+        barrier()
+        pr8_ms = sum(timed_window(eng, stream, flush, first, args.steps, args.warmup)) / args.steps
     del eng
 
     # end to end through the public API from host buffers: init (H2D of the
     # systems) + per-step run and D2H of energies and the condition map
     barrier()
     e2e0 = time.perf_counter()
-    e2 = cphremd.init_system(systems, grid, seed=seed)
+    e2, adv2 = make_engine()
     h2d = sum(s.n * (3 * 8 + 7 * 8) for s in systems) + sum(
         systems[s].n * 3 * 8 for s in grid.system_of_slot)
     n_e2e = args.steps
     d2h = 0
     for _ in range(n_e2e):
-        e2.run(1)
+        adv2(1)
         e2.energies()
         e2.condition_map()
         d2h += W * 6 * 8 + W * 4
     barrier()
-    e2e_s = time.perf_counter() - e2e0
+    e2e_s = aggregate_max(time.perf_counter() - e2e0, world, dev)
     e2e_value = W * n_e2e / e2e_s
     del e2
 
-    backward = backward_leg(dev, stream, barrier, clocks["sm_mhz"])
+    backward = backward_leg(dev, stream, barrier if not sharded else torch.cuda.synchronize,
+                            clocks["sm_mhz"]) if rank == 0 else None
 
     # the smaller workloads, each through the C ABI from host buffers
     ncores = host_cores()
@@ -599,23 +626,26 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "replica-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "replicas": W, "atoms": [s.n for s in systems],
                    "precision": "FP32 pair math, int64 fixed-point accumulation",
                    "schedule": "MC (pH then redox) every 10 steps, exchange every 100 (E,pH,T)",
                    "l2": "256 MB buffer written before every timed step",
                    "autotuned_chunk_jtiles": chunk,
-                   "parallelism": f"replicas batched per launch; {world} independent ensemble(s)"},
+                   "parallelism": ("replicas batched per launch" if not sharded else
+                                   f"one grid sharded by walker over {world} GPUs (rank 0: {len(mine)} "
+                                   "walkers); exchange rows all-gathered over NCCL at exchange steps")},
         "window": events,
-        "pair_evals_per_s": world * total_pairs * args.steps / t_max,
-        "per_replica": {"value": W / (pr_ms / 1e3), "unit": "replica-steps/s", "ms_per_step": pr_ms,
-                        "same_window": True, "pass_ms": [float(x) for x in pr_pass_ms],
-                        "speedup_batched": pr_ms / ms_step,
-                        "streams_8": {"value": W / (pr8_ms / 1e3), "ms_per_step": pr8_ms,
-                                      "speedup_batched": pr8_ms / ms_step}},
-        "graph_replay": {"value": W / (graph_ms / 1e3), "unit": "replica-steps/s",
-                         "ms_per_step": graph_ms, "steps": period},
+        "pair_evals_per_s": total_pairs * args.steps / t_max,
+        "per_replica": None if sharded else {
+            "value": W / (pr_ms / 1e3), "unit": "replica-steps/s", "ms_per_step": pr_ms,
+            "same_window": True, "pass_ms": [float(x) for x in pr_pass_ms],
+            "speedup_batched": pr_ms / ms_step,
+            "streams_8": {"value": W / (pr8_ms / 1e3), "ms_per_step": pr8_ms,
+                          "speedup_batched": pr8_ms / ms_step}},
+        "graph_replay": None if sharded else {"value": W / (graph_ms / 1e3), "unit": "replica-steps/s",
+                                              "ms_per_step": graph_ms, "steps": period},
         "pass_ms": {n: float(x) for n, x in zip(names, pass_ms)},
         "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
                      "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": PASS_DRAM_BYTES.get(names[dom]),

@@ -290,6 +290,48 @@ int cph_run(cph_engine* e, int64_t n_steps, void* stream);
 int cph_set_tile_shape(cph_engine* e, int system, int shape);
 int cph_get_tile_shapes(const cph_engine* e, int* shapes /* host [n_sys] */);
 
+/* ---- one replica grid sharded over several engines (one per GPU)
+ *
+ * Walkers are independent between exchanges ("AMBER's multidimensional REMD
+ * module" exchanges only conditions between replicas), so a grid can be split
+ * by walker over several engines, each built from the same systems, grid,
+ * parameters and seed on its own GPU: cph_set_local_walkers gives each the
+ * walkers it advances (the others are kept but not computed).  Every random
+ * number is keyed by the global walker, site and slot, so the sharded run is
+ * bitwise the single-engine run.  At an exchange step t (t > 0, t a multiple
+ * of exchange_every) the host of each engine:
+ *   1. cph_mc_titrate for the MC kinds due at t (Born radii at x_t, sweeps);
+ *   2. cph_exchange_rows: energies at x_t, then one row per local walker;
+ *   3. gathers the rows of all engines (any transport, e.g. an all-gather);
+ *   4. cph_exchange_apply with every walker's row: the same attempt, on the
+ *      same rows and random numbers, on every engine; it updates the condition
+ *      map and scales the local walkers' velocities after a T swap;
+ *   5. cph_step_replicas(e, 1): the MD step t.
+ * Other steps run through cph_run, which refuses (CPH_E_STATE, nothing
+ * launched) a span that holds an exchange step on a sharded engine; so does
+ * cph_attempt_exchanges.  Observables count local walkers only (sum the
+ * counts over the engines); getters of per-walker state are meaningful for
+ * local walkers only. */
+typedef struct cph_exchange_row {
+    int walker;           /* global walker index */
+    int n_prot, n_elec;   /* N_H and N_e of its current site states */
+    int pad_;
+    long long u_fix;      /* total potential energy at x_t, fixed point (2^-32 kcal/mol units) */
+    double uref_sum;      /* sum over its sites of U_ref(state), kcal/mol */
+    double e0ref_ne_sum;  /* sum over its redox sites of N_e(state) E0_ref, V */
+} cph_exchange_row;
+/* walkers: host [n] distinct global walker indices (n = W: all, the default).
+ * Drops captured graphs; the engine's state is otherwise unchanged. */
+int cph_set_local_walkers(cph_engine* e, int n, const int* walkers);
+/* Energies at the current state of the local walkers, then their rows into
+ * rows (host, max entries); *n_out = the number of local walkers.
+ * Synchronises `stream`.  CPH_E_INVALID if max is too small. */
+int cph_exchange_rows(cph_engine* e, cph_exchange_row* rows, int max, int* n_out, void* stream);
+/* One exchange attempt along `dim` (as cph_attempt_exchanges) on the rows of
+ * all W walkers (host, any order, each walker exactly once; CPH_E_INVALID
+ * otherwise, nothing launched). */
+int cph_exchange_apply(cph_engine* e, int dim, const cph_exchange_row* rows, int n_rows, void* stream);
+
 /* Diagnostic timing of the three pair passes at the current state, with CUDA
  * events recorded on `stream` around each launch (batched or per-replica, per
  * the launch mode): ms[0] Born radii, ms[1] GB + Coulomb + LJ, ms[2] chain

@@ -78,6 +78,16 @@ class MCRecord(C.Structure):
                 ("x", C.c_double), ("lnu", C.c_double)]
 
 
+class ExchangeRow(C.Structure):
+    _fields_ = [("walker", C.c_int), ("n_prot", C.c_int), ("n_elec", C.c_int), ("pad_", C.c_int),
+                ("u_fix", C.c_int64), ("uref_sum", C.c_double), ("e0ref_ne_sum", C.c_double)]
+
+
+ROW_DTYPE = np.dtype([("walker", np.int32), ("n_prot", np.int32), ("n_elec", np.int32),
+                      ("pad_", np.int32), ("u_fix", np.int64), ("uref_sum", np.float64),
+                      ("e0ref_ne_sum", np.float64)])
+
+
 class ExRecord(C.Structure):
     _fields_ = [("dim", C.c_int), ("slot_lo", C.c_int), ("slot_hi", C.c_int),
                 ("walker_lo", C.c_int), ("walker_hi", C.c_int), ("accepted", C.c_int),
@@ -152,6 +162,9 @@ def lib():
             "cph_time_passes": ([vp, i, vp, vp], i),
             "cph_autotune": ([vp, vp, C.POINTER(C.c_int)], i),
             "cph_set_tile_shape": ([vp, i, i], i),
+            "cph_set_local_walkers": ([vp, i, vp], i),
+            "cph_exchange_rows": ([vp, vp, i, C.POINTER(C.c_int), vp], i),
+            "cph_exchange_apply": ([vp, i, vp, i, vp], i),
             "cph_get_tile_shapes": ([vp, vp], i),
             "cph_probe_pipe_rates": ([C.POINTER(C.c_double), C.POINTER(C.c_double), vp], i),
             "cph_gb_workspace_bytes": ([i, i], C.c_size_t),
@@ -406,6 +419,23 @@ class Engine:
         c = C.c_int(0)
         self._c(lib().cph_autotune(self.ptr, _stream(stream), C.byref(c)))
         return c.value
+
+    # ---- one grid sharded over several engines
+    def set_local_walkers(self, walkers):
+        w = _i32(walkers).reshape(-1)
+        self._c(lib().cph_set_local_walkers(self.ptr, w.size, _p(w)))
+
+    def exchange_rows(self, stream=None):
+        """Energies at the current state, then one row per local walker
+        (a structured array of ROW_DTYPE)."""
+        out = np.zeros(self.W, ROW_DTYPE)
+        n = C.c_int(0)
+        self._c(lib().cph_exchange_rows(self.ptr, _p(out), self.W, C.byref(n), _stream(stream)))
+        return out[:n.value].copy()
+
+    def exchange_apply(self, dim, rows, stream=None):
+        r = np.ascontiguousarray(rows, ROW_DTYPE)
+        self._c(lib().cph_exchange_apply(self.ptr, int(dim), _p(r), r.size, _stream(stream)))
 
     def set_tile_shape(self, system, shape):
         self._c(lib().cph_set_tile_shape(self.ptr, int(system), int(shape)))

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_site(View V, int kind, int s_
     using Pr = Prec<Real>;
     using Acc = typename Pr::Acc;
     const int w = w_begin + blockIdx.y, k = blockIdx.x;
+    if (!V.w_local[w]) return;
     const int s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int g0 = V.sys_site_off[s], ns = V.sys_site_off[s + 1] - g0, so = V.w_site_off[w];
     if (k >= ns || V.site_kind[g0 + k] != kind) return;
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_sweep(View V, int kind, int c
     using Pr = Prec<Real>;
     using Acc = typename Pr::Acc;
     const int w = w_begin + blockIdx.x;
+    if (!V.w_local[w]) return;
     const int s = V.w_sys[w], A = V.w_off[w], P = V.sys_poff[s];
     const int g0 = V.sys_site_off[s], ns = V.sys_site_off[s + 1] - g0, so = V.w_site_off[w];
     const int tid = threadIdx.x;
@@ -314,10 +316,11 @@ constexpr int kObsThreads = 64;
 // one CTA per walker, threads over its sites
 __global__ void __launch_bounds__(kObsThreads) k_observe(View V) {
     const int w = blockIdx.x;
+    if (!V.w_local[w]) return; // a sharded grid's counts are summed over its engines
     const int s = V.slot_of[w];
     if (threadIdx.x == 0) {
         V.visits[(long long)w * V.W + s] += 1;
-        if (w == 0) *V.n_obs += 1;
+        if (w == V.first_local) *V.n_obs += 1;
     }
     // the walker at slot s belongs to the system of the walker that started
     // there, so slot s's rows are laid out like walker s's sites
@@ -346,23 +349,42 @@ __device__ inline int walker_nelec(const View& V, int w) {
     return n;
 }
 
-__device__ inline double walker_energy(const View& V, int w) {
-    long long e = 0;
-    for (int t = 0; t < kEAcc; ++t) e += V.eacc[w * kEAcc + t];
-    return (double)e / kScaleE;
-}
-
-// Semi-grand exchange energy of walker w at redox potential E (T exchange with
-// CPH_TEX_SEMIGRAND): U - sum_k U_ref,k(s_k) + sum_redox F N_e,k(s_k) (E - E0_ref,k).
-__device__ inline double walker_semigrand_energy(const View& V, int w, double E) {
-    double e = walker_energy(V, w);
+// Exchange inputs of every walker this engine advances: the total potential
+// energy in fixed point (the sum of the walker's energy accumulators, exact),
+// N_H and N_e of its site states, and the two sums the semi-grand T-exchange
+// energy needs: sum_k U_ref,k(s_k) and sum over redox sites of N_e,k(s_k) E0_ref,k.
+__global__ void k_exchange_rows(View V) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= V.W || !V.w_local[w]) return;
+    long long u = 0;
+    for (int t = 0; t < kEAcc; ++t) u += V.eacc[w * kEAcc + t];
     const int s = V.w_sys[w];
+    int np = 0, ne = 0;
+    double uref = 0.0, e0ne = 0.0;
     for (int g = V.sys_site_off[s], k = 0; g < V.sys_site_off[s + 1]; ++g, ++k) {
         const int b = V.site_state[V.w_site_off[w] + k], no = V.site_noff[g];
-        e -= V.site_uref[no + b];
-        if (V.site_kind[g] == CPH_SITE_REDOX) e += kFaraday * (double)V.site_ne[no + b] * (E - V.site_ref[g]);
+        np += V.site_np[no + b];
+        ne += V.site_ne[no + b];
+        uref += V.site_uref[no + b];
+        if (V.site_kind[g] == CPH_SITE_REDOX) e0ne += (double)V.site_ne[no + b] * V.site_ref[g];
     }
-    return e;
+    cph_exchange_row r;
+    r.walker = w;
+    r.n_prot = np;
+    r.n_elec = ne;
+    r.pad_ = 0;
+    r.u_fix = u;
+    r.uref_sum = uref;
+    r.e0ref_ne_sum = e0ne;
+    V.ex_rows[w] = r;
+}
+
+// Energy eq (5) uses for the walker of row r at redox potential E: U, or the
+// semi-grand U - sum U_ref + F (N_e E - sum_redox N_e E0_ref) (CPH_TEX_SEMIGRAND).
+__device__ inline double row_energy(const View& V, const cph_exchange_row& r, double E) {
+    const double u = (double)r.u_fix / kScaleE;
+    if (!V.tex_semigrand) return u;
+    return u - r.uref_sum + kFaraday * ((double)r.n_elec * E - r.e0ref_ne_sum);
 }
 
 constexpr int kExThreads = 256;
@@ -421,24 +443,17 @@ __global__ void __launch_bounds__(kExThreads) k_exchange(View V, int dim_req, in
             continue;
         }
         const double T1 = V.gT[s1 / (V.nE * V.npH)], T2 = V.gT[s2 / (V.nE * V.npH)];
+        const cph_exchange_row r1 = V.ex_rows[w1], r2 = V.ex_rows[w2];
         double x;
         if (dim == CPH_DIM_PH) {
             const double p1 = V.gpH[(s1 / V.nE) % V.npH], p2 = V.gpH[(s2 / V.nE) % V.npH];
-            x = kLn10 * (p1 - p2) * (double)(walker_nprot(V, w1) - walker_nprot(V, w2));
+            x = kLn10 * (p1 - p2) * (double)(r1.n_prot - r2.n_prot);
         } else if (dim == CPH_DIM_E) {
             const double e1 = V.gE[s1 % V.nE], e2 = V.gE[s2 % V.nE];
-            x = kFaraday / (kBoltzmann * T1) * (e1 - e2) * (double)(walker_nelec(V, w1) - walker_nelec(V, w2));
-        } else {
-            double u1, u2;
-            if (V.tex_semigrand) { // a T line shares E: s1 and s2 have the same E index
-                const double e = V.gE[s1 % V.nE];
-                u1 = walker_semigrand_energy(V, w1, e);
-                u2 = walker_semigrand_energy(V, w2, e);
-            } else {
-                u1 = walker_energy(V, w1);
-                u2 = walker_energy(V, w2);
-            }
-            x = (1.0 / (kBoltzmann * T1) - 1.0 / (kBoltzmann * T2)) * (u1 - u2);
+            x = kFaraday / (kBoltzmann * T1) * (e1 - e2) * (double)(r1.n_elec - r2.n_elec);
+        } else { // a T line shares E: s1 and s2 have the same E index
+            const double e = V.gE[s1 % V.nE];
+            x = (1.0 / (kBoltzmann * T1) - 1.0 / (kBoltzmann * T2)) * (row_energy(V, r1, e) - row_energy(V, r2, e));
         }
         const U4 u = draw(V.seed, (uint32_t)s1, (uint32_t)dim, t, kRngExchange);
         const double lnu = log(unit_open(u.a));
@@ -577,6 +592,10 @@ struct cph_engine {
     Item* d_items_by_w = nullptr;
     std::vector<int> h_sys_shape;  // CPH_SHAPE_* per system (FP32 mode)
     int* d_sys_ordered = nullptr;  // 1 where a system runs the ordered passes
+    std::vector<int> h_w_local;    // 1 for the walkers this engine advances
+    int* d_w_local = nullptr;
+    bool sharded = false;          // some walker is not local
+    cph_exchange_row* d_rows = nullptr;
     SymItem* d_sym = nullptr;          // symmetric FP32 items, largest system first
     SymItem* d_sym_by_w = nullptr;     // grouped by walker (per-replica mode)
     int n_sym = 0;
@@ -757,6 +776,7 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
         } else {
             TRY(fan_out(E, st));
             for (int w = 0; w < W; ++w) {
+                if (!E->h_w_local[w]) continue;
                 cudaStream_t s = lane_stream(E, w, st);
                 if (f32) k_mc_site<float><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
                 else k_mc_site<double><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
@@ -855,6 +875,7 @@ int launch_pass(cph_engine* E, int pass, bool energy, cudaStream_t st) {
     }
     TRY(fan_out(E, st));
     for (int w = 0; w < W; ++w) {
+        if (!E->h_w_local[w]) continue;
         const Item* it = E->d_items_by_w + E->item_w_off[w];
         const int ni = E->item_w_off[w + 1] - E->item_w_off[w];
         cudaStream_t s = lane_stream(E, w, st);
@@ -898,6 +919,7 @@ int launch_langevin(cph_engine* E, int s_off, cudaStream_t st) {
     } else {
         TRY(fan_out(E, st));
         for (int w = 0; w < E->V.W; ++w) {
+            if (!E->h_w_local[w]) continue;
             cudaStream_t s = lane_stream(E, w, st);
             one(E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], s);
             if (E->n_shk) shk(E->h_shk_w_off[w], E->h_shk_w_off[w + 1] - E->h_shk_w_off[w], s);
@@ -908,10 +930,23 @@ int launch_langevin(cph_engine* E, int s_off, cudaStream_t st) {
     return CPH_OK;
 }
 
-int launch_exchange(cph_engine* E, int dim, int s_off, cudaStream_t st) {
+int launch_exchange_rows(cph_engine* E, cudaStream_t st) {
+    const int bs = 128;
+    k_exchange_rows<<<(E->V.W + bs - 1) / bs, bs, 0, st>>>(E->V);
+    CK(cudaGetLastError());
+    return CPH_OK;
+}
+
+// one exchange attempt from the rows in V.ex_rows (every walker's)
+int launch_exchange_only(cph_engine* E, int dim, int s_off, cudaStream_t st) {
     k_exchange<<<1, kExThreads, 0, st>>>(E->V, dim, s_off);
     CK(cudaGetLastError());
     return CPH_OK;
+}
+
+int launch_exchange(cph_engine* E, int dim, int s_off, cudaStream_t st) {
+    TRY(launch_exchange_rows(E, st));
+    return launch_exchange_only(E, dim, s_off, st);
 }
 
 int launch_observe(cph_engine* E, cudaStream_t st) {
@@ -1004,7 +1039,7 @@ int build_items(cph_engine* E, int chunk) {
     for (int w = 0; w < W; ++w) {
         const int s = E->h_w_sys[w], N = E->h_sys_n[s];
         // the masked j-tiles of a group are those of the 128-atom i-tile it lies in
-        if (ordered[s])
+        if (ordered[s] && E->h_w_local[w])
             for (int i0 = 0; i0 < N; i0 += kWarpAtoms)
                 o_by_w.push_back(Item{w, i0, E->h_sys_st_off[s] + i0 / kTile, 0});
         o_off[w + 1] = (int)o_by_w.size();
@@ -1017,7 +1052,7 @@ int build_items(cph_engine* E, int chunk) {
     std::vector<int> w_off(W + 1, 0);
     for (int w = 0; w < W; ++w) {
         const int s = E->h_w_sys[w], N = E->h_sys_n[s];
-        if (ordered[s]) {
+        if (ordered[s] || !E->h_w_local[w]) {
             w_off[w + 1] = (int)by_w.size();
             continue;
         }
@@ -1569,6 +1604,16 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
         TRY(alloc0(E, (size_t)n_sys, &dso));
         E->d_sys_ordered = dso;
         V.sys_ordered = dso;
+        E->h_w_local.assign(W, 1);
+        int* dwl;
+        TRY(upload(E, E->h_w_local, &dwl));
+        E->d_w_local = dwl;
+        V.w_local = dwl;
+        V.first_local = 0;
+        cph_exchange_row* drw;
+        TRY(alloc0(E, (size_t)W, &drw));
+        E->d_rows = drw;
+        V.ex_rows = drw;
     }
     TRY(build_items(E, kSymChunk));
 
@@ -1732,6 +1777,67 @@ int cph_set_tile_shape(cph_engine* e, int system, int shape) {
     return build_items(e, e->sym_chunk);
 }
 
+int cph_set_local_walkers(cph_engine* e, int n, const int* walkers) {
+    if (!e || n < 1 || n > e->V.W || !walkers) return fail(e, CPH_E_INVALID, "bad arguments");
+    cph_engine* E = e;
+    std::vector<int> m(e->V.W, 0);
+    for (int k = 0; k < n; ++k) {
+        if (walkers[k] < 0 || walkers[k] >= e->V.W || m[walkers[k]])
+            return fail(e, CPH_E_INVALID, "walker list: entry %d is out of range or repeated", k);
+        m[walkers[k]] = 1;
+    }
+    e->h_w_local = m;
+    e->sharded = n < e->V.W;
+    int first = 0;
+    while (!m[first]) ++first;
+    e->V.first_local = first;
+    CK(cudaMemcpy(e->d_w_local, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice));
+    return build_items(e, e->sym_chunk);
+}
+
+int cph_exchange_rows(cph_engine* e, cph_exchange_row* rows, int max, int* n_out, void* stream) {
+    if (!e || !rows || !n_out) return fail(e, CPH_E_INVALID, "bad arguments");
+    cph_engine* E = e;
+    int nl = 0;
+    for (int w = 0; w < e->V.W; ++w) nl += e->h_w_local[w];
+    if (max < nl) return fail(e, CPH_E_INVALID, "rows: room for %d, %d local walkers", max, nl);
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(launch_forces(e, true, st, false, 0, 0)); // energies at the current state
+    TRY(launch_exchange_rows(e, st));
+    std::vector<cph_exchange_row> all(e->V.W);
+    CK(cudaMemcpyAsync(all.data(), e->d_rows, sizeof(cph_exchange_row) * all.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int k = 0;
+    for (int w = 0; w < e->V.W; ++w)
+        if (e->h_w_local[w]) rows[k++] = all[w];
+    *n_out = nl;
+    return CPH_OK;
+}
+
+int cph_exchange_apply(cph_engine* e, int dim, const cph_exchange_row* rows, int n_rows, void* stream) {
+    if (!e || !rows || dim < -1 || dim > 2) return fail(e, CPH_E_INVALID, "bad arguments");
+    cph_engine* E = e;
+    const int W = e->V.W;
+    if (n_rows != W) return fail(e, CPH_E_INVALID, "exchange rows: %d given, %d walkers", n_rows, W);
+    std::vector<cph_exchange_row> all(W);
+    std::vector<char> seen(W, 0);
+    for (int k = 0; k < n_rows; ++k) {
+        const int w = rows[k].walker;
+        if (w < 0 || w >= W || seen[w]) return fail(e, CPH_E_INVALID, "exchange rows: walker %d missing or repeated", w);
+        seen[w] = 1;
+        all[w] = rows[k];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(e->d_rows, all.data(), sizeof(cph_exchange_row) * W, cudaMemcpyHostToDevice, st));
+    TRY(launch_exchange_only(e, dim, 0, st));
+    const int n = e->V.total_atoms, bs = 256;
+    k_vscale<<<(n + bs - 1) / bs, bs, 0, st>>>(e->V);
+    k_vscale_reset<<<(W + bs - 1) / bs, bs, 0, st>>>(e->V);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st)); // the host rows may be reused once this returns
+    return CPH_OK;
+}
+
 int cph_get_tile_shapes(const cph_engine* e, int* shapes) {
     if (!e || !shapes) return fail(nullptr, CPH_E_INVALID, "bad arguments");
     for (int s = 0; s < e->n_sys; ++s)
@@ -1758,6 +1864,8 @@ int cph_mc_titrate(cph_engine* e, int kind, void* stream) {
 
 int cph_attempt_exchanges(cph_engine* e, int dim, void* stream) {
     if (!e || dim < -1 || dim > 2) return fail(e, CPH_E_INVALID, "bad arguments");
+    if (e->sharded)
+        return fail(e, CPH_E_STATE, "sharded engine: exchanges go through cph_exchange_rows / cph_exchange_apply");
     cudaStream_t st = (cudaStream_t)stream;
     cph_engine* E = e;
     // energies at the current state (needed for T; cheap to keep uniform)
@@ -1772,6 +1880,14 @@ int cph_attempt_exchanges(cph_engine* e, int dim, void* stream) {
 
 int cph_run(cph_engine* e, int64_t n_steps, void* stream) {
     if (!e || n_steps < 0) return fail(e, CPH_E_INVALID, "bad arguments");
+    if (e->sharded && e->ex_every > 0) {
+        const long long t0 = e->h_step, t1 = e->h_step + n_steps; // steps t0 .. t1 - 1
+        long long first = (t0 <= 0 ? 1 : t0);
+        first = (first + e->ex_every - 1) / e->ex_every * e->ex_every;
+        if (first < t1)
+            return fail(e, CPH_E_STATE, "sharded engine: step %lld is an exchange step; run it with "
+                        "cph_exchange_rows / cph_exchange_apply / cph_step_replicas", first);
+    }
     cudaStream_t st = (cudaStream_t)stream;
     cph_engine* E = e;
     const int P = e->graph_period;

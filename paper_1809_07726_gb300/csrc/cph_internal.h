@@ -110,6 +110,11 @@ struct View {
     unsigned long long seed;
     int tex_semigrand; // T exchange on U - sum U_ref + sum_redox F N_e (E - E0_ref) instead of U
     const int* sys_ordered; // per system: 1 = ordered passes (one warp per atom), 0 = symmetric tiles
+    // per walker: 1 = advanced by this engine; 0 = kept but not computed (a
+    // walker another engine of a sharded grid advances)
+    const int* w_local;
+    cph_exchange_row* ex_rows; // [W] exchange inputs per walker (this engine's or gathered)
+    int first_local;           // lowest local walker (counts the observables' samples)
 };
 
 } // namespace cph

@@ -584,6 +584,7 @@ __global__ void k_langevin(View V, int s_off, int a0, int n) {
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
+    if (!V.w_local[w]) return;
     const int li = a - V.w_off[w];
     const int P = V.sys_poff[V.w_sys[w]];
     const uint64_t t = (uint64_t)(*V.step + s_off);
@@ -622,6 +623,7 @@ __global__ void k_shake(View V, int i0, int n) {
     if (l >= n) return;
     const int it = i0 + l;
     const int w = V.shk_item_w[it], c = V.shk_item_c[it];
+    if (!V.w_local[w]) return;
     const int A = V.w_off[w], P = V.sys_poff[V.w_sys[w]];
     const int h0 = V.shk_off[c], nh = V.shk_off[c + 1] - h0;
     int at[kShakeMaxH + 1];

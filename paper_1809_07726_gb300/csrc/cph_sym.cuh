@@ -100,6 +100,7 @@ __global__ void k_stage_x(View V, int a0, int n) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
     const int a = a0 + l, o = V.w_off[V.a_walker[a]];
+    if (!V.w_local[V.a_walker[a]]) return;
     V.xs[a] = make_float4((float)(V.x[3 * a] - V.x[3 * o]), (float)(V.x[3 * a + 1] - V.x[3 * o + 1]),
                           (float)(V.x[3 * a + 2] - V.x[3 * o + 2]), 0.f);
 }
@@ -108,6 +109,7 @@ __global__ void k_stage_gb(View V, int a0, int n) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
     const int a = a0 + l;
+    if (!V.w_local[V.a_walker[a]]) return;
     const float R = (float)V.R[a], iR = __frcp_rn(R);
     V.gq[a] = make_float4((float)(V.q[a] * V.sqrt_k), R, iR, (0.25f * kLog2e) * iR);
 }
@@ -447,7 +449,7 @@ __global__ void k_fin_c(View V, int a0, int n) {
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
-    if (V.sys_ordered[V.w_sys[w]]) return; // the ordered passes finish these atoms themselves
+    if (V.sys_ordered[V.w_sys[w]] || !V.w_local[w]) return; // ordered passes finish their atoms themselves
     const int P = V.sys_poff[V.w_sys[w]] + (a - V.w_off[w]);
     const double q = V.q[a] * V.sqrt_k, R = V.R[a];
     const double esa = sa_ace(V.sa_gamma, V.sa_probe, V.rho[P], R);
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
     __shared__ double re[kBondedThreads / 32][2];
     const int w = w0 + blockIdx.y;
     const int s = V.w_sys[w], A = V.w_off[w];
-    if (V.sys_ordered[s]) return; // bonded terms of the ordered passes are in k_chain
+    if (V.sys_ordered[s] || !V.w_local[w]) return; // bonded terms of the ordered passes are in k_chain
     const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0;
     const int a0 = V.sys_ang_off[s], na = V.sys_ang_off[s + 1] - a0;
     const int t = blockIdx.x * kBondedThreads + threadIdx.x;
@@ -782,7 +784,7 @@ __global__ void k_final_forces(View V, int a0, int n) {
     const int a = a0 + l;
     const int w = V.a_walker[a];
     const int s = V.w_sys[w];
-    if (V.sys_ordered[s]) return;
+    if (V.sys_ordered[s] || !V.w_local[w]) return;
     const int A = V.w_off[w], li = a - A, P = V.sys_poff[s];
     double F[3] = {(double)V.Ffix[3 * a] / kScaleE, (double)V.Ffix[3 * a + 1] / kScaleE,
                    (double)V.Ffix[3 * a + 2] / kScaleE};
@@ -1054,7 +1056,7 @@ __global__ void k_fin_born(View V, int a0, int n, int zero_energy) {
     if (l >= n) return;
     const int a = a0 + l;
     const int w = V.a_walker[a];
-    if (V.sys_ordered[V.w_sys[w]]) return;
+    if (V.sys_ordered[V.w_sys[w]] || !V.w_local[w]) return;
     const int li = a - V.w_off[w];
     const int P = V.sys_poff[V.w_sys[w]] + li;
     const double rt = V.rt[P], rho = V.rho[P];

@@ -1,6 +1,6 @@
 """Multi-rank host logic of bench.py on CPU with the gloo backend (world
-size 2): every rank runs its own ensemble; the reported time is the max over
-ranks and the value counts every rank's replica-steps."""
+size 2): the ranks share one grid; the reported time is the max over ranks
+and the value counts the grid's replica-steps once."""
 import os
 import socket
 
@@ -37,4 +37,4 @@ def test_max_over_ranks_and_whole_job_value():
     mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
     assert out[0] == out[1] == 2.5
     import bench
-    assert bench.whole_job_value(world, 384, 10, 2.5) == pytest.approx(2 * 384 * 10 / 2.5)
+    assert bench.whole_job_value(384, 10, 2.5) == pytest.approx(384 * 10 / 2.5)
