@@ -68,7 +68,7 @@ BACKWARD_FAR_COST = (92, 3)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
-PASS_DRAM_BYTES = {"born": 33.38e6, "gb": 89.60e6 + 3.68e6, "chain": 60.35e6}
+PASS_DRAM_BYTES = {"born": 32.95e6 + 2.82e6, "gb": 88.55e6 + 5.88e6, "chain": 59.86e6 + 83.71e6}
 FP32_LANES = 128   # FP32 lane operations per clock per SM
 MUFU_LANES = 16    # MUFU operations per clock per SM
 
