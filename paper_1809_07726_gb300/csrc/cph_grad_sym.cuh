@@ -530,7 +530,8 @@ static __device__ __noinline__ GcNear gchain_near(float r2, float rinv, float ci
 
 template <bool MASKED, bool CUT>
 __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2 (&I)[2], float2 (&ai)[2][5],
-                                            float2 (&aj)[5], const uint32_t (&sk)[2][2], const PairBand& band) {
+                                            float2 (&aj)[5], const uint32_t (&sk)[2][2], const PairBand& band,
+                                            float* __restrict__ hti, float2* __restrict__ htj) {
     const int src = (lane + 1) & 31;
     const float skr2 = band.skr2;
     const float2 mone = splat<float2>(-1.f);
@@ -585,8 +586,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                     const GcNear o = gchain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.z, Nj.x,
                                                  Nj.z, Mj.x, band.rc);
                     t[u].x = o.t;
-                    ai[u][3].x += o.hti;
-                    aj[3].x += o.htj;
+                    hti[u * 32] += o.hti;
+                    htj[(lane + k) & (kGJ - 1)].x += o.htj;
                     asi[u].x = o.asi;
                     asj[u].x = o.asj;
                     wt[u].x = 1.f;
@@ -595,8 +596,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                     const GcNear o = gchain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.w, Nj.y,
                                                  Nj.w, Mj.y, band.rc);
                     t[u].y = o.t;
-                    ai[u][3].y += o.hti;
-                    aj[3].y += o.htj;
+                    hti[u * 32] += o.hti;
+                    htj[(lane + k) & (kGJ - 1)].y += o.htj;
                     asi[u].y = o.asi;
                     asj[u].y = o.asj;
                     wt[u].y = 1.f;
@@ -624,6 +625,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
         }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
+            if (c == 3) continue; // dH/drt partials are kept in shared memory (closed forms only)
             aj[c].x = __shfl_sync(0xffffffffu, aj[c].x, src);
             aj[c].y = __shfl_sync(0xffffffffu, aj[c].y, src);
         }
@@ -635,6 +637,10 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
     __shared__ GcJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ][5];
     __shared__ long long sfx[5][kGI]; // i-side sums, component-major (conflict-free)
+    // dH/drt sums, which only the rare closed-form pairs feed: i side per
+    // thread and atom over a staged group, partner side per warp and tile pair
+    __shared__ float hti_s[kGI];
+    __shared__ float2 htj_s[kGT / 32][kGJ];
     const GItem it = gitem(g);
     if (!it.ok) return;
     const int n = g.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -697,10 +703,14 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
         float2 ai[2][5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) ai[0][c] = ai[1][c] = make_float2(0.f, 0.f);
+        hti_s[warp * 64 + lane] = 0.f;
+        hti_s[warp * 64 + 32 + lane] = 0.f;
         for (int pr = 0; pr < npair; ++pr) {
             float2 aj[5];
 #pragma unroll
             for (int c = 0; c < 5; ++c) aj[c] = make_float2(0.f, 0.f);
+            htj_s[warp][lane] = make_float2(0.f, 0.f);
+            __syncwarp();
             uint32_t sk[2][2] = {{0u, 0u}, {0u, 0u}};
             bool masked = false;
 #pragma unroll
@@ -712,8 +722,10 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
                     for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
                 }
             }
-            if (masked) gchain_tile<true, CUT>(sj[pr], lane, I, ai, aj, sk, band);
-            else gchain_tile<false, CUT>(sj[pr], lane, I, ai, aj, sk, band);
+            if (masked) gchain_tile<true, CUT>(sj[pr], lane, I, ai, aj, sk, band, &hti_s[warp * 64 + lane], htj_s[warp]);
+            else gchain_tile<false, CUT>(sj[pr], lane, I, ai, aj, sk, band, &hti_s[warp * 64 + lane], htj_s[warp]);
+            __syncwarp();
+            aj[3] = htj_s[warp][lane]; // lane l: partner l of both tiles
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 const float sgn = c < 3 ? -1.f : 1.f;
@@ -724,6 +736,7 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int row = warp * 64 + u * 32 + lane;
+            ai[u][3] = make_float2(hti_s[row], 0.f);
 #pragma unroll
             for (int c = 0; c < 5; ++c) sfx[c][row] += to_fixed(ai[u][c].x + ai[u][c].y, (float)kScaleE);
         }
