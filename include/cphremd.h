@@ -141,7 +141,7 @@ typedef struct cph_grid_desc {
  * tau(f) = 1/eps_in - exp(-kappa f)/eps_out (f = R for the self terms); the
  * paper states no salt, and 0 (the default) gives the constant
  * 1/eps_in - 1/eps_out.  The differentiable energy (cph_gb_energy*) takes
- * kappa = 0 only; it includes the surface term. */
+ * every option: salt, the surface term and the cutoff. */
 typedef struct cph_gb_params {
     double eps_in, eps_out;
     double offset;                  /* rho_tilde = rho - offset */

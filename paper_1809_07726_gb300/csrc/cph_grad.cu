@@ -89,8 +89,8 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     if (!(gb->eps_in > 0) || !(gb->eps_out > 0)) return gfail(CPH_E_INVALID, "cph_gb_energy: bad dielectric");
     if (!std::isfinite(gb->sa_gamma) || !(gb->sa_probe >= 0))
         return gfail(CPH_E_INVALID, "cph_gb_energy: bad surface-term parameters");
-    if (gb->kappa != 0.0)
-        return gfail(CPH_E_INVALID, "cph_gb_energy: salt screening (kappa > 0) is not supported here");
+    if (!(gb->kappa >= 0) || !std::isfinite(gb->kappa))
+        return gfail(CPH_E_INVALID, "cph_gb_energy: salt screening kappa must be finite and >= 0");
     if (!(gb->rgbmax >= 0) || !std::isfinite(gb->rgbmax))
         return gfail(CPH_E_INVALID, "cph_gb_energy: rgbmax must be finite and >= 0 (0 = no cutoff)");
     g = SView{};
@@ -104,6 +104,10 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     g.rho = rho;
     g.screen = screen;
     g.tau = 1.0 / gb->eps_in - 1.0 / gb->eps_out;
+    g.kappa = gb->kappa;
+    g.inv_eps_in = 1.0 / gb->eps_in;
+    g.inv_eps_out = 1.0 / gb->eps_out;
+    g.tau_pair = gb->kappa > 0 ? 1.0 : g.tau;
     g.sqrt_k = std::sqrt(kCoulomb);
     g.alpha = gb->alpha;
     g.beta = gb->beta;
@@ -150,7 +154,8 @@ extern "C" int cph_gb_energy(int n_rep, int n, const float* x, const float* q, c
     if (rc != CPH_OK) return rc;
     const size_t na = (size_t)n_rep * n;
     const int ba = (int)((na + 255) / 256);
-    k_gpair_sym<false><<<n_rep * g.n_itile * g.n_chunk, kGT, 0, st>>>(g);
+    if (g.kappa > 0) k_gpair_sym<false, true><<<n_rep * g.n_itile * g.n_chunk, kGT, 0, st>>>(g);
+    else k_gpair_sym<false, false><<<n_rep * g.n_itile * g.n_chunk, kGT, 0, st>>>(g);
     k_gfin_c<false><<<ba, 256, 0, st>>>(g);
     k_genergy_out<<<(n_rep + 127) / 128, 128, 0, st>>>(g);
     cudaError_t ce = cudaGetLastError();
@@ -176,7 +181,8 @@ extern "C" int cph_gb_energy_backward(int n_rep, int n, const float* x, const fl
     const size_t na = (size_t)n_rep * n;
     const int ba = (int)((na + 255) / 256);
     const int grid = n_rep * g.n_itile * g.n_chunk;
-    k_gpair_sym<true><<<grid, kGT, 0, st>>>(g);
+    if (g.kappa > 0) k_gpair_sym<true, true><<<grid, kGT, 0, st>>>(g);
+    else k_gpair_sym<true, false><<<grid, kGT, 0, st>>>(g);
     k_gfin_c<true><<<ba, 256, 0, st>>>(g);
     if (g.rgbmax < INFINITY) k_gchain_sym<true><<<grid, kGT, 0, st>>>(g);
     else k_gchain_sym<false><<<grid, kGT, 0, st>>>(g);

@@ -35,6 +35,10 @@ struct SView {
     int n_rep, n, n_itile, n_jtile, n_chunk;
     const float *x, *q, *rho, *screen;
     double tau, sqrt_k, alpha, beta, gamma, offset;
+    // Debye-Hueckel salt screening: kappa (1/A), 1/eps_in, 1/eps_out; tau_pair is
+    // the factor the finishing kernels apply to the pair sums (tau without
+    // salt; 1 with salt, whose pair terms carry tau(f) per pair)
+    double kappa, inv_eps_in, inv_eps_out, tau_pair;
     double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
     double rgbmax;             // Born-radius cutoff, INFINITY = none
     // per replica-atom (index r * n + a); int64 slots alias double slots that
@@ -230,13 +234,19 @@ struct GpJs {
     float4 c[2 * kGJ]; // (RA, RB, 1/RA, 1/RB)
 };
 
-template <bool MASKED, bool BACKWARD>
+// SALT: every GB pair term carries tau(f) = 1/eps_in - exp(-kappa f)/eps_out
+// (energy, dE/dq) and taud(f) = tau(f) - kappa f exp(-kappa f)/eps_out (dE/df),
+// f the effective distance; the finishing kernels then scale the pair sums by
+// 1 instead of tau.  Salt steps always take the full form.
+template <bool MASKED, bool BACKWARD, bool SALT>
 __device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 (&I)[2], float2 (&ai)[2][5],
                                            float2 (&aj)[5], float2 (&ei)[2], const uint32_t (&sk)[2][2],
-                                           float tau) {
+                                           float tau, float iei, float ieo, float kappa) {
     const int src = (lane + 1) & 31;
     const float2 ln2 = splat<float2>(kLn2), one = splat<float2>(1.f), tau2 = splat<float2>(tau),
-                 mtau4 = splat<float2>(-0.25f * tau);
+                 mtau4 = splat<float2>(-0.25f * tau), ie = splat<float2>(iei), ieo2 = splat<float2>(ieo),
+                 mone = splat<float2>(-1.f), q25 = splat<float2>(0.25f), kap2 = splat<float2>(kappa);
+    const float kl = kappa * kLog2e;
 #pragma unroll 2
     for (int k = 0; k < kGJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
@@ -260,7 +270,7 @@ __device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 
         }
         // a step whose pairs all have D >= 18: 1/f = 1/r, no exponential, no
         // dE/dR term (see kGbFarD2)
-        const bool far = !MASKED &&
+        const bool far = !MASKED && !SALT &&
                          __all_sync(0xffffffffu, fminf(fminf(D2[0].x, D2[0].y), fminf(D2[1].x, D2[1].y)) >= kGbFarD2);
         if (far) {
 #pragma unroll
@@ -291,17 +301,27 @@ __device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 
                     fi.y = s1[u] ? 0.f : fi.y;
                 }
                 const float2 qq = __fmul2_rn(I[u].q, qj);
-                ei[u] = __ffma2_rn(qq, fi, ei[u]);
+                float2 tf = one, td = one;
+                if (SALT) {
+                    const float2 f = __fmul2_rn(fa, fi); // effective distance
+                    const float2 es = __fmul2_rn(ieo2, make_float2(exp2_ftz(-kl * f.x), exp2_ftz(-kl * f.y)));
+                    tf = __ffma2_rn(es, mone, ie);                                 // tau(f)
+                    td = __ffma2_rn(__fmul2_rn(kap2, f), __fmul2_rn(es, mone), tf); // taud(f)
+                }
+                const float2 fit = SALT ? __fmul2_rn(fi, tf) : fi; // tau(f) / f (tau factored out without salt)
+                ei[u] = __ffma2_rn(qq, fit, ei[u]);
                 if (BACKWARD) {
                     const float2 qf3 = __fmul2_rn(qq, __fmul2_rn(__fmul2_rn(fi, fi), fi));
                     const float2 qfe = __fmul2_rn(qf3, e);
-                    const float2 t = __fmul2_rn(qfe, __ffma2_rn(D2[u], ln2, one));
+                    float2 t = __fmul2_rn(qfe, __ffma2_rn(D2[u], ln2, one));
+                    if (SALT) t = __fmul2_rn(t, td);
                     ai[u][0] = __ffma2_rn(t, Rj, ai[u][0]);
                     aj[0] = __ffma2_rn(t, I[u].R, aj[0]);
-                    ai[u][1] = __ffma2_rn(qj, fi, ai[u][1]);
-                    aj[1] = __ffma2_rn(I[u].q, fi, aj[1]);
-                    // tau qf3 (1 - e/4)
-                    const float2 g2 = __ffma2_rn(mtau4, qfe, __fmul2_rn(tau2, qf3));
+                    ai[u][1] = __ffma2_rn(qj, fit, ai[u][1]);
+                    aj[1] = __ffma2_rn(I[u].q, fit, aj[1]);
+                    // tau qf3 (1 - e/4); with salt taud(f) in place of tau
+                    const float2 g2 = SALT ? __fmul2_rn(td, __ffma2_rn(mone, __fmul2_rn(q25, qfe), qf3))
+                                           : __ffma2_rn(mtau4, qfe, __fmul2_rn(tau2, qf3));
                     ai[u][2] = __ffma2_rn(g2, dx[u], ai[u][2]);
                     ai[u][3] = __ffma2_rn(g2, dy[u], ai[u][3]);
                     ai[u][4] = __ffma2_rn(g2, dz[u], ai[u][4]);
@@ -321,7 +341,7 @@ __device__ __forceinline__ void gpair_tile(const GpJs& sj, int lane, const GpI2 
     }
 }
 
-template <bool BACKWARD>
+template <bool BACKWARD, bool SALT>
 __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
     __shared__ GpJs sj[kGG / 2];
     __shared__ float red[kGG][4][kGJ][5];
@@ -333,7 +353,8 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* Q = g.q + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float sqk = (float)g.sqrt_k, tau = (float)g.tau;
+    const float sqk = (float)g.sqrt_k, tau = (float)g.tau, iei = (float)g.inv_eps_in, ieo = (float)g.inv_eps_out,
+                kap = (float)g.kappa;
     int ii[2];
     bool vi[2];
     GpI2 I[2];
@@ -400,8 +421,8 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
                     for (int u = 0; u < 2; ++u) sk[u][h] = gskip(ii[u], vi[u], jt * kGJ, n);
                 }
             }
-            if (masked) gpair_tile<true, BACKWARD>(sj[pr], lane, I, ai, aj, ei, sk, tau);
-            else gpair_tile<false, BACKWARD>(sj[pr], lane, I, ai, aj, ei, sk, tau);
+            if (masked) gpair_tile<true, BACKWARD, SALT>(sj[pr], lane, I, ai, aj, ei, sk, tau, iei, ieo, kap);
+            else gpair_tile<false, BACKWARD, SALT>(sj[pr], lane, I, ai, aj, ei, sk, tau, iei, ieo, kap);
             // energy: plain per-tile sums, compensated across tiles
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -458,7 +479,7 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
     __syncthreads();
     if (tid == 0) {
         const double v = ered[0] + ered[1] + ered[2] + ered[3];
-        atomicAdd((unsigned long long*)&g.eacc[it.rep], (unsigned long long)__double2ll_rn(-g.tau * v * kScaleE));
+        atomicAdd((unsigned long long*)&g.eacc[it.rep], (unsigned long long)__double2ll_rn(-g.tau_pair * v * kScaleE));
     }
 }
 
@@ -469,13 +490,16 @@ __global__ void k_gfin_c(SView g) {
     if (a >= (size_t)g.n_rep * g.n) return;
     const double q = (double)g.q[a] * g.sqrt_k, R = g.R[a];
     const double esa = sa_ace(g.sa_gamma, g.sa_probe, (double)g.rho[a], R);
+    const double ts = salt_tau(R, g.inv_eps_in, g.inv_eps_out, g.kappa); // tau of the self term
     atomicAdd((unsigned long long*)&g.eacc[a / g.n],
-              (unsigned long long)__double2ll_rn((-0.5 * g.tau * q * q / R + esa) * kScaleE));
+              (unsigned long long)__double2ll_rn((-0.5 * ts * q * q / R + esa) * kScaleE));
     if (!BACKWARD) return;
-    const double dEdR = 0.5 * g.tau * ((double)g.dRfix[a] / kScaleE + q * q / (R * R)) - 6.0 * esa / R;
+    const double dEdR = 0.5 * (g.tau_pair * ((double)g.dRfix[a] / kScaleE)
+                               + salt_taud(R, g.inv_eps_in, g.inv_eps_out, g.kappa) * q * q / (R * R))
+                      - 6.0 * esa / R;
     const double rt = (double)g.rho[a] - g.offset;
     const double gpsi = dEdR * g.gpsi[a]; // gpsi slot held dR/dpsi
-    const double dq = -g.tau * g.sqrt_k * ((double)g.dqfix[a] / kScaleE + q / R);
+    const double dq = -g.sqrt_k * (g.tau_pair * ((double)g.dqfix[a] / kScaleE) + ts * q / R);
     g.dEdR[a] = dEdR; // same slot as dRfix
     g.gpsi[a] = gpsi;
     g.c[a] = gpsi * 0.5 * rt;

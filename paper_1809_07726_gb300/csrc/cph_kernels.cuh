@@ -380,11 +380,13 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
 }
 
 // Bonded forces on atom i (system-local index li) and its owned energy
-// shares (a bond or angle is owned by its first atom).
-__device__ inline void bonded_atom(const View& V, int A, int P, int li, double F[3], double& eb,
+// shares (a bond or angle is owned by its first atom), split over the lanes of
+// a warp: lane l takes the atom's terms l, l + 32, ... of each kind (the
+// caller sums the lanes in a fixed order).
+__device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane, double F[3], double& eb,
                                    double& ea) {
     const double* x = V.x;
-    for (int e = V.bond_off[P + li]; e < V.bond_off[P + li + 1]; ++e) {
+    for (int e = V.bond_off[P + li] + lane; e < V.bond_off[P + li + 1]; e += 32) {
         const int b = V.bond_idx[e];
         const int ia = V.bond_ij[2 * b], ib = V.bond_ij[2 * b + 1];
         const int o = (ia == li) ? ib : ia;
@@ -396,7 +398,7 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, double F
         for (int c = 0; c < 3; ++c) F[c] -= g * d[c];
         if (ia == li) eb += V.bond_k[b] * dr * dr;
     }
-    for (int e = V.ang_off[P + li]; e < V.ang_off[P + li + 1]; ++e) {
+    for (int e = V.ang_off[P + li] + lane; e < V.ang_off[P + li + 1]; e += 32) {
         const int a = V.ang_idx[e];
         const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
         double u[3], v[3];
@@ -524,11 +526,19 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
     fy = warp_total(fy);
     fz = warp_total(fz);
     double eb = 0.0, ea = 0.0;
+    double Fb[3] = {0.0, 0.0, 0.0};
+    if (vi) { // bonded terms of atom i over the lanes, summed by a fixed tree
+        bonded_atom(V, A, P, i, lane, Fb, eb, ea);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Fb[c] = warp_total(Fb[c]);
+        eb = warp_total(eb);
+        ea = warp_total(ea);
+        if (lane != 0) eb = ea = 0.0; // the warp's totals sit in lane 0
+    }
     if (vi && lane == 0) {
-        double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE),
-                       V.Fd[3 * (A + i) + 1] + Pr::value(fy, kScaleE),
-                       V.Fd[3 * (A + i) + 2] + Pr::value(fz, kScaleE)};
-        bonded_atom(V, A, P, i, F, eb, ea);
+        double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE) + Fb[0],
+                       V.Fd[3 * (A + i) + 1] + Pr::value(fy, kScaleE) + Fb[1],
+                       V.Fd[3 * (A + i) + 2] + Pr::value(fz, kScaleE) + Fb[2]};
         V.F[3 * (A + i)] = F[0];
         V.F[3 * (A + i) + 1] = F[1];
         V.F[3 * (A + i) + 2] = F[2];

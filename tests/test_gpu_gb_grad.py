@@ -134,12 +134,41 @@ def test_cutoff_energy_and_gradient_match_oracle(rgbmax, n):
         assert _rel_rms(dr[r], gr) <= 1e-5
 
 
-def test_salt_is_refused_by_the_differentiable_energy():
+@pytest.mark.parametrize("kappa,extra", [(0.1, {}), (0.05, dict(sa_gamma=0.005, rgbmax=12.0))])
+def test_salt_energy_and_gradient_match_oracle(kappa, extra):
+    """Debye-Hueckel salt screening through the differentiable energy: every
+    GB term carries tau(f) per pair (energy, dE/dq) and its f-derivative (dE/dx,
+    dE/dR, hence dE/drho); alone and with the surface term and a cutoff."""
+    import torch
+    gb = cphremd.default_gb()
+    gb.kappa = kappa
+    gb.sa_gamma = extra.get("sa_gamma", 0.0)
+    gb.rgbmax = extra.get("rgbmax", 0.0)
+    s, x, q, rho = _batch(2, 300, 47)
+    xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
+    st = _torch(s.screen, torch.float32)
+    E = cphremd.gb_energy(xt, qt, rt, st, gb=gb).cpu().numpy()
+    dx, dq, dr = (t.cpu().numpy().astype(np.float64) for t in cphremd.gb_energy_backward(
+        xt, qt, rt, st, torch.ones(2, dtype=torch.float64, device="cuda:0"), gb=gb))
+    og = oracle.GBParams(kappa=kappa, sa_gamma=gb.sa_gamma, rgbmax=gb.rgbmax)
+    for r in range(2):
+        xr, qr, rr = (a[r].astype(np.float32).astype(np.float64) for a in (x, q, rho))
+        sc = s.screen.astype(np.float32).astype(np.float64)
+        Eo, gx, gq, gr = oracle.gb_grad(xr, qr, rr, sc, og)
+        E0 = oracle.gb_grad(xr, qr, rr, sc, oracle.GBParams(sa_gamma=gb.sa_gamma, rgbmax=gb.rgbmax))[0]
+        assert abs(Eo - E0) > 1e-4 * abs(E0)  # the salt matters here (100x the energy bar)
+        assert abs(E[r] - Eo) <= 1e-6 * abs(Eo), (E[r], Eo)
+        assert _rel_rms(dx[r], gx) <= 1e-5
+        assert _rel_rms(dq[r], gq) <= 1e-5
+        assert _rel_rms(dr[r], gr) <= 1e-5
+
+
+def test_negative_salt_is_refused_by_the_differentiable_energy():
     import torch
     s, x, q, rho = _batch(1, 40, 3)
     xt, qt, rt = _torch(x, torch.float32), _torch(q, torch.float32), _torch(rho, torch.float32)
     st = _torch(s.screen, torch.float32)
-    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, 0.1)
+    gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, -0.1)
     with pytest.raises(cphremd.CphError) as e:
         cphremd.gb_energy(xt, qt, rt, st, gb=gb)
     assert e.value.code == cphremd.E_INVALID
