@@ -671,6 +671,17 @@ def run_gpu(args):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+        # the differentiation workload's oracle: energy and analytic gradient of
+        # one replica of the 8000-atom system, single-threaded, measured
+        s5, x5, q5, rho5 = synth.config_c5(n_rep=1)
+        t0 = time.perf_counter()
+        oracle.gb_grad(x5[0], q5[0], rho5[0], s5.screen)
+        secs5 = time.perf_counter() - t0
+        if backward is not None:
+            backward["cpu_baseline"] = {"value": 1.0 / secs5, "unit": "replica evaluations/s", "cores": 1,
+                                        "kind": "oracle", "seconds": secs5,
+                                        "sample": "E_GB and its x, q, rho gradient of one 8000-atom "
+                                                  "replica, single-threaded; measured"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
