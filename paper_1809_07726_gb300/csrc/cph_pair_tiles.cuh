@@ -12,8 +12,10 @@ constexpr int kTileJ = 32; // atoms per j-tile
 // Far GB pairs: with D = r^2 / (4 R_i R_j) >= 18, e^-D <= 1.6e-8, so
 // 1/f = 1/r to 1e-10 relative, the GB force factor (1 - e^-D / 4) is 1 to
 // 4e-9, and the pair's dE/dR term (~ e^-D (1 + D)) is below 3e-7 of its
-// q_i q_j / r^3 (and far below the self and near-pair terms of dE/dR).  GB
-// tiles take that form for a step whose pairs all meet the bound.
+// q_i q_j / r^3 (and far below the self and near-pair terms of dE/dR).  The
+// engine's GB tiles take that form for each i-atom row of a step whose pairs
+// all meet the bound (a warp vote per row), the adjoint's tiles for a step
+// whose pairs all do (a warp vote per step).
 constexpr float kGbFarD2 = 18.f * kLog2e; // the threshold on D log2(e)
 
 // ========================================================= Born radii
