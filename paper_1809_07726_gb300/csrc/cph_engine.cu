@@ -592,6 +592,7 @@ struct cph_engine {
     Item* d_items_by_w = nullptr;
     std::vector<int> h_sys_shape;  // CPH_SHAPE_* per system (FP32 mode)
     int* d_sys_ordered = nullptr;  // 1 where a system runs the ordered passes
+    int ordered_wpa = 1;           // warps per atom of the ordered passes (1 or 4)
     std::vector<int> h_w_local;    // 1 for the walkers this engine advances
     int* d_w_local = nullptr;
     bool sharded = false;          // some walker is not local
@@ -689,6 +690,9 @@ bool finite_all(const double* p, size_t n) {
     return true;
 }
 
+// At most this many atoms on the FP64 ordered passes: four warps per atom.
+constexpr long long kOrderedFewAtoms = 2048;
+
 // Whether walkers of system s run the ordered passes (one warp per atom i):
 // always in FP64 mode, by the system's tile shape in FP32 mode.
 bool sys_ordered(const cph_engine* E, int s) {
@@ -696,38 +700,48 @@ bool sys_ordered(const cph_engine* E, int s) {
 }
 
 // ---- launch helpers
+// The ordered passes run one warp per atom (four atoms per CTA), or, in FP64
+// mode with few atoms (E->ordered_wpa = 4), four warps per atom: even a single
+// small walker then spreads its FP64 work over one CTA per atom.
+template <class Real, int WPA>
+void born_t(const Item* items, int n, View V, int ze, cudaStream_t st) {
+    k_born<Real, WPA><<<n, kTile, 0, st>>>(items, V, ze);
+}
+template <class Real, int WPA>
+void gb_t(const Item* items, int n, View V, bool energy, cudaStream_t st) {
+    if (energy) k_gb<Real, true, WPA><<<n, kTile, 0, st>>>(items, V);
+    else k_gb<Real, false, WPA><<<n, kTile, 0, st>>>(items, V);
+}
+template <class Real, int WPA>
+void chain_t(const Item* items, int n, View V, bool energy, cudaStream_t st) {
+    if (energy) k_chain<Real, true, WPA><<<n, kTile, 0, st>>>(items, V);
+    else k_chain<Real, false, WPA><<<n, kTile, 0, st>>>(items, V);
+}
+
 int launch_born(cph_engine* E, const Item* items, int n, bool zero_energy, cudaStream_t st) {
     if (n <= 0) return CPH_OK;
-    if (E->precision == CPH_PREC_FP32)
-        k_born<float><<<n, kTile, 0, st>>>(items, E->V, zero_energy ? 1 : 0);
-    else
-        k_born<double><<<n, kTile, 0, st>>>(items, E->V, zero_energy ? 1 : 0);
+    const bool f32 = E->precision == CPH_PREC_FP32, w4 = E->ordered_wpa == 4;
+    const int ze = zero_energy ? 1 : 0;
+    if (f32) (w4 ? born_t<float, 4> : born_t<float, 1>)(items, n, E->V, ze, st);
+    else (w4 ? born_t<double, 4> : born_t<double, 1>)(items, n, E->V, ze, st);
     CK(cudaGetLastError());
     return CPH_OK;
 }
 
 int launch_gb(cph_engine* E, const Item* items, int n, bool energy, cudaStream_t st) {
     if (n <= 0) return CPH_OK;
-    if (E->precision == CPH_PREC_FP32) {
-        if (energy) k_gb<float, true><<<n, kTile, 0, st>>>(items, E->V);
-        else k_gb<float, false><<<n, kTile, 0, st>>>(items, E->V);
-    } else {
-        if (energy) k_gb<double, true><<<n, kTile, 0, st>>>(items, E->V);
-        else k_gb<double, false><<<n, kTile, 0, st>>>(items, E->V);
-    }
+    const bool f32 = E->precision == CPH_PREC_FP32, w4 = E->ordered_wpa == 4;
+    if (f32) (w4 ? gb_t<float, 4> : gb_t<float, 1>)(items, n, E->V, energy, st);
+    else (w4 ? gb_t<double, 4> : gb_t<double, 1>)(items, n, E->V, energy, st);
     CK(cudaGetLastError());
     return CPH_OK;
 }
 
 int launch_chain(cph_engine* E, const Item* items, int n, bool energy, cudaStream_t st) {
     if (n <= 0) return CPH_OK;
-    if (E->precision == CPH_PREC_FP32) {
-        if (energy) k_chain<float, true><<<n, kTile, 0, st>>>(items, E->V);
-        else k_chain<float, false><<<n, kTile, 0, st>>>(items, E->V);
-    } else {
-        if (energy) k_chain<double, true><<<n, kTile, 0, st>>>(items, E->V);
-        else k_chain<double, false><<<n, kTile, 0, st>>>(items, E->V);
-    }
+    const bool f32 = E->precision == CPH_PREC_FP32, w4 = E->ordered_wpa == 4;
+    if (f32) (w4 ? chain_t<float, 4> : chain_t<float, 1>)(items, n, E->V, energy, st);
+    else (w4 ? chain_t<double, 4> : chain_t<double, 1>)(items, n, E->V, energy, st);
     CK(cudaGetLastError());
     return CPH_OK;
 }
@@ -1036,11 +1050,21 @@ int build_items(cph_engine* E, int chunk) {
     std::vector<int> o_off(W + 1, 0);
     std::vector<int> ordered(E->n_sys);
     for (int s = 0; s < E->n_sys; ++s) ordered[s] = sys_ordered(E, s) ? 1 : 0;
+    // FP64 arithmetic on few atoms (a small walker or two): four warps per atom,
+    // one atom per CTA, so that the scarce FP64 units of every SM share the
+    // work.  Counted over the whole grid, local or not, so that every engine of
+    // a sharded grid sums in the same order.  (FP32 small systems measured no
+    // faster this way: the staging of the j atoms, not the arithmetic, grows.)
+    long long n_oatoms = 0;
+    for (int w = 0; w < W; ++w)
+        if (ordered[E->h_w_sys[w]]) n_oatoms += E->h_sys_n[E->h_w_sys[w]];
+    E->ordered_wpa = (E->precision == CPH_PREC_FP64 && n_oatoms <= kOrderedFewAtoms) ? 4 : 1;
+    const int apc = kWarpAtoms / E->ordered_wpa; // atoms per CTA
     for (int w = 0; w < W; ++w) {
         const int s = E->h_w_sys[w], N = E->h_sys_n[s];
         // the masked j-tiles of a group are those of the 128-atom i-tile it lies in
         if (ordered[s] && E->h_w_local[w])
-            for (int i0 = 0; i0 < N; i0 += kWarpAtoms)
+            for (int i0 = 0; i0 < N; i0 += apc)
                 o_by_w.push_back(Item{w, i0, E->h_sys_st_off[s] + i0 / kTile, 0});
         o_off[w + 1] = (int)o_by_w.size();
     }

@@ -26,7 +26,7 @@
 namespace cph {
 
 constexpr int kTile = 128;
-constexpr int kWarpAtoms = kTile / 32; // atoms i per CTA of the ordered passes
+constexpr int kWarpAtoms = kTile / 32; // atoms i per CTA of the ordered passes, one warp each
 constexpr float kFarF = 1.0e4f;
 
 // Sum of a lane accumulator over the warp by a fixed shuffle tree; lane 0
@@ -36,6 +36,26 @@ __device__ __forceinline__ T warp_total(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sum over the WPA warps that share one atom (warps g WPA .. g WPA + WPA - 1 of
+// the CTA): warp totals, then the group's warps in index order through the
+// 8-byte shared slots sh[4].  Every thread of the CTA must call it.  The
+// result is exact in lane 0 of each warp for WPA = 1 and in every thread of
+// the group for WPA > 1.
+template <int WPA, class T>
+__device__ __forceinline__ T group_total(T v, long long* sh) {
+    v = warp_total(v);
+    if (WPA == 1) return v;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) reinterpret_cast<T*>(sh)[warp] = v;
+    __syncthreads();
+    T t = 0;
+    const int g0 = (warp / WPA) * WPA;
+#pragma unroll
+    for (int q = 0; q < WPA; ++q) t += reinterpret_cast<const T*>(sh)[g0 + q];
+    __syncthreads();
+    return t;
 }
 
 template <class Real>
@@ -85,15 +105,18 @@ __device__ inline void tile_masks(const View& V, int P, int i, bool vi, int j0, 
 // ------------------------------------------------------------- pass 1: Born radii
 // psi_i = rt_i/2 sum_{j != i} H(r_ij, rt_i, s_j); R_i = 1/(1/rt_i - tanh(theta)/rho_i)
 // with theta = alpha psi - beta psi^2 + gamma psi^3, finalised in FP64.
-template <class Real>
+template <class Real, int WPA>
 __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, View V,
                                                 int zero_energy) {
     using Pr = Prec<Real>;
     __shared__ J4<Real> sj[kTile];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int i = it.i0 + (tid >> 5);
+    // WPA warps per atom i: the CTA holds kWarpAtoms / WPA atoms; `sub` indexes
+    // the thread within its atom's group of 32 WPA threads
+    const int tid = threadIdx.x, warp = tid >> 5, sub = tid - (warp / WPA) * 32 * WPA;
+    const int i = it.i0 + warp / WPA;
+    __shared__ long long gsh[kTile / 32];
     const bool vi = i < N;
     if (it.i0 == 0) {
         if (zero_energy && tid < kEAcc) V.eacc[w * kEAcc + tid] = 0;
@@ -134,7 +157,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         Real part = 0;
         if (jt != next) {
 #pragma unroll
-            for (int k = lane; k < kTile; k += 32) {
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 const J4<Real> b = sj[k];
                 const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
                 const Real r2 = dx * dx + dy * dy + dz * dz;
@@ -146,7 +169,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
             next = mp < me ? V.mt_list[mp] : 0x7fffffff;
             const int dself = i - j0;
 #pragma unroll
-            for (int k = lane; k < kTile; k += 32) {
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 const J4<Real> b = sj[k];
                 const bool self = (k == dself);
                 const Real dx = xi - b.x, dy = yi - b.y, dz = zi - b.z;
@@ -159,8 +182,8 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
         }
         Pr::add(acc, part, Real(kScaleH));
     }
-    acc = warp_total(acc);
-    if (vi && lane == 0) {
+    acc = group_total<WPA>(acc, gsh);
+    if (vi && sub == 0) {
         const double sumH = Pr::value(acc, kScaleH);
         const double rt = V.rt[P + i], rho = V.rho[P + i];
         const double psi = 0.5 * rt * sumH;
@@ -179,7 +202,7 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
 // ------------------------------------------- pass 2: GB + Coulomb + LJ pair pass
 // Owner i accumulates the direct force, dE_GB/dR_i and (optionally) its share
 // of the energies; the epilogue turns dE/dR_i into c_i = dE/dR_i dR_i/dpsi_i rt_i/2.
-template <class Real, bool ENERGY>
+template <class Real, bool ENERGY, int WPA>
 __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, View V) {
     using Pr = Prec<Real>;
     using Acc = typename Pr::Acc;
@@ -188,8 +211,11 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
     __shared__ long long red[4];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int i = it.i0 + (tid >> 5);
+    // WPA warps per atom i: the CTA holds kWarpAtoms / WPA atoms; `sub` indexes
+    // the thread within its atom's group of 32 WPA threads
+    const int tid = threadIdx.x, warp = tid >> 5, sub = tid - (warp / WPA) * 32 * WPA;
+    const int i = it.i0 + warp / WPA;
+    __shared__ long long gsh[kTile / 32];
     const bool vi = i < N;
     const Real sqk = Real(V.sqrt_k);
     const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
@@ -241,7 +267,7 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         KSum<Real> pgb, pc, plj;
         if (jt != next) {
 #pragma unroll
-            for (int k = lane; k < kTile; k += 32) {
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 const J4<Real> a = sa[k];
                 const J4<Real> b = sb[k];
                 const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
@@ -281,13 +307,11 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
             uint32_t mex[4], mself[4];
             tile_masks(V, P, i, vi, j0, mex, mself);
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                const uint32_t me_ = mex[q4], ms_ = mself[q4];
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 {
-                    const int kk = lane;
-                    const int k = q4 * 32 + kk;
-                    const bool self = (ms_ >> kk) & 1u;
-                    const bool ex = (me_ >> kk) & 1u;
+                    const int q4 = k >> 5, kk = k & 31;
+                    const bool self = (mself[q4] >> kk) & 1u;
+                    const bool ex = (mex[q4] >> kk) & 1u;
                     const J4<Real> a = sa[k];
                     const J4<Real> b = sb[k];
                     const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
@@ -337,16 +361,16 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
             Pr::add(elj, plj.value(), Real(kScaleE));
         }
     }
-    fx = warp_total(fx);
-    fy = warp_total(fy);
-    fz = warp_total(fz);
-    adr = warp_total(adr);
+    fx = group_total<WPA>(fx, gsh);
+    fy = group_total<WPA>(fy, gsh);
+    fz = group_total<WPA>(fz, gsh);
+    adr = group_total<WPA>(adr, gsh);
     if (ENERGY) {
-        egb = warp_total(egb);
-        ec = warp_total(ec);
-        elj = warp_total(elj);
+        egb = group_total<WPA>(egb, gsh);
+        ec = group_total<WPA>(ec, gsh);
+        elj = group_total<WPA>(elj, gsh);
     }
-    if (vi && lane == 0) {
+    if (vi && sub == 0) {
         const double q = V.q[A + i] * V.sqrt_k;
         const double R = V.R[A + i];
         const double dEdR = 0.5 * (V.tau_pair * Pr::value(adr, kScaleE)
@@ -359,7 +383,7 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
     }
     if (ENERGY) {
         long long e0 = 0, e1 = 0, e2 = 0;
-        if (vi && lane == 0) {
+        if (vi && sub == 0) {
             const double q = V.q[A + i] * V.sqrt_k;
             const double R = V.R[A + i];
             e0 = __double2ll_rn((-0.5 * (V.tau_pair * Pr::value(egb, kScaleE)
@@ -380,13 +404,13 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
 }
 
 // Bonded forces on atom i (system-local index li) and its owned energy
-// shares (a bond or angle is owned by its first atom), split over the lanes of
-// a warp: lane l takes the atom's terms l, l + 32, ... of each kind (the
-// caller sums the lanes in a fixed order).
-__device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane, double F[3], double& eb,
-                                   double& ea) {
+// shares (a bond or angle is owned by its first atom), split over the threads
+// of the atom's group: thread l takes the atom's terms l, l + stride, ... of
+// each kind (the caller sums the threads in a fixed order).
+__device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane, int stride, double F[3],
+                                   double& eb, double& ea) {
     const double* x = V.x;
-    for (int e = V.bond_off[P + li] + lane; e < V.bond_off[P + li + 1]; e += 32) {
+    for (int e = V.bond_off[P + li] + lane; e < V.bond_off[P + li + 1]; e += stride) {
         const int b = V.bond_idx[e];
         const int ia = V.bond_ij[2 * b], ib = V.bond_ij[2 * b + 1];
         const int o = (ia == li) ? ib : ia;
@@ -398,7 +422,7 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
         for (int c = 0; c < 3; ++c) F[c] -= g * d[c];
         if (ia == li) eb += V.bond_k[b] * dr * dr;
     }
-    for (int e = V.ang_off[P + li] + lane; e < V.ang_off[P + li + 1]; e += 32) {
+    for (int e = V.ang_off[P + li] + lane; e < V.ang_off[P + li + 1]; e += stride) {
         const int a = V.ang_idx[e];
         const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
         double u[3], v[3];
@@ -430,7 +454,7 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
 // ------------------------------------------ pass 3: chain rule through Born radii
 // F_i -= sum_j (c_i dH(r; rt_i, s_j)/dr + c_j dH(r; rt_j, s_i)/dr) (x_i - x_j)/r,
 // then the direct pair force and the bonded terms are added: F is the total force.
-template <class Real, bool ENERGY>
+template <class Real, bool ENERGY, int WPA>
 __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items, View V) {
     using Pr = Prec<Real>;
     using Acc = typename Pr::Acc;
@@ -439,8 +463,11 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
     __shared__ long long red[4];
     const Item it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int i = it.i0 + (tid >> 5);
+    // WPA warps per atom i: the CTA holds kWarpAtoms / WPA atoms; `sub` indexes
+    // the thread within its atom's group of 32 WPA threads
+    const int tid = threadIdx.x, warp = tid >> 5, sub = tid - (warp / WPA) * 32 * WPA;
+    const int i = it.i0 + warp / WPA;
+    __shared__ long long gsh[kTile / 32];
     const bool vi = i < N;
     const double cx = V.x[3 * (A + it.i0)], cy = V.x[3 * (A + it.i0) + 1],
                  cz = V.x[3 * (A + it.i0) + 2];
@@ -484,7 +511,7 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
         Real px = 0, py = 0, pz = 0;
         if (jt != next) {
 #pragma unroll
-            for (int k = lane; k < kTile; k += 32) {
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 const J4<Real> a = sa[k];
                 const J2<Real> b = sb[k];
                 const Real dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
@@ -502,7 +529,7 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
             next = mp < me ? V.mt_list[mp] : 0x7fffffff;
             const int dself = i - j0;
 #pragma unroll
-            for (int k = lane; k < kTile; k += 32) {
+            for (int k = sub; k < kTile; k += 32 * WPA) {
                 const J4<Real> a = sa[k];
                 const J2<Real> b = sb[k];
                 const bool self = (k == dself);
@@ -522,20 +549,19 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
         Pr::add(fy, py, Real(kScaleE));
         Pr::add(fz, pz, Real(kScaleE));
     }
-    fx = warp_total(fx);
-    fy = warp_total(fy);
-    fz = warp_total(fz);
+    fx = group_total<WPA>(fx, gsh);
+    fy = group_total<WPA>(fy, gsh);
+    fz = group_total<WPA>(fz, gsh);
     double eb = 0.0, ea = 0.0;
     double Fb[3] = {0.0, 0.0, 0.0};
-    if (vi) { // bonded terms of atom i over the lanes, summed by a fixed tree
-        bonded_atom(V, A, P, i, lane, Fb, eb, ea);
+    // bonded terms of atom i over the group's threads, summed in a fixed order
+    if (vi) bonded_atom(V, A, P, i, sub, 32 * WPA, Fb, eb, ea);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Fb[c] = warp_total(Fb[c]);
-        eb = warp_total(eb);
-        ea = warp_total(ea);
-        if (lane != 0) eb = ea = 0.0; // the warp's totals sit in lane 0
-    }
-    if (vi && lane == 0) {
+    for (int c = 0; c < 3; ++c) Fb[c] = group_total<WPA>(Fb[c], gsh);
+    eb = group_total<WPA>(eb, gsh);
+    ea = group_total<WPA>(ea, gsh);
+    if (sub != 0) eb = ea = 0.0; // the group's totals, counted once
+    if (vi && sub == 0) {
         double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE) + Fb[0],
                        V.Fd[3 * (A + i) + 1] + Pr::value(fy, kScaleE) + Fb[1],
                        V.Fd[3 * (A + i) + 2] + Pr::value(fz, kScaleE) + Fb[2]};
