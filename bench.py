@@ -144,16 +144,21 @@ def workload():
     return synth.config_c4()
 
 
-def gb_far_fraction(eng, systems, grid, samples=200000, seed=0):
+def gb_far_fraction(eng, systems, grid, samples=200000, seed=0, walkers=None):
     """Fraction of the workload's unordered pairs with D >= GB_FAR_D, from the
     engine's current positions and Born radii (one walker per system, random
-    pairs), weighted by each system's pair count over the grid."""
+    pairs), weighted by each system's pair count over the grid (or over the
+    given walkers, the ones this engine advances)."""
     rng = np.random.default_rng(seed)
     x_all, r_all = eng.positions(), eng.born_radii()
     sos = np.asarray(grid.system_of_slot)
+    if walkers is not None:
+        keep = np.zeros(len(sos), bool)
+        keep[np.asarray(walkers)] = True
+        sos = np.where(keep, sos, -1)
     num = den = 0.0
-    for s in np.unique(sos):
-        w = int(np.nonzero(sos == s)[0][0])  # the walker that starts in system s's first slot
+    for s in np.unique(sos[sos >= 0]):
+        w = int(np.nonzero(sos == s)[0][0])  # the first walker of system s
         sl = eng.walker_slice(w)
         x, R = x_all[sl], r_all[sl]
         n = len(R)
@@ -189,6 +194,8 @@ def aggregate_max(t_local, world, device=None):
         return t_local
     import torch
     import torch.distributed as dist
+    if dist.get_backend() == "gloo":
+        device = "cpu"
     tt = torch.tensor([t_local], dtype=torch.float64, device=device)
     dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     return float(tt.item())
@@ -450,7 +457,10 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl")
+        # NCCL between GPUs; CPH_BENCH_DIST_BACKEND=gloo runs the same sharded
+        # path with host collectives (several ranks may then share a device)
+        dist.init_process_group(os.environ.get("CPH_BENCH_DIST_BACKEND", "nccl"))
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     build.build()
     dev = torch.device("cuda", local)
@@ -536,7 +546,7 @@ def run_gpu(args):
     names = ["born", "gb", "chain"]
     dom = int(np.argmax(pass_ms))
     f_mhz = clocks["sm_mhz"] or 2070.0
-    gb_far = gb_far_fraction(eng, systems, grid)
+    gb_far = gb_far_fraction(eng, systems, grid, walkers=mine)
     peak = N_SM * f_mhz * 1e6 / pass_clk(names[dom], gb_far) / 1e9
     achieved = local_pairs / (pass_ms[dom] / 1e3) / 1e9
     step_peak = N_SM * f_mhz * 1e6 / sum(pass_clk(n, gb_far) for n in names) / 1e9
