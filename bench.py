@@ -402,6 +402,7 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
     # (graphs captured, caches warm)
     eng2 = cphremd.init_system(systems, grid, seed=7, precision=precision)
     chunk = eng2.autotune()
+    shapes = ["symmetric" if v == cphremd.SHAPE_SYMMETRIC else "warp per atom" for v in eng2.tile_shapes()]
     eng2.run(min(n_steps, 201))
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -414,7 +415,7 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
     eng2.status()
     out = {"workload": name, "replicas": W, "atoms": [s.n for s in systems],
            "precision": "FP64" if precision == cphremd.PREC_FP64 else "FP32 pair math, int64 fixed point",
-           "autotuned_chunk_jtiles": chunk,
+           "autotuned_chunk_jtiles": chunk, "tile_shapes": shapes,
            "steps": n_steps, "steps_timed_from": c0, "ms_per_step": ms / n_steps,
            "value": W * n_steps / (ms / 1e3), "unit": "replica-steps/s",
            "pair_evals_per_s": pairs_step * n_steps / (ms / 1e3),
@@ -492,7 +493,8 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    chunk = eng.autotune()  # tile shape for this workload (outside the timed region)
+    chunk = eng.autotune()  # tile shapes for this workload (outside the timed region)
+    shapes = ["symmetric" if v == cphremd.SHAPE_SYMMETRIC else "warp per atom" for v in eng.tile_shapes()]
     first = window_start(args.steps, args.warmup)
     events = schedule_events(first, args.steps)
     advance(1)  # step 0
@@ -642,7 +644,7 @@ def run_gpu(args):
                    "precision": "FP32 pair math, int64 fixed-point accumulation",
                    "schedule": "MC (pH then redox) every 10 steps, exchange every 100 (E,pH,T)",
                    "l2": "256 MB buffer written before every timed step",
-                   "autotuned_chunk_jtiles": chunk,
+                   "autotuned_chunk_jtiles": chunk, "autotuned_tile_shapes": shapes,
                    "parallelism": ("replicas batched per launch" if not sharded else
                                    f"one grid sharded by walker over {world} GPUs (rank 0: {len(mine)} "
                                    "walkers); exchange rows all-gathered over NCCL at exchange steps")},

@@ -446,15 +446,21 @@ def test_cutoff_beyond_every_pair_changes_nothing(ragged_systems):
     assert (R8 <= R0 * (1 + 1e-6)).all() and (R8 < R0 * (1 - 1e-4)).mean() > 0.5
 
 
-@pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
-                                           (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11)])
+@pytest.mark.parametrize("prec,tf,te,tr,warp", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, False),
+                                                (cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, True),
+                                                (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11, False)])
 @pytest.mark.parametrize("v", GB_VARIANTS)
-def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr):
+def test_gb_variants_match_oracle(ragged_systems, v, prec, tf, te, tr, warp):
+    """Every GB variant on both FP32 tile shapes (warp: every system on one
+    warp per atom) and in FP64 mode."""
     grid = _grid_for(ragged_systems)
     gb = cphremd.GBParams(v["eps_in"], v["eps_out"], v["offset"], v["alpha"], v["beta"], v["gamma"],
                           v["kappa"], v.get("sa_gamma", 0.0), v.get("sa_probe", 1.4),
                           v.get("rgbmax", 0.0))
     eng = cphremd.init_system(ragged_systems, grid, seed=3, precision=prec, gb=gb)
+    if warp:
+        for k in range(len(ragged_systems)):
+            eng.set_tile_shape(k, cphremd.SHAPE_WARP_PER_ATOM)
     eng.evaluate()
     og = oracle.GBParams(**v)
     for w in range(grid.n_slots):

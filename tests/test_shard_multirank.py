@@ -1,7 +1,7 @@
 """One replica grid sharded over ranks: the host-side driver
-(paper_1809_07726_gb300/shard.py) run by two gloo ranks on CPU, with the FP64
+(paper_1809_07726_gb300/shard.py) run by two and by three gloo ranks on CPU, with the FP64
 oracle standing in for each rank's engine (an adapter with the engine's
-methods, advancing only the rank's walkers).  The two-rank run must give the
+methods, advancing only the rank's walkers).  Each sharded run must give the
 same condition map, site states, positions and velocities, bit for bit, as
 the one-rank run of the same driver and as the oracle's own schedule (which
 attempts its exchanges inside the step, every walker in one process)."""
@@ -147,8 +147,8 @@ def test_partition_balances_pair_work():
     assert shard.partition(sizes, sos, 2) == shard.partition(sizes, sos, 2)  # deterministic
 
 
-def test_two_gloo_ranks_match_one_rank_and_the_oracle_schedule():
-    world = 2
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_match_one_rank_and_the_oracle_schedule(world):
     port = _free_port()
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
