@@ -84,16 +84,71 @@ def pairs_per_clk_per_sm(fp32, mufu):
     return 1.0 / clk_per_pair_per_sm(fp32, mufu)
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, and the
+    clocks-event reasons bit mask) for one device, found by PCI bus id when
+    torch reports it, else by index.  Unavailable -> ok is False."""
+    SM = 1  # NVML_CLOCK_SM
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, pci, idx):
+        import ctypes
+        self.c = ctypes
+        self.ok = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            rc = lib.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(h)) if pci else 1
+            if rc != 0 and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) != 0:
+                return
+            try:
+                self.reasons_fn = lib.nvmlDeviceGetCurrentClocksEventReasons
+            except AttributeError:
+                self.reasons_fn = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.lib, self.h, self.ok = lib, h, True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def max_sm(self):
+        v = self.c.c_uint()
+        return float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, self.c.byref(v)) == 0 else None
+
+    def sample(self):
+        v, r = self.c.c_uint(), self.c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.c.byref(v)) != 0:
+            return None
+        bits = r.value if self.reasons_fn(self.h, self.c.byref(r)) == 0 else 0
+        return float(v.value), {nm for b, nm in self.BITS.items() if bits & b}
+
+
+def _pci_bus_id(dev):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:  # older torch without the PCI fields, or no GPU
+        return None
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """Clocks and throttle reasons sampled during the timed region: nvidia-smi
+    every 100 ms (the recipe's query) and NVML every 10 ms in a thread, so a
+    window of a few hundred ms still holds tens of samples.  The median SM
+    clock is taken over the NVML samples when there are any."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NVML_PERIOD_S = 0.010
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
+        self.pci = _pci_bus_id(gpu_index)
         self.proc = None
         self.lines = []
+        self.nv_sm, self.nv_reasons, self.nv_max = [], set(), None
+        self.stop = threading.Event()
 
     def __enter__(self):
         try:
@@ -104,13 +159,28 @@ class ClockSampler:
             self.t.start()
         except OSError:
             self.proc = None
+        self.nvml = _Nvml(self.pci, self.idx)
+        if self.nvml.ok:
+            self.nv_max = self.nvml.max_sm()
+            self.tn = threading.Thread(target=self._poll, daemon=True)
+            self.tn.start()
         return self
 
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    def _poll(self):
+        while not self.stop.wait(self.NVML_PERIOD_S):
+            s = self.nvml.sample()
+            if s:
+                self.nv_sm.append(s[0])
+                self.nv_reasons |= s[1]
+
     def __exit__(self, *a):
+        self.stop.set()
+        if self.nvml.ok:
+            self.tn.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -119,7 +189,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons = [], None, set(self.nv_reasons)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -133,10 +203,13 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        if not sm:
+        src = self.nv_sm or sm
+        if not src:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(src), "sm_max_mhz": mx or self.nv_max, "reasons": sorted(reasons),
+                "samples": len(src), "sampler": "nvml 10 ms" if self.nv_sm else "nvidia-smi 100 ms",
+                "nvidia_smi_samples": len(sm),
+                "nvidia_smi_sm_mhz": statistics.median(sm) if sm else None}
 
 
 def workload():
