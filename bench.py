@@ -281,12 +281,15 @@ def whole_job_value(grid_walkers, steps, t_max):
 
 
 def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
-    # batched FP32 step: Born-radii pair kernel + finish, GB pair kernel + finish,
-    # chain pair kernel + bonded terms + force finish, observables, Langevin,
-    # and the step-counter tick of a one-step cph_run
-    n = 2 + 2 + 3 + 1 + 1 + 1
+    """Kernels one batched FP32 step t launches through a one-step cph_run:
+    position staging + Born-radii pair kernel + finish, GB staging + pair
+    kernel + finish, chain pair kernel + bonded terms + force finish,
+    observables, Langevin, the step-counter tick; each MC sweep kind adds its
+    per-site and per-walker kernels, an exchange step its row and attempt
+    kernels."""
+    n = 3 + 3 + 3 + 1 + 1 + 1
     if t > 0:
-        n += int(t % mc_ph == 0) + int(t % mc_redox == 0) + int(t % ex_every == 0)
+        n += 2 * (int(t % mc_ph == 0) + int(t % mc_redox == 0)) + 2 * int(t % ex_every == 0)
     return n
 
 

@@ -43,3 +43,13 @@ def test_timed_window_holds_the_schedule_events(steps, warmup):
     assert abs(ev["mc_ph_steps"] - steps / 10) <= 1
     if steps % 100 == 0:
         assert ev["exchange_steps"] == steps // 100 and ev["mc_ph_steps"] == steps // 10
+
+
+def test_schedule_launches_counts_the_launch_list():
+    """The kernels of one step as the launch list of the 384-walker workload
+    shows them: 12 per plain step; +4 at an MC step with both kinds; +2 more
+    at an exchange step."""
+    assert bench.schedule_launches(91) == 12
+    assert bench.schedule_launches(110) == 16
+    assert bench.schedule_launches(100) == 18
+    assert sum(bench.schedule_launches(t) for t in range(91, 111)) == 20 * 12 + 8 + 2
