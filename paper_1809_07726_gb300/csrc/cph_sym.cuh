@@ -45,6 +45,17 @@ struct SymItem {
     int w, i0, jt0, jt1, st, pad;
 };
 
+// Tile pairs of the staged group at g0 (npair of them) that a warp passes by:
+// the first pairs whose two j-tiles hold only partners j <= i of the warp's
+// 64 i atoms (an i-tile starts at a multiple of kSymI atoms), or all of them
+// when the warp has no atom.  Every pair there is skipped, so their partials
+// are exact zeros and the warp starts at the returned pair.
+__device__ __forceinline__ int first_live_pair(int i0, int warp, int N, int g0, int npair) {
+    if (i0 + warp * 64 >= N) return npair;
+    const int d = i0 / kSymJ + 2 * warp - g0; // tiles below g0 + d are passed by
+    return d <= 0 ? 0 : min(npair, d >> 1);
+}
+
 // Non-finite partials would saturate in the float -> int64 conversion and
 // vanish into a finite-looking sum, so they are flagged before converting.
 __device__ __forceinline__ void red_add(long long* p, float v, int* status) {
@@ -1012,7 +1023,16 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_born_sym(const SymItem* __re
             }
         }
         __syncthreads();
-        for (int pr = 0; pr < npair; ++pr) {
+        const int pr0 = first_live_pair(it.i0, warp, N, g0, npair);
+        for (int pr = 0; pr < pr0; ++pr) {
+            red[2 * pr][warp][lane] = 0.f;
+            red[2 * pr + 1][warp][lane] = 0.f;
+        }
+        while (next < min(g0 + 2 * pr0, it.jt1)) { // masked tiles passed by
+            ++mp;
+            next = mp < me ? V.smt_list[mp] : 0x7fffffff;
+        }
+        for (int pr = pr0; pr < npair; ++pr) {
             const int jtA = g0 + 2 * pr;
             float2 jh = make_float2(0.f, 0.f);
             float2 ah[2] = {{0.f, 0.f}, {0.f, 0.f}};
