@@ -456,8 +456,8 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
     """One of the smaller workloads through the public API: device time of
     n_steps of cph_run (CUDA events) after a few warm-up steps, and end to end
     from host buffers (init_system uploads the systems, run, then the final
-    positions and energies are read back) in wall time.  oracle_plan =
-    (walkers, steps, threads) times the FP64 oracle on that sample."""
+    positions and energies are read back) in wall time.  oracle_plan = a list
+    of (walkers, steps, threads) samples of the FP64 oracle to time."""
     import torch
 
     from paper_1809_07726_gb300 import cphremd
@@ -515,12 +515,18 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
                                    "of a few microseconds each"}
     del eng, eng2
     if oracle_plan is not None:
-        ws, n, threads = oracle_plan
-        secs, pairs = oracle_sample(systems, grid, ws, n, seed=7, threads=threads, t0=1)
-        out["cpu_baseline"] = {"value": len(ws) * n / secs, "unit": "replica-steps/s", "cores": threads,
-                               "kind": "oracle", "seconds": secs,
-                               "sample": f"{n} schedule steps (from step 1, MC every 10) of "
-                                         f"{len(ws)} walker(s) on {threads} thread(s); measured"}
+        # plans: (walkers, steps, threads); the first is the leg's cpu_baseline,
+        # the others are the same workload at another core count
+        runs = []
+        for ws, n, threads in oracle_plan:
+            secs, pairs = oracle_sample(systems, grid, ws, n, seed=7, threads=threads, t0=1)
+            runs.append({"value": len(ws) * n / secs, "unit": "replica-steps/s", "cores": threads,
+                         "kind": "oracle", "seconds": secs,
+                         "sample": f"{n} schedule steps (from step 1, MC every 10) of "
+                                   f"{len(ws)} walker(s) on {threads} thread(s); measured"})
+        out["cpu_baseline"] = runs[0]
+        if len(runs) > 1:
+            out["cpu_baseline"]["other_core_counts"] = runs[1:]
     return out
 
 
@@ -679,15 +685,20 @@ def run_gpu(args):
     legs = {}
     if not args.no_legs:
         on_cpu = world == 1 and rank == 0
+        # oracle samples: C1 whole (one walker: the oracle spreads walkers, not
+        # atoms, over threads, so one core is all it uses); C2 on one core and
+        # on one thread per walker; C3 on every core and one walker on one core
         legs["c1"] = config_leg("C(pH,E)MD, 1 replica of 160 atoms, FP64, 1000 steps", synth.config_c1,
                                 cphremd.PREC_FP64, 1000, dev, stream, clocks["sm_mhz"],
-                                ([0], 1000, 1) if on_cpu else None)
+                                [([0], 1000, 1)] if on_cpu else None)
         legs["c2"] = config_leg("1D E-REMD, 8 replicas of 160 atoms, FP32, 20000 steps", synth.config_c2,
                                 cphremd.PREC_FP32, 20000, dev, stream, clocks["sm_mhz"],
-                                (list(range(8)), 200, 1) if on_cpu else None)
+                                [(list(range(8)), 200, 1), (list(range(8)), 200, min(8, ncores))]
+                                if on_cpu else None)
         legs["c3"] = config_leg("2D E,pH-REMD, 64 replicas of 2400 atoms, FP32, 2000 steps", synth.config_c3,
                                 cphremd.PREC_FP32, 2000, dev, stream, clocks["sm_mhz"],
-                                (list(range(min(ncores, 64))), 10, ncores) if on_cpu else None)
+                                [(list(range(min(ncores, 64))), 10, ncores), ([0], 2, 1)]
+                                if on_cpu else None)
 
     if rank != 0:
         if world > 1:
