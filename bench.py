@@ -520,10 +520,11 @@ def config_leg(name, cfg, precision, n_steps, dev, stream, sm_mhz, oracle_plan=N
         runs = []
         for ws, n, threads in oracle_plan:
             secs, pairs = oracle_sample(systems, grid, ws, n, seed=7, threads=threads, t0=1)
+            ev = schedule_events(1, n)
             runs.append({"value": len(ws) * n / secs, "unit": "replica-steps/s", "cores": threads,
                          "kind": "oracle", "seconds": secs,
-                         "sample": f"{n} schedule steps (from step 1, MC every 10) of "
-                                   f"{len(ws)} walker(s) on {threads} thread(s); measured"})
+                         "sample": f"{n} schedule steps (steps 1-{n}, {ev['mc_ph_steps']} of them with MC "
+                                   f"sweeps) of {len(ws)} walker(s) on {threads} thread(s); measured"})
         out["cpu_baseline"] = runs[0]
         if len(runs) > 1:
             out["cpu_baseline"]["other_core_counts"] = runs[1:]
