@@ -1593,6 +1593,10 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.sa_probe = p->gb.sa_probe;
     V.rgbmax = p->gb.rgbmax > 0 ? p->gb.rgbmax : INFINITY;
     V.inv_eps_in = 1.0 / p->gb.eps_in;
+    V.tau32 = (float)V.tau;
+    V.iei32 = (float)V.inv_eps_in;
+    V.ieo32 = (float)V.inv_eps_out;
+    V.kappa32 = (float)V.kappa;
     V.sqrt_k = std::sqrt(kCoulomb);
     V.alpha = p->gb.alpha;
     V.beta = p->gb.beta;

@@ -116,6 +116,13 @@ int setup(SView& g, int n_rep, int n, const float* x, const float* q, const floa
     g.sa_gamma = gb->sa_gamma;
     g.sa_probe = gb->sa_probe;
     g.rgbmax = gb->rgbmax > 0 ? gb->rgbmax : INFINITY;
+    g.tau32 = (float)g.tau;
+    g.sqk32 = (float)g.sqrt_k;
+    g.iei32 = (float)g.inv_eps_in;
+    g.ieo32 = (float)g.inv_eps_out;
+    g.kap32 = (float)g.kappa;
+    g.off32 = (float)g.offset;
+    g.rgbmax32 = (float)g.rgbmax;
     ws_carve_sym(g, ws);
     return CPH_OK;
 }

@@ -39,6 +39,10 @@ struct SView {
     // the factor the finishing kernels apply to the pair sums (tau without
     // salt; 1 with salt, whose pair terms carry tau(f) per pair)
     double kappa, inv_eps_in, inv_eps_out, tau_pair;
+    // FP32 copies for the pair kernels, rounded once on the host (a reload
+    // under register pressure then reads a parameter instead of converting
+    // the double again on the narrow FP64 pipe)
+    float tau32, sqk32, iei32, ieo32, kap32, off32, rgbmax32;
     double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
     double rgbmax;             // Born-radius cutoff, INFINITY = none
     // per replica-atom (index r * n + a); int64 slots alias double slots that
@@ -56,7 +60,7 @@ struct SView {
 __global__ void k_gbound(SView g) {
     const size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= (size_t)g.n_rep * g.n) return;
-    const float rt = g.rho[a] - (float)g.offset;
+    const float rt = g.rho[a] - g.off32;
     const float s = g.screen[a % g.n] * rt;
     // positive floats order like their bit patterns
     atomicMax(&g.bound[0], __float_as_uint(fmaxf(s, 0.f)));
@@ -66,7 +70,7 @@ __global__ void k_gbound(SView g) {
 __device__ __forceinline__ PairBand gband(const SView& g) {
     const float smax = __uint_as_float(g.bound[0]), rtmax = __uint_as_float(g.bound[1]);
     const float rf = fmaxf(smax / kHctXmax, smax + rtmax) * 1.0001f;
-    return pair_band(rf * rf, smax, (float)g.rgbmax);
+    return pair_band(rf * rf, smax, g.rgbmax32);
 }
 
 struct GItem {
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float off = (float)g.offset;
+    const float off = g.off32;
     const PairBand band = gband(g);
     int ii[2];
     bool vi[2];
@@ -353,8 +357,7 @@ __global__ void __launch_bounds__(kGT, 5) k_gpair_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* Q = g.q + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float sqk = (float)g.sqrt_k, tau = (float)g.tau, iei = (float)g.inv_eps_in, ieo = (float)g.inv_eps_out,
-                kap = (float)g.kappa;
+    const float sqk = g.sqk32, tau = g.tau32, iei = g.iei32, ieo = g.ieo32, kap = g.kap32;
     int ii[2];
     bool vi[2];
     GpI2 I[2];
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(kGT, 4) k_gchain_sym(SView g) {
     const float* X = g.x + (size_t)it.rep * n * 3;
     const float* RH = g.rho + (size_t)it.rep * n;
     const size_t base = (size_t)it.rep * n;
-    const float off = (float)g.offset;
+    const float off = g.off32;
     const PairBand band = gband(g);
     int ii[2];
     bool vi[2];

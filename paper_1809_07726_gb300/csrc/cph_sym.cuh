@@ -322,8 +322,7 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_gb_sym(const SymItem* __rest
     const SymItem it = items[blockIdx.x];
     const int w = it.w, s = V.w_sys[w], N = V.sys_n[s], A = V.w_off[w], P = V.sys_poff[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float tau = (float)V.tau, iei = (float)V.inv_eps_in, kappa = (float)V.kappa,
-                ieo = (float)V.inv_eps_out;
+    const float tau = V.tau32, iei = V.iei32, kappa = V.kappa32, ieo = V.ieo32;
     int ii[2];
     bool vi[2];
     GbI2 I[2];
