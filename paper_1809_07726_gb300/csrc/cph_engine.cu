@@ -54,6 +54,12 @@ __device__ __forceinline__ Real mc_pair(Real dx, Real dy, Real dz, Real Rm, Real
     return (excluded ? Real(0) : iei * rinv) - tf * fi;
 }
 
+template <class Real>
+__device__ __forceinline__ Real mc_const(double d, float f) {
+    if constexpr (sizeof(Real) == 4) return f;
+    else return d;
+}
+
 __device__ inline bool mc_excluded(const View& V, int P, int at, int an) {
     for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e)
         if (V.excl_j[e] == an) return true;
@@ -80,8 +86,10 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_site(View V, int kind, int s_
     __shared__ long long redl[kMcThreads / 32];
     __shared__ double redd[kMcThreads / 32];
     const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
-    const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
-    const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
+    // FP32: the host-rounded copies (no double -> float conversion in the loops)
+    const Real sqk = mc_const<Real>(V.sqrt_k, V.sqk32), tau = mc_const<Real>(V.tau, V.tau32),
+               iei = mc_const<Real>(V.inv_eps_in, V.iei32);
+    const Real kap = mc_const<Real>(V.kappa, V.kappa32), ieo = mc_const<Real>(V.inv_eps_out, V.ieo32);
     const bool salt = V.kappa > 0;
     const int nat = V.site_nat[g], nst = V.site_nst[g], ao = V.site_aoff[g], qo = V.site_qoff[g];
     if (tid == 0) {
@@ -204,8 +212,10 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_sweep(View V, int kind, int c
     __shared__ long long redl[kMcThreads / 32];
     __shared__ double redd[kMcThreads / 32];
     const double cx = V.x[3 * A], cy = V.x[3 * A + 1], cz = V.x[3 * A + 2];
-    const Real sqk = Real(V.sqrt_k), tau = Real(V.tau), iei = Real(V.inv_eps_in);
-    const Real kap = Real(V.kappa), ieo = Real(V.inv_eps_out);
+    // FP32: the host-rounded copies (no double -> float conversion in the loops)
+    const Real sqk = mc_const<Real>(V.sqrt_k, V.sqk32), tau = mc_const<Real>(V.tau, V.tau32),
+               iei = mc_const<Real>(V.inv_eps_in, V.iei32);
+    const Real kap = mc_const<Real>(V.kappa, V.kappa32), ieo = mc_const<Real>(V.inv_eps_out, V.ieo32);
     const bool salt = V.kappa > 0;
     int n_taken = 0; // sites of this sweep accepted so far (uniform across the CTA)
     for (int k = 0; k < ns; ++k) {
@@ -1597,6 +1607,7 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     V.iei32 = (float)V.inv_eps_in;
     V.ieo32 = (float)V.inv_eps_out;
     V.kappa32 = (float)V.kappa;
+    V.sqk32 = (float)std::sqrt(kCoulomb);
     V.sqrt_k = std::sqrt(kCoulomb);
     V.alpha = p->gb.alpha;
     V.beta = p->gb.beta;

@@ -89,11 +89,11 @@ struct View {
     // kernels apply to pair sums (tau without salt; 1 with salt, whose pair
     // kernels carry tau(f) per pair)
     double kappa, inv_eps_out, tau_pair;
-    // the FP32 GB kernel's copies of tau, 1/eps_in, 1/eps_out and kappa,
-    // rounded once on the host: a kernel that reloads one of them under
-    // register pressure then reads a parameter instead of converting the
+    // the FP32 GB and MC kernels' copies of tau, 1/eps_in, 1/eps_out, kappa and
+    // sqrt(k), rounded once on the host: a kernel that reloads one of them
+    // under register pressure then reads a parameter instead of converting the
     // double again (a conversion issues to the narrow FP64 pipe)
-    float tau32, iei32, ieo32, kappa32;
+    float tau32, iei32, ieo32, kappa32, sqk32;
     double sa_gamma, sa_probe; // nonpolar surface term (ACE), 0 = off
     // SHAKE: clusters (one heavy atom and its hydrogens) per system, work
     // items (walker, cluster), positions before the Langevin step
