@@ -90,10 +90,14 @@ __host__ __device__ inline double unit_open(uint32_t u) {
 // tau(f) = 1/eps_in - exp(-kappa f)/eps_out; d(tau(f)/f)/df = -taud(f)/f^2 with
 // taud(f) = tau(f) - kappa f exp(-kappa f)/eps_out.  kappa = 0: both are the
 // constant 1/eps_in - 1/eps_out.
+// Without salt both are iei - ieo exactly (exp(-0) = 1): the FP64 exponential,
+// slow on GB300's narrow FP64 pipe, is skipped.
 __host__ __device__ inline double salt_tau(double f, double iei, double ieo, double kappa) {
+    if (!(kappa > 0)) return iei - ieo;
     return iei - exp(-kappa * f) * ieo;
 }
 __host__ __device__ inline double salt_taud(double f, double iei, double ieo, double kappa) {
+    if (!(kappa > 0)) return iei - ieo;
     const double es = exp(-kappa * f) * ieo;
     return iei - es - kappa * f * es;
 }

@@ -478,7 +478,7 @@ __global__ void k_fin_c(View V, int a0, int n) {
     const double esa = sa_ace(V.sa_gamma, V.sa_probe, V.rho[P], R);
     const double dEdR = 0.5 * (V.tau_pair * ((double)V.dRfix[a] / kScaleE)
                                + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R))
-                      - 6.0 * esa / R;
+                      - (V.sa_gamma != 0.0 ? 6.0 * esa / R : 0.0); // no FP64 division without the term
     const double c = dEdR * V.dRdpsi[a] * 0.5 * V.rt[P];
     V.c[a] = c;
     V.c32[a] = (float)c;
