@@ -115,11 +115,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_site(View V, int kind, int s_
     }
     __syncthreads();
     Acc lin = 0;
-    for (int j = tid; j < N; j += kMcThreads) {
-        const Real xj = Real(V.x[3 * (A + j)] - cx), yj = Real(V.x[3 * (A + j) + 1] - cy),
-                   zj = Real(V.x[3 * (A + j) + 2] - cz);
-        const Real qj = Real(V.q[A + j]) * sqk;
-        const Real Rj = Real(V.R[A + j]);
+    auto linear_j = [&](int j, Real xj, Real yj, Real zj, Real qj, Real Rj) {
         Real part = 0;
         for (int m = 0; m < nat; ++m) {
             if (mat[m] == j) {
@@ -131,40 +127,97 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_site(View V, int kind, int s_
             }
         }
         Pr::add(lin, part, Real(kScaleE));
+    };
+    if (sizeof(Real) == 4 && !V.sys_ordered[s]) {
+        // FP32 on the symmetric tiles: the partners from the step's staged FP32
+        // operands (positions relative to the walker's first atom from the
+        // Born-radii pass; sqrt(k) q and R staged again just before this
+        // sweep), with no FP64 subtraction or conversion per partner (both
+        // issue to the narrow FP64 pipe)
+        for (int j = tid; j < N; j += kMcThreads) {
+            const float4 p = V.xs[A + j], gj = V.gq[A + j];
+            linear_j(j, Real(p.x), Real(p.y), Real(p.z), Real(gj.x), Real(gj.y));
+        }
+    } else {
+        for (int j = tid; j < N; j += kMcThreads)
+            linear_j(j, Real(V.x[3 * (A + j)] - cx), Real(V.x[3 * (A + j) + 1] - cy),
+                     Real(V.x[3 * (A + j) + 2] - cz), Real(V.q[A + j]) * sqk, Real(V.R[A + j]));
     }
-    // FP64: the Coulomb part of excluded pairs (index nat * nat + m) and the
-    // quadratic term's pairs (index m * nat + n)
+    // The Coulomb part of excluded pairs (index nat * nat + m) and the
+    // quadratic term's pairs (index m * nat + n): in the pass's precision from
+    // the site atoms' staged values (FP32: no FP64 arithmetic per pair on the
+    // narrow FP64 pipe; the FP32 terms are at the linear term's accuracy), the
+    // FP64 mode in FP64 from the master positions.
     double corr = 0.0;
-    for (int idx = tid; idx < nat * nat + nat; idx += kMcThreads) {
-        if (idx >= nat * nat) {
-            const int m = idx - nat * nat, at = mat[m];
-            const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
-            const double xm0 = V.x[3 * (A + at)], xm1 = V.x[3 * (A + at) + 1], xm2 = V.x[3 * (A + at) + 2];
-            for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e) {
-                const int j = V.excl_j[e];
-                const double d0 = xm0 - V.x[3 * (A + j)], d1 = xm1 - V.x[3 * (A + j) + 1],
-                             d2 = xm2 - V.x[3 * (A + j) + 2];
-                const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                corr -= dqm * V.q[A + j] * kCoulomb * V.inv_eps_in / r;
+    if (sizeof(Real) == 4) {
+        const bool staged = !V.sys_ordered[s];
+        for (int idx = tid; idx < nat * nat + nat; idx += kMcThreads) {
+            Real term = 0;
+            if (idx >= nat * nat) {
+                const int m = idx - nat * nat, at = mat[m];
+                for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e) {
+                    const int j = V.excl_j[e];
+                    Real xj, yj, zj, qj;
+                    if (staged) {
+                        const float4 p = V.xs[A + j];
+                        xj = Real(p.x);
+                        yj = Real(p.y);
+                        zj = Real(p.z);
+                        qj = Real(V.gq[A + j].x);
+                    } else {
+                        xj = Real(V.x[3 * (A + j)] - cx);
+                        yj = Real(V.x[3 * (A + j) + 1] - cy);
+                        zj = Real(V.x[3 * (A + j) + 2] - cz);
+                        qj = Real(V.q[A + j]) * sqk;
+                    }
+                    const Real d0 = mx[m] - xj, d1 = my[m] - yj, d2 = mz[m] - zj;
+                    term -= mdq[m] * qj * iei * Pr::rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                }
+            } else {
+                const int m = idx / nat, n = idx % nat;
+                if (n == m) {
+                    const Real ts = salt ? iei - ieo * Pr::expm(kap * mR[m]) : tau;
+                    term = Real(0.5) * mdq[m] * mdq[m] * (-ts / mR[m]);
+                } else {
+                    term = Real(0.5) * mdq[m] * mdq[n] *
+                           mc_pair<Real>(mx[m] - mx[n], my[m] - my[n], mz[m] - mz[n], mR[m], mR[n],
+                                         mc_excluded(V, P, mat[m], mat[n]), iei, tau, kap, ieo, salt);
+                }
             }
-            continue;
+            corr += (double)term;
         }
-        const int m = idx / nat, n = idx % nat, at = mat[m], an = mat[n];
-        const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
-        const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
-        const double Rm = V.R[A + at];
-        if (n == m) {
-            corr += 0.5 * dqm * dqn * (-salt_tau(Rm, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / Rm);
-            continue;
+    } else {
+        for (int idx = tid; idx < nat * nat + nat; idx += kMcThreads) {
+            if (idx >= nat * nat) {
+                const int m = idx - nat * nat, at = mat[m];
+                const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
+                const double xm0 = V.x[3 * (A + at)], xm1 = V.x[3 * (A + at) + 1], xm2 = V.x[3 * (A + at) + 2];
+                for (int e = V.excl_off[P + at]; e < V.excl_off[P + at + 1]; ++e) {
+                    const int j = V.excl_j[e];
+                    const double d0 = xm0 - V.x[3 * (A + j)], d1 = xm1 - V.x[3 * (A + j) + 1],
+                                 d2 = xm2 - V.x[3 * (A + j) + 2];
+                    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    corr -= dqm * V.q[A + j] * kCoulomb * V.inv_eps_in / r;
+                }
+                continue;
+            }
+            const int m = idx / nat, n = idx % nat, at = mat[m], an = mat[n];
+            const double dqm = (V.site_q[qo + b * nat + m] - V.q[A + at]);
+            const double dqn = (V.site_q[qo + b * nat + n] - V.q[A + an]);
+            const double Rm = V.R[A + at];
+            if (n == m) {
+                corr += 0.5 * dqm * dqn * (-salt_tau(Rm, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / Rm);
+                continue;
+            }
+            const double d0 = V.x[3 * (A + at)] - V.x[3 * (A + an)], d1 = V.x[3 * (A + at) + 1] - V.x[3 * (A + an) + 1],
+                         d2 = V.x[3 * (A + at) + 2] - V.x[3 * (A + an) + 2];
+            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const double RR = Rm * V.R[A + an];
+            const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
+            double amn = -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / f;
+            if (!mc_excluded(V, P, at, an)) amn += kCoulomb * V.inv_eps_in / sqrt(r2);
+            corr += 0.5 * dqm * dqn * amn;
         }
-        const double d0 = V.x[3 * (A + at)] - V.x[3 * (A + an)], d1 = V.x[3 * (A + at) + 1] - V.x[3 * (A + an) + 1],
-                     d2 = V.x[3 * (A + at) + 2] - V.x[3 * (A + an) + 2];
-        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-        const double RR = Rm * V.R[A + an];
-        const double f = sqrt(r2 + RR * exp(-0.25 * r2 / RR));
-        double amn = -salt_tau(f, V.inv_eps_in, V.inv_eps_out, V.kappa) * kCoulomb / f;
-        if (!mc_excluded(V, P, at, an)) amn += kCoulomb * V.inv_eps_in / sqrt(r2);
-        corr += 0.5 * dqm * dqn * amn;
     }
     // block reduction (fixed order)
     long long lv = 0;
@@ -783,6 +836,8 @@ cudaStream_t lane_stream(const cph_engine* E, int w, cudaStream_t st) {
     return E->n_rs > 1 ? E->rs[w % E->n_rs] : st;
 }
 
+int launch_stage(cph_engine* E, int pass, int a0, int n, cudaStream_t st);
+
 int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
     const int W = E->V.W;
     int first = 1;
@@ -791,7 +846,10 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
         if (!(kinds & bit)) continue;
         if (E->max_sites <= 0) break;
         const bool f32 = E->precision == CPH_PREC_FP32;
+        // the per-site kernel reads sqrt(k) q and R from the FP32 staging of the
+        // symmetric tiles: stage them at this sweep's charges
         if (E->launch_mode == 0) {
+            if (f32 && E->n_sym > 0) TRY(launch_stage(E, 1, 0, E->V.total_atoms, st));
             const dim3 g1(E->max_sites, W);
             if (f32) k_mc_site<float><<<g1, kMcThreads, 0, st>>>(E->V, kind, s_off, 0);
             else k_mc_site<double><<<g1, kMcThreads, 0, st>>>(E->V, kind, s_off, 0);
@@ -802,6 +860,8 @@ int launch_mc(cph_engine* E, int kinds, int s_off, cudaStream_t st) {
             for (int w = 0; w < W; ++w) {
                 if (!E->h_w_local[w]) continue;
                 cudaStream_t s = lane_stream(E, w, st);
+                if (f32 && !sys_ordered(E, E->h_w_sys[w]))
+                    TRY(launch_stage(E, 1, E->h_w_off[w], E->h_w_off[w + 1] - E->h_w_off[w], s));
                 if (f32) k_mc_site<float><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
                 else k_mc_site<double><<<E->max_sites, kMcThreads, 0, s>>>(E->V, kind, s_off, w);
                 if (f32) k_mc_sweep<float><<<1, kMcThreads, 0, s>>>(E->V, kind, first, w);
