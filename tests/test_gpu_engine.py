@@ -172,11 +172,24 @@ def test_mc_sweep_matches_oracle(prec, kappa, rgbmax):
     dU against the oracle's full recomputation, identical decisions; without
     salt, with Debye-Hueckel screening (kappa = 0.1 / A), and with a 10 A
     Born-radius cutoff (which the sites' reference compounds see too)."""
+    _mc_sweep_vs_oracle(prec, kappa, rgbmax)
+
+
+def test_mc_sweep_on_the_warp_per_atom_shape_matches_oracle():
+    """The same in FP32 with the system on one warp per atom: the per-site
+    kernel then reads its partners from the FP64 master arrays instead of the
+    symmetric tiles' FP32 staging."""
+    _mc_sweep_vs_oracle(cphremd.PREC_FP32, 0.0, 0.0, warp=True)
+
+
+def _mc_sweep_vs_oracle(prec, kappa, rgbmax, warp=False):
     systems, grid = synth.config_c3()
     grid = synth.Grid(grid.E[[0, 3, 5, 7]], grid.pH[[0, 4]], grid.T, np.zeros(8, np.int32),
                       order=("E", "pH"))
     gb = cphremd.GBParams(1.0, 78.5, 0.09, 0.8, 0.0, 2.909125, kappa, 0.0, 1.4, rgbmax)
     eng = cphremd.init_system(systems, grid, seed=11, precision=prec, gb=gb)
+    if warp:
+        eng.set_tile_shape(0, cphremd.SHAPE_WARP_PER_ATOM)
     eng.set_step(10)
     eng.mc_titrate(cphremd.MC_BOTH)
     recs = eng.mc_records()
