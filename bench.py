@@ -47,24 +47,24 @@ WORKLOAD = "3D E,T,pH-REMD: 8 E x 6 T x 8 pH = 384 replicas over 500/2000/8000-a
 # Algorithmic cost of one unordered pair in each pass, counted from the forms
 # the method evaluates for a far pair (r >= r_far: the HCT series; over 99 % of
 # the pairs here): FP32 lane operations (an FMA counts once) and MUFU
-# operations (rsqrt, ex2).  born: distance 6, powers of 1/r 2, two series
-# terms (y, P, s^3) 14, r^-4-weighted fused sums 2; gb: distance 6, GB kernel and dE/dR 18, LJ 9, Coulomb 2,
+# operations (rsqrt, rcp, ex2).  born: distance 6, 1/r^4 from 1/r^2 (one rcp) 1,
+# two series terms (y, P, s^3) 14, r^-4-weighted fused sums 2; gb: distance 6, GB kernel and dE/dR 18, LJ 9, Coulomb 2,
 # force and partner force 6 (minus fused products), 3 MUFU; chain: distance 6,
-# powers 3, two dH/dr series 12, weights 5, forces 6.
-PASS_COST = {"born": (24, 1), "gb": (40, 3), "chain": (32, 1)}
+# powers 2 (1/r^2 from one rcp), two dH/dr series 12, weights 5, forces 6.
+PASS_COST = {"born": (23, 1), "gb": (40, 3), "chain": (31, 1)}
 # A GB pair with D = r^2 / (4 R_i R_j) >= 18 needs no exponential and no second
 # square root (1/f = 1/r and e^-D to FP32 precision): distance 6, D 2, LJ 9,
 # charges and eps 2, combined GB + Coulomb force factor ((q_i q_j / r) / eps_out
 # + LJ) / r^2 2, forces 6, 1 MUFU.
 GB_FAR_COST = (27, 1)
 GB_FAR_D = 18.0
-# GB-energy backward (Born radii recomputed): born 24/1 + GB adjoint (energy,
+# GB-energy backward (Born radii recomputed): born 23/1 + GB adjoint (energy,
 # dE/dR, dE/dq, direct dE/dx) 32/2 + chain adjoint (dH/dr and dH/ds both ways,
-# dH/drt = 0 far, r^-4-weighted fused s sums) 46/1
-BACKWARD_COST = (102, 4)
+# dH/drt = 0 far, r^-4-weighted fused s sums) 45/1
+BACKWARD_COST = (100, 4)
 # the same with the GB adjoint in its far form (1/f = 1/r: no exponential, no
 # dE/dR term; 22 FP32 lane operations and 1 MUFU) for a pair with D >= 18
-BACKWARD_FAR_COST = (92, 3)
+BACKWARD_FAR_COST = (90, 3)
 N_SM = 152
 # DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
 # capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)

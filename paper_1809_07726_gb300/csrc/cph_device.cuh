@@ -128,6 +128,14 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
     return y;
 }
 
+// The PTX ISA's approximate reciprocal (rcp.approx.ftz.f32): 1/r^2 in one MUFU
+// operation where the tile needs no 1/r.
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float exp2_ftz(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -566,7 +566,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
     for (int k = 0; k < kGJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 cj = make_float2(B.z, B.w), s2j = make_float2(C.x, C.y), s3j = make_float2(C.z, C.w);
-        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2], asi[2], asj[2], wt[2];
+        float2 dx[2], dy[2], dz[2], r2[2], t[2], asi[2], asj[2], wt[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
@@ -578,8 +578,7 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                 r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
                 r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
-            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
-            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv2 = make_float2(rcp_ftz(r2[u].x), rcp_ftz(r2[u].y));
             const float2 rinv4 = __fmul2_rn(rinv2, rinv2);
             const float2 yj = __fmul2_rn(s2j, rinv2), yi = __fmul2_rn(I[u].s2, rinv2);
             const float2 qj = hct_series_dr(yj), qi = hct_series_dr(yi);
@@ -610,8 +609,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (band_near<CUT>(r2[u].x, band)) {
-                    const GcNear o = gchain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.z, Nj.x,
-                                                 Nj.z, Mj.x, band.rc);
+                    const GcNear o = gchain_near(r2[u].x, rsqrt_ftz(r2[u].x), I[u].c.x, I[u].rt, I[u].irt,
+                                                 I[u].s, B.z, Nj.x, Nj.z, Mj.x, band.rc);
                     t[u].x = o.t;
                     hti[u * 32] += o.hti;
                     htj[(lane + k) & (kGJ - 1)].x += o.htj;
@@ -620,8 +619,8 @@ __device__ __forceinline__ void gchain_tile(const GcJs& sj, int lane, const GcI2
                     wt[u].x = 1.f;
                 }
                 if (band_near<CUT>(r2[u].y, band)) {
-                    const GcNear o = gchain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].irt, I[u].s, B.w, Nj.y,
-                                                 Nj.w, Mj.y, band.rc);
+                    const GcNear o = gchain_near(r2[u].y, rsqrt_ftz(r2[u].y), I[u].c.x, I[u].rt, I[u].irt,
+                                                 I[u].s, B.w, Nj.y, Nj.w, Mj.y, band.rc);
                     t[u].y = o.t;
                     hti[u * 32] += o.hti;
                     htj[(lane + k) & (kGJ - 1)].y += o.htj;

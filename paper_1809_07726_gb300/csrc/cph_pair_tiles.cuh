@@ -92,7 +92,7 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
     for (int k = 0; k < kTileJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 s2j = make_float2(B.z, B.w), s3j = make_float2(C.x, C.y);
-        float2 r2[2], rinv[2], hi[2], hj[2], wt[2];
+        float2 r2[2], hi[2], hj[2], wt[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const float2 dx = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
@@ -104,8 +104,7 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
                 r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
                 r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
-            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
-            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv2 = make_float2(rcp_ftz(r2[u].x), rcp_ftz(r2[u].y));
             wt[u] = __fmul2_rn(rinv2, rinv2); // r^-4, the weight of both far terms
             hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), s3j);
             hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), I[u].s3);
@@ -122,14 +121,14 @@ __device__ __forceinline__ void born_tile(const BoJs& sj, int lane, const BoI2 (
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (band_near<CUT>(r2[u].x, band)) {
-                    const float2 h = born_near(r2[u].x, rinv[u].x, I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z,
+                    const float2 h = born_near(r2[u].x, rsqrt_ftz(r2[u].x), I[u].rt, I[u].irt, I[u].s, C.z, Nj.x, Nj.z,
                                                band.rc);
                     hi[u].x = h.x;
                     hj[u].x = h.y;
                     wt[u].x = 1.f;
                 }
                 if (band_near<CUT>(r2[u].y, band)) {
-                    const float2 h = born_near(r2[u].y, rinv[u].y, I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w,
+                    const float2 h = born_near(r2[u].y, rsqrt_ftz(r2[u].y), I[u].rt, I[u].irt, I[u].s, C.w, Nj.y, Nj.w,
                                                band.rc);
                     hi[u].y = h.x;
                     hj[u].y = h.y;

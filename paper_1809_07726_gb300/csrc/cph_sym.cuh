@@ -525,7 +525,7 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
     for (int k = 0; k < kSymJ; ++k) {
         const float4 A = sj.a[lane + k], B = sj.b[lane + k], C = sj.c[lane + k];
         const float2 cj = make_float2(B.z, B.w), s2j = make_float2(C.x, C.y), s3j = make_float2(C.z, C.w);
-        float2 dx[2], dy[2], dz[2], r2[2], rinv[2], t[2];
+        float2 dx[2], dy[2], dz[2], r2[2], t[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             dx[u] = __fadd2_rn(I[u].x, make_float2(A.x, A.y));
@@ -537,8 +537,7 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
                 r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
                 r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
-            rinv[u] = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
-            const float2 rinv2 = __fmul2_rn(rinv[u], rinv[u]);
+            const float2 rinv2 = make_float2(rcp_ftz(r2[u].x), rcp_ftz(r2[u].y));
             const float2 qj = hct_series_dr(__fmul2_rn(s2j, rinv2));
             const float2 qi = hct_series_dr(__fmul2_rn(I[u].s2, rinv2));
             const float2 term = __ffma2_rn(__fmul2_rn(I[u].c, s3j), qj, __fmul2_rn(__fmul2_rn(cj, I[u].s3), qi));
@@ -557,9 +556,11 @@ __device__ __forceinline__ void chain_tile(const ChJs& sj, int lane, const ChI2 
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (band_near<CUT>(r2[u].x, band))
-                    t[u].x = chain_near(r2[u].x, rinv[u].x, I[u].c.x, I[u].rt, I[u].s, B.z, Nj.x, Nj.z, band.rc);
+                    t[u].x = chain_near(r2[u].x, rsqrt_ftz(r2[u].x), I[u].c.x, I[u].rt, I[u].s, B.z, Nj.x, Nj.z,
+                                        band.rc);
                 if (band_near<CUT>(r2[u].y, band))
-                    t[u].y = chain_near(r2[u].y, rinv[u].y, I[u].c.x, I[u].rt, I[u].s, B.w, Nj.y, Nj.w, band.rc);
+                    t[u].y = chain_near(r2[u].y, rsqrt_ftz(r2[u].y), I[u].c.x, I[u].rt, I[u].s, B.w, Nj.y, Nj.w,
+                                        band.rc);
             }
         }
 #pragma unroll
@@ -896,8 +897,7 @@ __device__ __forceinline__ void born_tile_q(const BoJs* sjg, int pr, int lane, i
                 r2[u].x = ((sk[u][0] >> jj) & 1u) ? skr2 : r2[u].x;
                 r2[u].y = ((sk[u][1] >> jj) & 1u) ? skr2 : r2[u].y;
             }
-            const float2 rinv = make_float2(rsqrt_ftz(r2[u].x), rsqrt_ftz(r2[u].y));
-            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+            const float2 rinv2 = make_float2(rcp_ftz(r2[u].x), rcp_ftz(r2[u].y));
             wt[u] = __fmul2_rn(rinv2, rinv2); // r^-4, the weight of both far terms
             hi[u] = __fmul2_rn(hct_series_h(__fmul2_rn(s2j, rinv2)), s3j);
             hj[u] = __fmul2_rn(hct_series_h(__fmul2_rn(I[u].s2, rinv2)), I[u].s3);
