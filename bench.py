@@ -66,9 +66,9 @@ BACKWARD_COST = (100, 4)
 # dE/dR term; 22 FP32 lane operations and 1 MUFU) for a pair with D >= 18
 BACKWARD_FAR_COST = (90, 3)
 N_SM = 152
-# DRAM bytes (read + write) per launch of a pass's pair kernel, from one ncu
-# capture of the current kernels on this workload (profiles/pair_passes_c4_ncu.md)
-PASS_DRAM_BYTES = {"born": 32.95e6 + 2.82e6, "gb": 88.55e6 + 5.88e6, "chain": 59.86e6 + 83.71e6}
+# DRAM bytes (read + write) per launch of a pass's pair kernel, from one
+# one-kernel ncu capture of each current kernel on this workload
+PASS_DRAM_BYTES = {"born": 32.95e6 + 0.0, "gb": 89.23e6 + 6.39e6, "chain": 59.86e6 + 0.09e6}
 FP32_LANES = 128   # FP32 lane operations per clock per SM
 MUFU_LANES = 16    # MUFU operations per clock per SM
 
@@ -284,12 +284,12 @@ def schedule_launches(t, mc_ph=10, mc_redox=10, ex_every=100):
     """Kernels one batched FP32 step t launches through a one-step cph_run:
     position staging + Born-radii pair kernel + finish, GB staging + pair
     kernel + finish, chain pair kernel + bonded terms + force finish,
-    observables, Langevin, the step-counter tick; each MC sweep kind adds its
-    per-site and per-walker kernels, an exchange step its row and attempt
-    kernels."""
+    observables, Langevin, the step-counter tick; each MC sweep kind adds the
+    staging of its charges and radii and its per-site and per-walker kernels,
+    an exchange step its row and attempt kernels."""
     n = 3 + 3 + 3 + 1 + 1 + 1
     if t > 0:
-        n += 2 * (int(t % mc_ph == 0) + int(t % mc_redox == 0)) + 2 * int(t % ex_every == 0)
+        n += 3 * (int(t % mc_ph == 0) + int(t % mc_redox == 0)) + 2 * int(t % ex_every == 0)
     return n
 
 

@@ -47,9 +47,9 @@ def test_timed_window_holds_the_schedule_events(steps, warmup):
 
 def test_schedule_launches_counts_the_launch_list():
     """The kernels of one step as the launch list of the 384-walker workload
-    shows them: 12 per plain step; +4 at an MC step with both kinds; +2 more
+    shows them: 12 per plain step; +6 at an MC step with both kinds; +2 more
     at an exchange step."""
     assert bench.schedule_launches(91) == 12
-    assert bench.schedule_launches(110) == 16
-    assert bench.schedule_launches(100) == 18
-    assert sum(bench.schedule_launches(t) for t in range(91, 111)) == 20 * 12 + 8 + 2
+    assert bench.schedule_launches(110) == 18
+    assert bench.schedule_launches(100) == 20
+    assert sum(bench.schedule_launches(t) for t in range(91, 111)) == 20 * 12 + 12 + 2
