@@ -1494,6 +1494,13 @@ int cph_init_system(const cph_system_desc* sys, int n_sys, const cph_grid_desc* 
     TRY(upload(E, sys_site_off, &d)); V.sys_site_off = d;
     TRY(upload(E, rho, &dd)); V.rho = dd;
     TRY(upload(E, rt, &dd)); V.rt = dd;
+    {
+        std::vector<double> irt(rt.size()), irho(rho.size());
+        for (size_t q = 0; q < rt.size(); ++q) irt[q] = 1.0 / rt[q];
+        for (size_t q = 0; q < rho.size(); ++q) irho[q] = 1.0 / rho[q];
+        TRY(upload(E, irt, &dd)); V.irt = dd;
+        TRY(upload(E, irho, &dd)); V.irho = dd;
+    }
     TRY(upload(E, sc, &dd)); V.sc = dd;
     TRY(upload(E, sigh, &dd)); V.sigh = dd;
     TRY(upload(E, sqe, &dd)); V.sqe = dd;

@@ -40,6 +40,7 @@ struct View {
     const int* sys_poff;
     const int* sys_site_off;
     const double *rho, *rt, *sc, *sigh, *sqe, *mass;
+    const double *irt, *irho; // 1/rt and 1/rho per system atom (no FP64 division per step)
     const int *excl_off, *excl_j;
     const int *bond_off, *bond_idx, *bond_ij;
     const double *bond_k, *bond_r0;

@@ -810,25 +810,28 @@ __global__ void k_final_forces(View V, int a0, int n) {
     const int s = V.w_sys[w];
     if (V.sys_ordered[s] || !V.w_local[w]) return;
     const int A = V.w_off[w], li = a - A, P = V.sys_poff[s];
-    double F[3] = {(double)V.Ffix[3 * a] / kScaleE, (double)V.Ffix[3 * a + 1] / kScaleE,
-                   (double)V.Ffix[3 * a + 2] / kScaleE};
+    // the atom's bonded-term forces (FP32, a few terms) are summed in FP32 and
+    // added once per component: FP64 conversions and additions are scarce
+    float fb[3] = {0.f, 0.f, 0.f};
     const float* buf = V.tforce + V.w_tf_off[w];
     const int b0 = V.sys_bond_off[s], nb = V.sys_bond_off[s + 1] - b0, an0 = V.sys_ang_off[s];
     for (int e = V.bond_off[P + li]; e < V.bond_off[P + li + 1]; ++e) {
         const int b = V.bond_idx[e];
         const int role = (V.bond_ij[2 * b] == li) ? 0 : 1;
         const float* o = buf + 6 * (b - b0) + 3 * role;
-        for (int c = 0; c < 3; ++c) F[c] += o[c];
+        for (int c = 0; c < 3; ++c) fb[c] += o[c];
     }
     for (int e = V.ang_off[P + li]; e < V.ang_off[P + li + 1]; ++e) {
         const int ag = V.ang_idx[e];
         const int role = (V.ang_ijk[3 * ag] == li) ? 0 : ((V.ang_ijk[3 * ag + 1] == li) ? 1 : 2);
         const float* o = buf + 6 * (size_t)nb + 9 * (size_t)(ag - an0) + 3 * role;
-        for (int c = 0; c < 3; ++c) F[c] += o[c];
+        for (int c = 0; c < 3; ++c) fb[c] += o[c];
     }
-    V.F[3 * a] = F[0];
-    V.F[3 * a + 1] = F[1];
-    V.F[3 * a + 2] = F[2];
+    double F[3];
+    for (int c = 0; c < 3; ++c) {
+        F[c] = (double)V.Ffix[3 * a + c] / kScaleE + (double)fb[c];
+        V.F[3 * a + c] = F[c];
+    }
     if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(V.status, 1);
 }
 
@@ -1091,14 +1094,16 @@ __global__ void k_fin_born(View V, int a0, int n, int zero_energy) {
     if (V.sys_ordered[V.w_sys[w]] || !V.w_local[w]) return;
     const int li = a - V.w_off[w];
     const int P = V.sys_poff[V.w_sys[w]] + li;
-    const double rt = V.rt[P], rho = V.rho[P];
+    // 1/rt and 1/rho come from set-up: one FP64 division per atom (FP64
+    // arithmetic is scarce on GB300)
+    const double rt = V.rt[P], irho = V.irho[P];
     const double psi = 0.5 * rt * ((double)V.Hfix[a] / kScaleH);
     V.Hfix[a] = 0;
     const double th = tanh(psi * (V.alpha + psi * (-V.beta + psi * V.gamma)));
-    const double R = 1.0 / (1.0 / rt - th / rho);
+    const double R = 1.0 / (V.irt[P] - th * irho);
     V.psi[a] = psi;
     V.R[a] = R;
-    V.dRdpsi[a] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) / rho;
+    V.dRdpsi[a] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) * irho;
     V.Ffix[3 * a] = 0;
     V.Ffix[3 * a + 1] = 0;
     V.Ffix[3 * a + 2] = 0;
