@@ -185,17 +185,17 @@ __global__ void __launch_bounds__(kTile) k_born(const Item* __restrict__ items, 
     acc = group_total<WPA>(acc, gsh);
     if (vi && sub == 0) {
         const double sumH = Pr::value(acc, kScaleH);
-        const double rt = V.rt[P + i], rho = V.rho[P + i];
+        const double rt = V.rt[P + i], irho = V.irho[P + i]; // 1/rt, 1/rho from set-up
         const double psi = 0.5 * rt * sumH;
         const double th = tanh(psi * (V.alpha + psi * (-V.beta + psi * V.gamma)));
-        const double R = 1.0 / (1.0 / rt - th / rho);
+        const double R = 1.0 / (V.irt[P + i] - th * irho);
         V.psi[A + i] = psi;
         V.R[A + i] = R;
         V.Ffix[3 * (A + i)] = 0;
         V.Ffix[3 * (A + i) + 1] = 0;
         V.Ffix[3 * (A + i) + 2] = 0;
         V.dRfix[A + i] = 0;
-        V.dRdpsi[A + i] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) / rho;
+        V.dRdpsi[A + i] = R * R * (1.0 - th * th) * (V.alpha + psi * (-2.0 * V.beta + 3.0 * V.gamma * psi)) * irho;
     }
 }
 
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kTile) k_gb(const Item* __restrict__ items, Vi
         const double R = V.R[A + i];
         const double dEdR = 0.5 * (V.tau_pair * Pr::value(adr, kScaleE)
                                    + salt_taud(R, V.inv_eps_in, V.inv_eps_out, V.kappa) * q * q / (R * R))
-                          - 6.0 * sa_ace(V.sa_gamma, V.sa_probe, V.rho[P + i], R) / R;
+                          - (V.sa_gamma != 0.0 ? 6.0 * sa_ace(V.sa_gamma, V.sa_probe, V.rho[P + i], R) / R : 0.0);
         V.c[A + i] = dEdR * V.dRdpsi[A + i] * 0.5 * V.rt[P + i];
         V.Fd[3 * (A + i)] = Pr::value(fx, kScaleE);
         V.Fd[3 * (A + i) + 1] = Pr::value(fy, kScaleE);
@@ -448,6 +448,69 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
             if (li == ib) F[c] += gi[c] + gk[c];
         }
         if (ia == li) ea += V.ang_k[a] * dth * dth;
+    }
+}
+
+// The same terms for the FP32 mode, in the arithmetic of the symmetric path's
+// bonded kernel: FP64 only where a difference of nearly equal numbers decides
+// the result (the separations, r^2 - r0^2, the dot and cross products behind
+// the sine and cosine of theta - theta0), FP32 elsewhere (atan2f for theta -
+// theta0), so that the few FP64 units of the chip are not the bound; the
+// atom's forces and energies are summed in FP32.
+__device__ inline void bonded_atom32(const View& V, int A, int P, int li, int lane, int stride, float F[3],
+                                     float& eb, float& ea) {
+    const double* x = V.x;
+    for (int e = V.bond_off[P + li] + lane; e < V.bond_off[P + li + 1]; e += stride) {
+        const int b = V.bond_idx[e];
+        const int ia = V.bond_ij[2 * b], ib = V.bond_ij[2 * b + 1];
+        const int o = (ia == li) ? ib : ia;
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + li) + c] - x[3 * (A + o) + c];
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double r0 = V.bond_r0[b];
+        const float r = sqrtf((float)r2);
+        const float dr = (float)(r2 - r0 * r0) / (r + (float)r0); // r - r0 at FP32 relative precision
+        const float kb = (float)V.bond_k[b];
+        const float g = 2.f * kb * dr / r;
+        for (int c = 0; c < 3; ++c) F[c] -= g * (float)d[c];
+        if (ia == li) eb += kb * dr * dr;
+    }
+    for (int e = V.ang_off[P + li] + lane; e < V.ang_off[P + li + 1]; e += stride) {
+        const int a = V.ang_idx[e];
+        const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
+        double u[3], v[3];
+        for (int c = 0; c < 3; ++c) {
+            u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
+            v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
+        }
+        const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                     cz = u[0] * v[1] - u[1] * v[0];
+        const double w2 = cx * cx + cy * cy + cz * cz;
+        const double y = (double)rsqrtf(fmaxf((float)w2, 1e-30f));
+        double wn = w2 * y; // |u x v| by an FP32 reciprocal square root and one Newton step
+        wn += 0.5 * (w2 - wn * wn) * y;
+        const double2 cs0 = V.ang_cs0[a];
+        const float dth = atan2f((float)(wn * cs0.x - uv * cs0.y), (float)(uv * cs0.x + wn * cs0.y));
+        const float ka = (float)V.ang_k[a];
+        float uf[3], vf[3];
+        for (int c = 0; c < 3; ++c) {
+            uf[c] = (float)u[c];
+            vf[c] = (float)v[c];
+        }
+        const float ru2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+        const float rv2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+        const float iuv = rsqrtf(ru2 * rv2);
+        const float cs = (float)uv * iuv, sn = fmaxf((float)wn * iuv, 1e-20f);
+        const float k = -2.f * ka * dth / sn; // dE/dcos(theta)
+        for (int c = 0; c < 3; ++c) {
+            const float gi = k * (vf[c] * iuv - cs * uf[c] / ru2);
+            const float gk = k * (uf[c] * iuv - cs * vf[c] / rv2);
+            if (li == ia) F[c] -= gi;
+            if (li == ic) F[c] -= gk;
+            if (li == ib) F[c] += gi + gk;
+        }
+        if (ia == li) ea += ka * dth * dth;
     }
 }
 
@@ -555,11 +618,20 @@ __global__ void __launch_bounds__(kTile) k_chain(const Item* __restrict__ items,
     double eb = 0.0, ea = 0.0;
     double Fb[3] = {0.0, 0.0, 0.0};
     // bonded terms of atom i over the group's threads, summed in a fixed order
-    if (vi) bonded_atom(V, A, P, i, sub, 32 * WPA, Fb, eb, ea);
+    if constexpr (sizeof(Real) == 4) {
+        float fb[3] = {0.f, 0.f, 0.f}, ebf = 0.f, eaf = 0.f;
+        if (vi) bonded_atom32(V, A, P, i, sub, 32 * WPA, fb, ebf, eaf);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) Fb[c] = group_total<WPA>(Fb[c], gsh);
-    eb = group_total<WPA>(eb, gsh);
-    ea = group_total<WPA>(ea, gsh);
+        for (int c = 0; c < 3; ++c) Fb[c] = (double)group_total<WPA>(fb[c], gsh);
+        eb = (double)group_total<WPA>(ebf, gsh);
+        ea = (double)group_total<WPA>(eaf, gsh);
+    } else {
+        if (vi) bonded_atom(V, A, P, i, sub, 32 * WPA, Fb, eb, ea);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Fb[c] = group_total<WPA>(Fb[c], gsh);
+        eb = group_total<WPA>(eb, gsh);
+        ea = group_total<WPA>(ea, gsh);
+    }
     if (sub != 0) eb = ea = 0.0; // the group's totals, counted once
     if (vi && sub == 0) {
         double F[3] = {V.Fd[3 * (A + i)] + Pr::value(fx, kScaleE) + Fb[0],
