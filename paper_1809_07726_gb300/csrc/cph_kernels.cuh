@@ -418,7 +418,7 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
         for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + li) + c] - x[3 * (A + o) + c];
         const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const double dr = r - V.bond_r0[b];
-        const double g = 2.0 * V.bond_k[b] * dr / r;
+        const double g = 2.0 * V.bond_k[b] * dr / r; // one FP64 division per bond
         for (int c = 0; c < 3; ++c) F[c] -= g * d[c];
         if (ia == li) eb += V.bond_k[b] * dr * dr;
     }
@@ -430,17 +430,19 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
             u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
             v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
         }
-        const double ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        const double rv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (ru * rv);
+        const double ru2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const double rv2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        // three FP64 divisions per angle (FP64 arithmetic is scarce on GB300)
+        const double iuv = 1.0 / sqrt(ru2 * rv2), iru2 = 1.0 / ru2, irv2 = 1.0 / rv2;
+        double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) * iuv;
         cs = fmin(1.0, fmax(-1.0, cs));
         const double th = acos(cs);
         const double dth = th - V.ang_t0[a];
         const double k = -2.0 * V.ang_k[a] * dth / sqrt(fmax(1e-300, 1.0 - cs * cs)); // dE/dcos
         double gi[3], gk[3];
         for (int c = 0; c < 3; ++c) {
-            gi[c] = k * (v[c] / (ru * rv) - cs * u[c] / (ru * ru));
-            gk[c] = k * (u[c] / (ru * rv) - cs * v[c] / (rv * rv));
+            gi[c] = k * (v[c] * iuv - cs * u[c] * iru2);
+            gk[c] = k * (u[c] * iuv - cs * v[c] * irv2);
         }
         for (int c = 0; c < 3; ++c) {
             if (li == ia) F[c] -= gi[c];
