@@ -173,9 +173,10 @@ def test_site_less_batch_runs_with_mc_switched_on():
     assert (v.sum(0) == 12).all() and (v.sum(1) == 12).all()
 
 
-@pytest.mark.parametrize("prec,tf,te,tr", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL),
-                                           (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11)])
-def test_perturbed_geometry_matches_oracle(prec, tf, te, tr):
+@pytest.mark.parametrize("prec,tf,te,tr,warp", [(cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, False),
+                                                (cphremd.PREC_FP32, FORCE_RMS, ENERGY_REL, R_REL, True),
+                                                (cphremd.PREC_FP64, 1e-10, 1e-10, 1e-11, False)])
+def test_perturbed_geometry_matches_oracle(prec, tf, te, tr, warp):
     """The synthetic chains start at their bond lengths and angles, where the
     bonded terms vanish; here every atom is displaced (0.1 A) and a few angles
     are opened to within ~3 degrees of linear, so bonds, angles (and their
@@ -184,11 +185,16 @@ def test_perturbed_geometry_matches_oracle(prec, tf, te, tr):
     of components ~100 times larger than itself; FP32 coordinates and pair
     terms are exact to ~1e-7 of each term, so in FP32 E_LJ is held to 1e-6 of
     sum |e_ij| and the total to 1e-6 of the sum of its components' scales
-    (every other term to 1e-6 of itself)."""
+    (every other term to 1e-6 of itself).  warp: both systems on one warp per
+    atom (the ordered kernels, whose FP32 bonded terms are the mixed-precision
+    form)."""
     systems = [synth.make_system(290, 45, n_ph=3, ph_atoms=(6, 12), ph_states=(2, 4)),
                synth.make_system(1100, 46, n_ph=4)]
     grid = _grid(systems)
     eng = cphremd.init_system(systems, grid, seed=2, precision=prec)
+    if warp:
+        for k in range(len(systems)):
+            eng.set_tile_shape(k, cphremd.SHAPE_WARP_PER_ATOM)
     rng = np.random.default_rng(5)
     x = eng.positions()
     xs = []
