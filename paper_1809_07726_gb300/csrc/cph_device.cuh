@@ -257,6 +257,24 @@ __device__ __forceinline__ float hct_dr(float r, float rinv, float rt, float s, 
     return d;
 }
 
+// dH/dr with the fast logarithm (__logf) in the closed form: the chain-rule
+// force of a near pair, where the log term is O(1) and its ~1e-7 absolute
+// error stays far below the force bar.
+__device__ __forceinline__ float hct_dr_fastlog(float r, float rinv, float rt, float s, float rc = INFINITY) {
+    float rinv2 = rinv * rinv;
+    if (hct_far(r, rt, s, rc)) {
+        float x = s * rinv, y = x * x;
+        return -x * y * hct_series_dr(y) * rinv2;
+    }
+    float d = 0.f;
+    if (!hct_empty(r, rt, s, rc)) {
+        const float U = fminf(r + s, rc), L = fmaxf(rt, fabsf(r - s));
+        const float iLU = __fdividef(1.f, L * U), iL = U * iLU, iU = L * iLU;
+        d = -0.25f * (iL - iU) * (iL + iU) * fmaf(s * s, rinv2, 1.f) - 0.5f * __logf(L * iU) * rinv2;
+    }
+    return d;
+}
+
 __device__ __forceinline__ float hct_ds(float r, float rinv, float rt, float s, float rc = INFINITY) {
     if (hct_far(r, rt, s, rc)) {
         float x = s * rinv, y = x * x;

@@ -512,7 +512,7 @@ struct ChJs {
 __device__ __forceinline__ float chain_near(float r2, float rinv, float c_i, float rt_i, float s_i, float c_j,
                                          float s_j, float rt_j, float rc) {
     const float r = r2 * rinv;
-    const float g = c_i * hct_dr(r, rinv, rt_i, s_j, rc) + c_j * hct_dr(r, rinv, rt_j, s_i, rc);
+    const float g = c_i * hct_dr_fastlog(r, rinv, rt_i, s_j, rc) + c_j * hct_dr_fastlog(r, rinv, rt_j, s_i, rc);
     return -g * rinv;
 }
 
