@@ -453,12 +453,58 @@ __device__ inline void bonded_atom(const View& V, int A, int P, int li, int lane
     }
 }
 
-// The same terms for the FP32 mode, in the arithmetic of the symmetric path's
-// bonded kernel: FP64 only where a difference of nearly equal numbers decides
-// the result (the separations, r^2 - r0^2, the dot and cross products behind
-// the sine and cosine of theta - theta0), FP32 elsewhere (atan2f for theta -
-// theta0), so that the few FP64 units of the chip are not the bound; the
-// atom's forces and energies are summed in FP32.
+// FP32-mode bonded terms (the symmetric bonded kernel and the ordered chain
+// kernel share them): FP64 only where a difference of nearly equal numbers
+// decides the result (the separations, r^2 - r0^2, the dot and cross products
+// behind the sine and cosine of theta - theta0), FP32 elsewhere (atan2f for
+// theta - theta0), so that the few FP64 units of the chip are not the bound.
+//
+// One harmonic bond from its FP64 separation d = x_i - x_j: the force on i is
+// -g d, on j +g d; e its energy.
+__device__ __forceinline__ void bond_term32(const double (&d)[3], double r0d, double kbd, float& g, float& e) {
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float r = sqrtf((float)r2);
+    const float dr = (float)(r2 - r0d * r0d) / (r + (float)r0d); // r - r0 at FP32 relative precision
+    const float kb = (float)kbd;
+    g = 2.f * kb * dr / r;
+    e = kb * dr * dr;
+}
+
+// One harmonic angle i-j-k from u = x_i - x_j, v = x_k - x_j (FP64) and
+// (cos theta0, sin theta0): the force on i is -gi, on k -gk, on j gi + gk;
+// e its energy.
+__device__ __forceinline__ void angle_term32(const double (&u)[3], const double (&v)[3], double2 cs0, double kad,
+                                             float (&gi)[3], float (&gk)[3], float& e) {
+    // |u||v| cos(theta) and |u||v| sin(theta) in FP64 (the norm of the cross
+    // product by an FP32 reciprocal square root and one Newton step)
+    const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+    const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    const double w2 = cx * cx + cy * cy + cz * cz;
+    const double y = (double)rsqrtf(fmaxf((float)w2, 1e-30f));
+    double wn = w2 * y;
+    wn += 0.5 * (w2 - wn * wn) * y;
+    // theta - theta0 = atan2(sin(theta - theta0), cos(theta - theta0))
+    const float dth = atan2f((float)(wn * cs0.x - uv * cs0.y), (float)(uv * cs0.x + wn * cs0.y));
+    const float ka = (float)kad;
+    float uf[3], vf[3];
+    for (int c = 0; c < 3; ++c) {
+        uf[c] = (float)u[c];
+        vf[c] = (float)v[c];
+    }
+    const float ru2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+    const float rv2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+    const float iuv = rsqrtf(ru2 * rv2);                     // 1 / (|u| |v|)
+    const float cs = (float)uv * iuv, sn = fmaxf((float)wn * iuv, 1e-20f);
+    const float k = -2.f * ka * dth / sn;                     // dE/dcos(theta)
+    for (int c = 0; c < 3; ++c) {
+        gi[c] = k * (vf[c] * iuv - cs * uf[c] / ru2);
+        gk[c] = k * (uf[c] * iuv - cs * vf[c] / rv2);
+    }
+    e = ka * dth * dth;
+}
+
+// The FP32-mode terms of one atom (the ordered chain kernel: each atom takes
+// the terms it is part of), its forces and energies summed in FP32.
 __device__ inline void bonded_atom32(const View& V, int A, int P, int li, int lane, int stride, float F[3],
                                      float& eb, float& ea) {
     const double* x = V.x;
@@ -468,14 +514,10 @@ __device__ inline void bonded_atom32(const View& V, int A, int P, int li, int la
         const int o = (ia == li) ? ib : ia;
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + li) + c] - x[3 * (A + o) + c];
-        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const double r0 = V.bond_r0[b];
-        const float r = sqrtf((float)r2);
-        const float dr = (float)(r2 - r0 * r0) / (r + (float)r0); // r - r0 at FP32 relative precision
-        const float kb = (float)V.bond_k[b];
-        const float g = 2.f * kb * dr / r;
+        float g, en;
+        bond_term32(d, V.bond_r0[b], V.bond_k[b], g, en);
         for (int c = 0; c < 3; ++c) F[c] -= g * (float)d[c];
-        if (ia == li) eb += kb * dr * dr;
+        if (ia == li) eb += en;
     }
     for (int e = V.ang_off[P + li] + lane; e < V.ang_off[P + li + 1]; e += stride) {
         const int a = V.ang_idx[e];
@@ -485,34 +527,14 @@ __device__ inline void bonded_atom32(const View& V, int A, int P, int li, int la
             u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
             v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
         }
-        const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
-        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
-                     cz = u[0] * v[1] - u[1] * v[0];
-        const double w2 = cx * cx + cy * cy + cz * cz;
-        const double y = (double)rsqrtf(fmaxf((float)w2, 1e-30f));
-        double wn = w2 * y; // |u x v| by an FP32 reciprocal square root and one Newton step
-        wn += 0.5 * (w2 - wn * wn) * y;
-        const double2 cs0 = V.ang_cs0[a];
-        const float dth = atan2f((float)(wn * cs0.x - uv * cs0.y), (float)(uv * cs0.x + wn * cs0.y));
-        const float ka = (float)V.ang_k[a];
-        float uf[3], vf[3];
+        float gi[3], gk[3], en;
+        angle_term32(u, v, V.ang_cs0[a], V.ang_k[a], gi, gk, en);
         for (int c = 0; c < 3; ++c) {
-            uf[c] = (float)u[c];
-            vf[c] = (float)v[c];
+            if (li == ia) F[c] -= gi[c];
+            if (li == ic) F[c] -= gk[c];
+            if (li == ib) F[c] += gi[c] + gk[c];
         }
-        const float ru2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-        const float rv2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
-        const float iuv = rsqrtf(ru2 * rv2);
-        const float cs = (float)uv * iuv, sn = fmaxf((float)wn * iuv, 1e-20f);
-        const float k = -2.f * ka * dth / sn; // dE/dcos(theta)
-        for (int c = 0; c < 3; ++c) {
-            const float gi = k * (vf[c] * iuv - cs * uf[c] / ru2);
-            const float gk = k * (uf[c] * iuv - cs * vf[c] / rv2);
-            if (li == ia) F[c] -= gi;
-            if (li == ic) F[c] -= gk;
-            if (li == ib) F[c] += gi + gk;
-        }
-        if (ia == li) ea += ka * dth * dth;
+        if (ia == li) ea += en;
     }
 }
 

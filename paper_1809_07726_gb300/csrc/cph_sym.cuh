@@ -32,6 +32,7 @@
 #include "cph_device.cuh"
 #include "cph_internal.h"
 #include "cph_pair_tiles.cuh"
+#include "cph_kernels.cuh"
 
 namespace cph {
 
@@ -718,26 +719,20 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
     float* buf = V.tforce + V.w_tf_off[w];
     const double* x = V.x;
     double eb = 0.0, ea = 0.0;
-    // FP64 only where a difference of nearly equal numbers decides the result
-    // (r^2 - r0^2; the sine and cosine of theta - theta0); FP32 elsewhere, so
-    // that the few FP64 units of the chip are not the bound.
+    // the FP32-mode term arithmetic of bond_term32 / angle_term32
     if (t < nb) {
         const int b = b0 + t;
         const int i = V.bond_ij[2 * b], j = V.bond_ij[2 * b + 1];
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = x[3 * (A + i) + c] - x[3 * (A + j) + c];
-        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const double r0 = V.bond_r0[b];
-        const float r = sqrtf((float)r2);
-        const float dr = (float)(r2 - r0 * r0) / (r + (float)r0); // r - r0 at FP32 relative precision
-        const float kb = (float)V.bond_k[b];
-        const float g = 2.f * kb * dr / r;
+        float g, e;
+        bond_term32(d, V.bond_r0[b], V.bond_k[b], g, e);
         for (int c = 0; c < 3; ++c) {
             const float f = g * (float)d[c];
             buf[6 * t + c] = -f;
             buf[6 * t + 3 + c] = f;
         }
-        eb = (double)(kb * dr * dr);
+        eb = (double)e;
     } else if (t < nb + na) {
         const int la = t - nb, a = a0 + la;
         const int ia = V.ang_ijk[3 * a], ib = V.ang_ijk[3 * a + 1], ic = V.ang_ijk[3 * a + 2];
@@ -746,38 +741,15 @@ __global__ void __launch_bounds__(kBondedThreads) k_bonded_terms(View V, int w0)
             u[c] = x[3 * (A + ia) + c] - x[3 * (A + ib) + c];
             v[c] = x[3 * (A + ic) + c] - x[3 * (A + ib) + c];
         }
-        // |u||v| cos(theta) and |u||v| sin(theta) in FP64 (the norm of the cross
-        // product by an FP32 reciprocal square root and one Newton step)
-        const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
-        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
-                     cz = u[0] * v[1] - u[1] * v[0];
-        const double w2 = cx * cx + cy * cy + cz * cz;
-        const double y = (double)rsqrtf(fmaxf((float)w2, 1e-30f));
-        double wn = w2 * y;
-        wn += 0.5 * (w2 - wn * wn) * y;
-        // theta - theta0 = atan2(sin(theta - theta0), cos(theta - theta0))
-        const double2 cs0 = V.ang_cs0[a];
-        const float dth = atan2f((float)(wn * cs0.x - uv * cs0.y), (float)(uv * cs0.x + wn * cs0.y));
-        const float ka = (float)V.ang_k[a];
-        float uf[3], vf[3];
-        for (int c = 0; c < 3; ++c) {
-            uf[c] = (float)u[c];
-            vf[c] = (float)v[c];
-        }
-        const float ru2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-        const float rv2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
-        const float iuv = rsqrtf(ru2 * rv2);                     // 1 / (|u| |v|)
-        const float cs = (float)uv * iuv, sn = fmaxf((float)wn * iuv, 1e-20f);
-        const float k = -2.f * ka * dth / sn;                     // dE/dcos(theta)
+        float gi[3], gk[3], e;
+        angle_term32(u, v, V.ang_cs0[a], V.ang_k[a], gi, gk, e);
         float* o = buf + 6 * (size_t)nb + 9 * (size_t)la;
         for (int c = 0; c < 3; ++c) {
-            const float gi = k * (vf[c] * iuv - cs * uf[c] / ru2);
-            const float gk = k * (uf[c] * iuv - cs * vf[c] / rv2);
-            o[c] = -gi;
-            o[3 + c] = gi + gk;
-            o[6 + c] = -gk;
+            o[c] = -gi[c];
+            o[3 + c] = gi[c] + gk[c];
+            o[6 + c] = -gk[c];
         }
-        ea = (double)(ka * dth * dth);
+        ea = (double)e;
     }
     if (ENERGY) {
 #pragma unroll
