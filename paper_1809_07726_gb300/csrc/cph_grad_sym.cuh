@@ -208,13 +208,13 @@ __global__ void __launch_bounds__(kGT, 6) k_gborn_sym(SView g) {
 __global__ void k_gfin_born(SView g) {
     const size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= (size_t)g.n_rep * g.n) return;
-    const double rho = g.rho[a], rt = rho - g.offset;
+    const double rho = g.rho[a], rt = rho - g.offset, irho = 1.0 / rho;
     const double psi = 0.5 * rt * ((double)g.Hfix[a] / kScaleH);
     const double th = tanh(psi * (g.alpha + psi * (-g.beta + psi * g.gamma)));
-    const double R = 1.0 / (1.0 / rt - th / rho);
+    const double R = 1.0 / (1.0 / rt - th * irho);
     g.psi[a] = psi;
     g.R[a] = R;
-    g.gpsi[a] = R * R * (1.0 - th * th) * (g.alpha + psi * (-2.0 * g.beta + 3.0 * g.gamma * psi)) / rho; // dR/dpsi for now
+    g.gpsi[a] = R * R * (1.0 - th * th) * (g.alpha + psi * (-2.0 * g.beta + 3.0 * g.gamma * psi)) * irho; // dR/dpsi for now
     g.dRfix[a] = 0; // same slot as Hfix
     g.dqfix[a] = 0;
     g.gfix[3 * a] = 0;
@@ -494,12 +494,24 @@ __global__ void k_gfin_c(SView g) {
     const double q = (double)g.q[a] * g.sqrt_k, R = g.R[a];
     const double esa = sa_ace(g.sa_gamma, g.sa_probe, (double)g.rho[a], R);
     const double ts = salt_tau(R, g.inv_eps_in, g.inv_eps_out, g.kappa); // tau of the self term
-    atomicAdd((unsigned long long*)&g.eacc[a / g.n],
-              (unsigned long long)__double2ll_rn((-0.5 * ts * q * q / R + esa) * kScaleE));
+    const long long e = __double2ll_rn((-0.5 * ts * q * q / R + esa) * kScaleE);
+    // one atomic per warp when the warp's atoms share a replica (exact integer
+    // sums, so the total is the same whichever way they are grouped)
+    const unsigned mask = __activemask();
+    const long long rep = (long long)(a / g.n);
+    const long long rep0 = __shfl_sync(mask, rep, __ffs(mask) - 1);
+    if (mask == 0xffffffffu && __all_sync(mask, rep == rep0)) {
+        long long t = e;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long*)&g.eacc[rep], (unsigned long long)t);
+    } else {
+        atomicAdd((unsigned long long*)&g.eacc[rep], (unsigned long long)e);
+    }
     if (!BACKWARD) return;
     const double dEdR = 0.5 * (g.tau_pair * ((double)g.dRfix[a] / kScaleE)
                                + salt_taud(R, g.inv_eps_in, g.inv_eps_out, g.kappa) * q * q / (R * R))
-                      - 6.0 * esa / R;
+                      - (g.sa_gamma != 0.0 ? 6.0 * esa / R : 0.0); // no FP64 division without the term
     const double rt = (double)g.rho[a] - g.offset;
     const double gpsi = dEdR * g.gpsi[a]; // gpsi slot held dR/dpsi
     const double dq = -g.sqrt_k * (g.tau_pair * ((double)g.dqfix[a] / kScaleE) + ts * q / R);
