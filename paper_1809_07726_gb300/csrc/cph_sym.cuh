@@ -1026,10 +1026,10 @@ __global__ void __launch_bounds__(kSymThreads, 5) k_born_sym(const SymItem* __re
             }
             if (masked) born_tile_q<true, CUT>(sj, pr, lane, warp, I, ah, jh, sk, band, nb, nq, V.status);
             else born_tile_q<false, CUT>(sj, pr, lane, warp, I, ah, jh, sk, band, nb, nq, V.status);
-            // per-tile conversion (each half is one tile)
+            // one conversion per tile pair (the two tiles' partials summed in FP32)
 #pragma unroll
             for (int u = 0; u < 2; ++u)
-                hx[u] += to_fixed(ah[u].x, (float)kScaleH) + to_fixed(ah[u].y, (float)kScaleH);
+                hx[u] += to_fixed(ah[u].x + ah[u].y, (float)kScaleH);
             red[2 * pr][warp][lane] = jh.x;
             red[2 * pr + 1][warp][lane] = jh.y;
         }
