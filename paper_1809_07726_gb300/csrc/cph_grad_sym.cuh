@@ -559,7 +559,7 @@ static __device__ __noinline__ GcNear gchain_near(float r2, float rinv, float ci
                                                   float cj, float sj, float rtj, float irtj, float rc) {
     const float r = r2 * rinv;
     GcNear o;
-    o.t = (ci * hct_dr(r, rinv, rti, sj, rc) + cj * hct_dr(r, rinv, rtj, si, rc)) * rinv;
+    o.t = (ci * hct_dr_fastlog(r, rinv, rti, sj, rc) + cj * hct_dr_fastlog(r, rinv, rtj, si, rc)) * rinv;
     o.hti = hct_drt(r, rti, irti, sj, rc);
     o.htj = hct_drt(r, rtj, irtj, si, rc);
     o.asi = cj * hct_ds(r, rinv, rtj, si, rc);
