@@ -735,7 +735,8 @@ def run_gpu(args):
                    "autotuned_chunk_jtiles": chunk, "autotuned_tile_shapes": shapes,
                    "parallelism": ("replicas batched per launch" if not sharded else
                                    f"one grid sharded by walker over {world} GPUs (rank 0: {len(mine)} "
-                                   "walkers); exchange rows all-gathered over NCCL at exchange steps")},
+                                   "walkers); exchange rows all-gathered over "
+                                   f"{os.environ.get('CPH_BENCH_DIST_BACKEND', 'nccl')} at exchange steps")},
         "window": events,
         "pair_evals_per_s": total_pairs * args.steps / t_max,
         "per_replica": None if sharded else {
@@ -747,7 +748,7 @@ def run_gpu(args):
         "graph_replay": None if sharded else {"value": W / (graph_ms / 1e3), "unit": "replica-steps/s",
                                               "ms_per_step": graph_ms, "steps": period},
         "pass_ms": {n: float(x) for n, x in zip(names, pass_ms)},
-        "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": f"k_{names[dom]}_sym", "achieved": achieved,
                      "peak": peak, "unit": "Gpair/s", "frac": achieved / peak, "traffic": PASS_DRAM_BYTES.get(names[dom]),
                      "traffic_basis": "DRAM read + write bytes per launch of the pass's pair kernel (ncu)",
                      "peak_basis": f"{N_SM} SM x {f_mhz:.0f} MHz (median sampled) / "
